@@ -1,0 +1,223 @@
+"""Seeded synthetic inputs for the contracted-ERI path.
+
+This module holds random numbers and geometry only: molecule layouts, shell
+lists, primitive exponents and contraction coefficients, quartet lists.  It
+contains none of the integral arithmetic (no normalisation, no Gaussian
+products, no recurrences), so both the CPU oracle and the CUDA path may use it.
+
+Units: the workload recipes are stated in Angstrom and converted here to bohr
+(1 bohr = 0.529177210903 Angstrom, CODATA 2018); every array handed out is in
+bohr.
+
+A ``Basis`` is a flat, C-friendly description:
+
+* ``centers``   float64 [ncenter, 3]   bohr
+* ``shell_l``   int32   [nshell]       angular momentum, 0..4
+* ``shell_nprim`` int32 [nshell]       contraction depth K
+* ``shell_center`` int32 [nshell]      index into ``centers``
+* ``shell_prim`` int32  [nshell]       offset of the shell's first primitive
+* ``exps``      float64 [nprim_total]  primitive exponents (bohr^-2)
+* ``coefs``     float64 [nprim_total]  raw contraction coefficients; the
+                                       primitive normalisation is applied by
+                                       the integral code, not here.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+ANGSTROM_TO_BOHR = 1.0 / 0.529177210903
+
+L_LETTER = "spdfg"
+
+
+@dataclass
+class Basis:
+    centers: np.ndarray
+    shell_l: np.ndarray
+    shell_nprim: np.ndarray
+    shell_center: np.ndarray
+    shell_prim: np.ndarray
+    exps: np.ndarray
+    coefs: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nshell(self) -> int:
+        return int(self.shell_l.shape[0])
+
+    def validate(self) -> None:
+        assert self.centers.dtype == np.float64 and self.centers.ndim == 2 and self.centers.shape[1] == 3
+        for a in (self.shell_l, self.shell_nprim, self.shell_center, self.shell_prim):
+            assert a.dtype == np.int32 and a.shape == (self.nshell,)
+        assert self.exps.dtype == np.float64 and self.coefs.dtype == np.float64
+        assert np.all(self.shell_prim + self.shell_nprim <= self.exps.shape[0])
+
+
+class _BasisBuilder:
+    def __init__(self):
+        self.centers: list = []
+        self.l: list = []
+        self.k: list = []
+        self.c: list = []
+        self.p: list = []
+        self.exps: list = []
+        self.coefs: list = []
+
+    def add_center(self, xyz) -> int:
+        self.centers.append(np.asarray(xyz, dtype=np.float64))
+        return len(self.centers) - 1
+
+    def add_shell(self, l: int, center: int, exps, coefs) -> int:
+        exps = np.asarray(exps, dtype=np.float64)
+        coefs = np.asarray(coefs, dtype=np.float64)
+        assert exps.shape == coefs.shape and exps.ndim == 1 and exps.size >= 1
+        self.l.append(l)
+        self.k.append(exps.size)
+        self.c.append(center)
+        self.p.append(sum(len(e) for e in self.exps))
+        self.exps.append(exps)
+        self.coefs.append(coefs)
+        return len(self.l) - 1
+
+    def build(self, **meta) -> Basis:
+        b = Basis(
+            centers=np.ascontiguousarray(np.array(self.centers, dtype=np.float64).reshape(-1, 3)),
+            shell_l=np.array(self.l, dtype=np.int32),
+            shell_nprim=np.array(self.k, dtype=np.int32),
+            shell_center=np.array(self.c, dtype=np.int32),
+            shell_prim=np.array(self.p, dtype=np.int32),
+            exps=np.concatenate(self.exps) if self.exps else np.zeros(0),
+            coefs=np.concatenate(self.coefs) if self.coefs else np.zeros(0),
+            meta=dict(meta),
+        )
+        b.validate()
+        return b
+
+
+def log_uniform(rng: np.random.Generator, lo: float, hi: float, n: int) -> np.ndarray:
+    return np.exp(rng.uniform(math.log(lo), math.log(hi), size=n))
+
+
+def all_unique_quartets(nshell: int) -> np.ndarray:
+    """Every shell quartet (ab|cd) with a >= b, c >= d and pair(ab) >= pair(cd):
+    one representative per 8-fold permutation orbit."""
+    pairs = [(a, b) for a in range(nshell) for b in range(a + 1)]
+    out = [(p[0], p[1], q[0], q[1]) for i, p in enumerate(pairs) for q in pairs[: i + 1]]
+    return np.array(out, dtype=np.int32).reshape(-1, 4)
+
+
+# ---------------------------------------------------------------------------
+# Workload: tiny plain FP64 set (3 atoms, s s p shells, K = 3)
+# ---------------------------------------------------------------------------
+def tiny_set(seed: int = 1, natom: int = 3, box_angstrom: float = 3.0, nprim: int = 3):
+    """3 atoms uniform in a 3 Angstrom cube; each atom carries two s shells and
+    one p shell of 3 primitives, exponents log-uniform in [0.1, 100], raw
+    coefficients uniform in [0.1, 1].  Returns (basis, all unique quartets)."""
+    rng = np.random.default_rng(seed)
+    bb = _BasisBuilder()
+    for _ in range(natom):
+        c = bb.add_center(rng.uniform(0.0, box_angstrom, size=3) * ANGSTROM_TO_BOHR)
+        for l in (0, 0, 1):
+            bb.add_shell(l, c, log_uniform(rng, 0.1, 100.0, nprim), rng.uniform(0.1, 1.0, size=nprim))
+    basis = bb.build(workload="tiny", seed=seed)
+    return basis, all_unique_quartets(basis.nshell)
+
+
+# ---------------------------------------------------------------------------
+# Workload: per-class sweep (independent random quartets of one class)
+# ---------------------------------------------------------------------------
+def class_sweep(ls, nquartet: int, kset=(1,), seed: int = 2000, box_angstrom: float = 10.0,
+                exp_range=(0.05, 500.0), coef_range=(0.1, 1.0)):
+    """``nquartet`` independent shell quartets of class ``ls = (la, lb, lc, ld)``.
+
+    Each quartet has four fresh centres uniform in a 10 Angstrom cube and four
+    fresh shells; each shell's contraction depth K is drawn uniformly from
+    ``kset`` (a single value gives a fixed-K run), exponents log-uniform in
+    [0.05, 500], coefficients uniform in [0.1, 1].  Quartet q uses shells
+    4q..4q+3 in (a, b, c, d) order."""
+    rng = np.random.default_rng(seed)
+    ls = tuple(int(x) for x in ls)
+    kset = np.asarray(kset, dtype=np.int64)
+    n = int(nquartet)
+    centers = rng.uniform(0.0, box_angstrom, size=(4 * n, 3)) * ANGSTROM_TO_BOHR
+    kk = kset[rng.integers(0, kset.size, size=4 * n)] if kset.size > 1 else np.full(4 * n, kset[0])
+    prim = np.zeros(4 * n, dtype=np.int64)
+    prim[1:] = np.cumsum(kk)[:-1]
+    ntot = int(kk.sum())
+    exps = log_uniform(rng, exp_range[0], exp_range[1], ntot)
+    coefs = rng.uniform(coef_range[0], coef_range[1], size=ntot)
+    basis = Basis(
+        centers=np.ascontiguousarray(centers),
+        shell_l=np.tile(np.array(ls, dtype=np.int32), n),
+        shell_nprim=kk.astype(np.int32),
+        shell_center=np.arange(4 * n, dtype=np.int32),
+        shell_prim=prim.astype(np.int32),
+        exps=exps,
+        coefs=coefs,
+        meta=dict(workload="class_sweep", ls=ls, kset=tuple(int(k) for k in kset), seed=seed),
+    )
+    basis.validate()
+    quartets = np.arange(4 * n, dtype=np.int32).reshape(n, 4)
+    return basis, quartets
+
+
+def mixed_class_set(classes, nquartet_each: int, kset=(1,), seed: int = 7):
+    """Concatenation of several per-class sweeps (one basis, one quartet list),
+    quartets interleaved in a seeded random order so that a batch mixes classes."""
+    parts = [class_sweep(ls, nquartet_each, kset=kset, seed=seed + 17 * i) for i, ls in enumerate(classes)]
+    return concat_sets(parts, shuffle_seed=seed)
+
+
+def concat_sets(parts, shuffle_seed=None):
+    bb_centers, bl, bk, bc, bp, be, bco, qs = [], [], [], [], [], [], [], []
+    coff = soff = poff = 0
+    for basis, q in parts:
+        bb_centers.append(basis.centers)
+        bl.append(basis.shell_l)
+        bk.append(basis.shell_nprim)
+        bc.append(basis.shell_center + coff)
+        bp.append(basis.shell_prim + poff)
+        be.append(basis.exps)
+        bco.append(basis.coefs)
+        qs.append(q + soff)
+        coff += basis.centers.shape[0]
+        soff += basis.nshell
+        poff += basis.exps.shape[0]
+    basis = Basis(
+        centers=np.ascontiguousarray(np.concatenate(bb_centers)),
+        shell_l=np.concatenate(bl).astype(np.int32),
+        shell_nprim=np.concatenate(bk).astype(np.int32),
+        shell_center=np.concatenate(bc).astype(np.int32),
+        shell_prim=np.concatenate(bp).astype(np.int32),
+        exps=np.concatenate(be),
+        coefs=np.concatenate(bco),
+        meta=dict(workload="concat"),
+    )
+    quartets = np.ascontiguousarray(np.concatenate(qs).astype(np.int32))
+    if shuffle_seed is not None:
+        perm = np.random.default_rng(shuffle_seed).permutation(quartets.shape[0])
+        quartets = np.ascontiguousarray(quartets[perm])
+    basis.validate()
+    return basis, quartets
+
+
+def random_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniform random rotation matrix from a uniform unit quaternion."""
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def with_centers(basis: Basis, centers: np.ndarray) -> Basis:
+    b = Basis(np.ascontiguousarray(centers, dtype=np.float64), basis.shell_l, basis.shell_nprim,
+              basis.shell_center, basis.shell_prim, basis.exps, basis.coefs, dict(basis.meta))
+    b.validate()
+    return b
