@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the contracted-ERI path on GB300.
+
+Workload: the per-class FP64 sweep -- (pp|pp), (dd|dd), (ff|ff), (gg|gg),
+each a batch of random shell quartets with fresh centres uniform in a
+10 Angstrom box, exponents log-uniform in [0.05, 500], coefficients uniform
+in [0.1, 1] and the contraction depth of every shell drawn from {1, 3, 6};
+spherical output in FP64.  One step evaluates every quartet of every class
+once (one eri_compute per class plan).
+
+Prints one JSON line (rank 0).  value = quartets/s of the whole step with
+inputs resident on the device; e2e = the same through the public API with
+host buffers (plan upload, compute, copy of the results to pinned host
+memory every step).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2605_10312_gb300 import synth  # noqa: E402
+
+METRIC = "contracted ERI shell-quartets/s (per-class FP64 sweep)"
+UNIT = "quartets/s"
+# (class, quartets per step): sized so that one step is about a second
+SWEEP = [((1, 1, 1, 1), 400_000), ((2, 2, 2, 2), 100_000), ((3, 3, 3, 3), 10_000), ((4, 4, 4, 4), 1_000)]
+KSET = (1, 3, 6)
+SEED = 2000
+# FP64 fused multiply-add lanes per SM per clock, measured on GB300 with the
+# fp_peak microbenchmark (independent FMA chains on every SM)
+FP64_LANES_PER_SM_CLK = 1.683
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def fp64_peak_tflops(mhz=SM_MAX_MHZ):
+    return FP64_LANES_PER_SM_CLK * 2 * SM_COUNT * mhz * 1e6 / 1e12
+
+
+def workload(rank=0):
+    parts = []
+    for ls, n in SWEEP:
+        basis, q = synth.class_sweep(ls, n, kset=KSET, seed=SEED + 10 * ls[0] + 1000 * rank)
+        parts.append((ls, basis, q))
+    return parts
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.gpu = gpu_index
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (also the --impl reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rates(parts, budget_s=15.0, nthreads=None):
+    """Oracle quartets/s per class on a bounded sample of each class's
+    quartets (same geometry and contraction mix), all host cores."""
+    import oracle
+    oracle.build()
+    nthreads = nthreads or os.cpu_count() or 1
+    rates, samples = {}, {}
+    per_class = budget_s / len(parts)
+    for ls, basis, q in parts:
+        n, done, t_used = 16, 0, 0.0
+        while t_used < per_class and done < q.shape[0]:
+            sel = q[done:done + n]
+            t0 = time.perf_counter()
+            oracle.eri(basis, sel, nthreads=nthreads)
+            t_used += time.perf_counter() - t0
+            done += sel.shape[0]
+            n = max(16, int(n * 2))
+        rates[ls] = done / t_used
+        samples[ls] = done
+    return rates, samples, nthreads
+
+
+def mix_rate(rates):
+    """Quartets/s of the whole step's class mix given per-class rates."""
+    tot = sum(n for _, n in SWEEP)
+    t = sum(n / rates[ls] for ls, n in SWEEP)
+    return tot / t
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    parts = workload()
+    times = []
+    per_step = max(2.0, 30.0 / max(1, args.steps + args.warmup))
+    rates = None
+    for s in range(args.warmup + args.steps):
+        r, samples, cores = oracle_rates(parts, budget_s=per_step)
+        if s >= args.warmup:
+            times.append(mix_rate(r))
+            rates = (r, samples, cores)
+    value = statistics.median(times)
+    r, samples, cores = rates
+    tot = sum(n for _, n in SWEEP)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(),
+        "per_class": {"".join("spdfg"[x] for x in ls): {"quartets_per_s": r[ls], "sample": samples[ls]}
+                      for ls in r},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "per step, a bounded prefix of each class's quartets ({} s of CPU work)".format(
+                             round(per_step, 1))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict():
+    return {"workload": "per-class FP64 sweep: " + ", ".join(
+        "({0}{0}|{0}{0}) x {1}".format("spdfg"[ls[0]], n) for ls, n in SWEEP),
+        "K_per_shell": list(KSET), "box_angstrom": 10.0, "exponents": [0.05, 500.0], "output": "spherical",
+        "quartets_per_step": sum(n for _, n in SWEEP), "l2": "flushed between steps (512 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_2605_10312_gb300 import eri
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.distributed.is_nccl_available() else "gloo")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    parts = workload(rank)
+    plans, outs = [], []
+    for ls, basis, q in parts:
+        p = eri.Plan(basis, q)
+        p.set_timing(True)
+        plans.append((ls, p))
+        outs.append(torch.empty(p.output_count, dtype=torch.float64, device=dev))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        for (ls, p), o in zip(plans, outs):
+            p.compute(o, stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    step_ms, launch_ms = [], {}
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush, outside the timed region
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for ls, p in plans:
+            for i, rec in enumerate(p.launches()):
+                key = (ls, i)
+                launch_ms.setdefault(key, []).append((rec, rec["ms"]))
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    quartets = sum(n for _, n in SWEEP)
+    value = quartets * world * args.steps / (total_ms * 1e-3)
+
+    # dominant kernel: the launch with the largest time share
+    dom_key = max(launch_ms, key=lambda k: sum(ms for _, ms in launch_ms[k]))
+    recs = launch_ms[dom_key]
+    dom_rec = recs[0][0]
+    dom_ms = statistics.mean(ms for _, ms in recs)
+    achieved = dom_rec["flops"] / (dom_ms * 1e-3) / 1e12
+    peak = fp64_peak_tflops()
+    per_class = {}
+    for ls, p in plans:
+        ms = [statistics.mean(m for _, m in launch_ms[(ls, i)]) for i in range(len(p.launches()))]
+        fl = sum(r["flops"] for r in p.launches())
+        n = p.nq
+        per_class["".join("spdfg"[x] for x in ls)] = {
+            "quartets": n, "ms": sum(ms), "quartets_per_s": n / (sum(ms) * 1e-3),
+            "fp64_tflops": fl / (sum(ms) * 1e-3) / 1e12, "fp64_frac_of_peak": fl / (sum(ms) * 1e-3) / 1e12 / peak,
+            "tier": [eri.TIERS_INV.get(r["tier"], r["tier"]) for r in p.launches()[1:]]}
+    nlaunch = sum(len(p.launches()) for _, p in plans)
+    traffic = _traffic_for(dom_rec)
+
+    # end to end through the public API with host buffers
+    e2e_ms, h2d, d2h = [], 0, 0
+    host_outs = [torch.empty(p.output_count, dtype=torch.float64).pin_memory() for _, p in plans]
+    for it in range(args.warmup + args.steps):
+        barrier()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for (ls, basis, q), ho in zip(parts, host_outs):
+            p = eri.Plan(basis, q)
+            p.compute_host(ho, stream)
+            h2d += p.stats()["h2d_bytes"]
+            d2h += ho.numel() * 8
+            stream.synchronize()
+            p.close()
+        barrier()
+        if it >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = quartets * world * args.steps / (e2e_total * 1e-3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rates, samples, cores = oracle_rates(parts, budget_s=args.cpu_seconds)
+        cpu = {"value": mix_rate(rates), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "prefix of each class's quartets: " + ", ".join(
+                   "{} {}".format("".join("spdfg"[x] for x in ls), samples[ls]) for ls in samples) +
+               " ({:.0f} s of CPU work)".format(args.cpu_seconds),
+               "per_class": {"".join("spdfg"[x] for x in ls): rates[ls] for ls in rates}}
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(),
+        "per_class": per_class,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "{} tier {} ({} quartets)".format(
+                         "".join("spdfg"[x] for x in dom_rec["cls"]) if dom_rec["cls"][0] >= 0 else "pair set-up",
+                         eri.TIERS_INV.get(dom_rec["tier"], dom_rec["tier"]), dom_rec["quartets"]),
+                     "peak_basis": "FP64 FMA issue rate measured by fp_peak ({} lanes/SM/clk) x 2 x 152 SMs x "
+                                   "2070 MHz".format(FP64_LANES_PER_SM_CLK)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": nlaunch * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _traffic_for(rec):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    summary, when it was taken on the current kernel source; else null."""
+    path = os.path.join(ROOT, "profiles", "dominant_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("eri_exec.cu", "eri_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2605_10312_gb300", "csrc", f), "rb").read())
+    key = "".join("spdfg"[x] for x in rec["cls"]) if rec["cls"][0] >= 0 else "setup"
+    ent = d.get(key)
+    if not ent or ent.get("source_sha256") != h.hexdigest():
+        return None
+    return ent["bytes_per_quartet"] * rec["quartets"]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,137 @@
+/*
+ * eri.h -- C ABI of the GB300 contracted-ERI engine.
+ *
+ * The library evaluates contracted Gaussian electron repulsion integrals
+ * (ab|cd) (FusionRCG paper, Sec. II-A, Eq. 1) by the Head-Gordon-Pople
+ * scheme: Boys function and Obara-Saika vertical recurrence per primitive
+ * quartet (Eq. 2), contraction, horizontal recurrence (Eq. 3) with the
+ * Cartesian-to-spherical transform fused stepwise (Eqs. 8, 16).  All
+ * arithmetic is FP64 and runs in CUDA kernels for sm_103a.
+ *
+ * Conventions (bohr, Hartree atomic units):
+ *  - a primitive x^i y^j z^k exp(-a r^2) of shell angular momentum l carries
+ *    N(a, l) = (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2l-1)!!); contraction
+ *    coefficients are used as given (no renormalisation);
+ *  - Cartesian components in x-descending, then y-descending order
+ *    (xx, xy, xz, yy, yz, zz);
+ *  - spherical components: real solid harmonics, Racah normalised, no
+ *    Condon-Shortley phase, m = -l..l (so p is ordered y, z, x);
+ *  - the block of quartet (s0 s1 | s2 s3) is row-major over the components
+ *    of s0, s1, s2, s3 in that order; blocks follow the quartet list.
+ *
+ * Errors: every call returns ERI_OK (0) or a negative ERI_E* code;
+ * eri_last_error() gives a message for the calling thread's last failure.
+ * Plans are not thread-safe: one thread at a time may use a plan, and one
+ * eri_compute per plan may be in flight (the plan's device buffers are
+ * reused by the next call).
+ */
+#ifndef ERI_H
+#define ERI_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ERI_OK = 0,
+  ERI_EINVAL = -1,        /* bad argument: l, K, index, non-positive or non-finite exponent */
+  ERI_EUNSUPPORTED = -2,  /* l > 4, or a tier/option combination that is not built */
+  ERI_ENOMEM = -3,        /* device or host allocation failed */
+  ERI_ECUDA = -4,         /* a CUDA call failed (message in eri_last_error) */
+  ERI_EBUSY = -5,         /* reserved: plan in use */
+  ERI_ETIMEOUT = -6,      /* reserved: bounded device wait expired */
+  ERI_ESTATE = -7         /* library files missing or inconsistent */
+};
+
+/* One contracted shell: angular momentum l (0..4), contraction depth nprim
+ * (1..ERI_MAX_NPRIM), index of its centre, offset of its first primitive in
+ * the exponent/coefficient arrays. */
+typedef struct {
+  int32_t l;
+  int32_t nprim;
+  int32_t center;
+  int32_t prim_offset;
+} eri_shell;
+
+#define ERI_MAX_L 4
+#define ERI_MAX_NPRIM 32
+
+/* Basis data, host memory, read during eri_plan only (copied). */
+typedef struct {
+  const double* centers;    /* [ncenter][3], bohr */
+  int32_t ncenter;
+  const double* exponents;  /* [nprim_total], > 0 */
+  const double* coefs;      /* [nprim_total], raw contraction coefficients */
+  int32_t nprim_total;
+} eri_basis;
+
+/* Plan options; pass NULL for the defaults (all zero). */
+typedef struct {
+  int32_t axis_rule;    /* 0 consumer-first z->y->x (Sec. III-A), 1 Algorithm 1 as printed, 2 bra-first x->y->z */
+  int32_t schedule;     /* 0 DSA (Eq. 7), 1 level order (no DSA) */
+  int32_t sph_mode;     /* 0 stepwise fusion (Eq. 16), 1 materialize-then-transform (Eq. 17), 2 Cartesian output */
+  int32_t tier;         /* 0 auto, 1 register (compiled), 2 shared-memory program, 3 global-scratch program */
+  int32_t orientation;  /* 0 tighter shell of each pair on the recurrence centre, 1 higher l first */
+  int32_t reserved[3];
+} eri_opts;
+
+typedef struct eri_plan_s eri_plan_t;
+
+/* Build a plan for nq shell quartets (quartets = [nq][4] shell indices, any
+ * order, host memory).  Validates every input, canonicalises each quartet to
+ * its class and orientation, uploads basis, pair list and quartet records to
+ * the current CUDA device and sizes the scratch.  Host inputs are copied;
+ * the plan owns its device memory.  nq may be 0.  Synchronous. */
+int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
+             int64_t nq, const eri_opts* opts, eri_plan_t** plan_out);
+
+/* Total number of doubles eri_compute writes (sum of block sizes). */
+int64_t eri_output_count(const eri_plan_t* plan);
+
+/* offsets[q] = first element of quartet q's block, offsets[nq] = total;
+ * offsets is a host array of nq + 1 int64. */
+int eri_output_offsets(const eri_plan_t* plan, int64_t* offsets);
+
+/* Evaluate every quartet of the plan into out (device memory, at least
+ * eri_output_count doubles, 8-byte aligned), asynchronously on stream
+ * (a cudaStream_t; NULL = the legacy default stream).  Kernel launch errors
+ * are returned; the caller synchronises the stream to observe completion. */
+int eri_compute(eri_plan_t* plan, double* out, void* stream);
+
+/* eri_compute into a plan-owned device buffer followed by an asynchronous
+ * copy to host_out (host memory, pinned for a truly asynchronous copy, at
+ * least eri_output_count doubles) on the same stream. */
+int eri_compute_host(eri_plan_t* plan, double* host_out, void* stream);
+
+/* Per-plan statistics, host memory: stats[0] = number of class launches,
+ * stats[1] = algorithmic FP64 flops of one eri_compute (FMA = 2),
+ * stats[2] = scratch bytes, stats[3] = quartets, stats[4] = primitive
+ * quartets, stats[5] = bytes eri_plan copied host-to-device.
+ * n = entries wanted (<= 6). */
+int eri_plan_stats(const eri_plan_t* plan, double* stats, int n);
+
+/* Launch timing: when enabled, eri_compute records a CUDA event pair on its
+ * stream around each of its launches (launch 0 = pair set-up, then one per
+ * class bucket). */
+int eri_plan_set_timing(eri_plan_t* plan, int enable);
+
+/* Number of kernel launches one eri_compute makes (0 for an empty plan). */
+int eri_plan_launch_count(const eri_plan_t* plan);
+
+/* Launch i of the last eri_compute: info[8] = {la, lb, lc, ld, tier, grid,
+ * block, quartets} (-1 for the pair set-up), *flops = its algorithmic FP64
+ * flops, *ms = its duration from the event pair (-1 when timing is off);
+ * the stream must have completed.  Any output pointer may be NULL. */
+int eri_plan_launch_info(const eri_plan_t* plan, int i, int32_t* info, double* flops, float* ms);
+
+/* Release the plan and its device memory (synchronises the device first). */
+int eri_plan_destroy(eri_plan_t* plan);
+
+/* Message for the calling thread's last error ("" if none). */
+const char* eri_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ERI_H */

@@ -1,0 +1,214 @@
+"""Build of the CUDA library: run the generator, compile for sm_103a, link.
+
+Steps (FusionRCG Sec. IV, stages 8-9):
+  1. class programs for every class (default options) -> eri_programs.bin,
+     together with the Boys Taylor table and the transform coefficients;
+  2. straight-line register-tier kernels for the classes whose program is
+     small enough to compile quickly, one translation unit per class, and
+     the registry that lists them;
+  3. nvcc -gencode arch=compute_103a,code=sm_103a for every unit, in
+     parallel, then one shared library liberi.so.
+Everything lands in paper_2605_10312_gb300/_build/.  Units whose source did
+not change are not recompiled.
+"""
+from __future__ import annotations
+
+import hashlib
+import math
+import multiprocessing as mp
+import os
+import shutil
+import struct
+import subprocess
+import sys
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+ROOT = os.path.dirname(HERE)
+BUILD = os.path.join(HERE, "_build")
+GEN_DIR = os.path.join(BUILD, "gen")
+LIB = os.path.join(BUILD, "liberi.so")
+NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + CSRC, "-I" + os.path.join(ROOT, "include")]
+# straight-line size (VRR terms + 1.5 x Phase-2 operations) up to which a
+# class gets a compiled register-tier kernel; larger classes run as programs
+REG_TIER_MAX = 3000
+
+AXIS = {"prose": 0, "literal": 1, "common": 2}
+SCHED = {"dsa": 0, "level": 1}
+SPH = {"stepwise": 0, "materialize": 1, "cart": 2}
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if c and os.path.exists(c):
+            return c
+    raise RuntimeError("nvcc not found")
+
+
+def boys_table(ngrid=362, ncol=24, step=0.1, dps=32):
+    """F_n(T_k), n < ncol, T_k = k step: F_n(T) = 1F1(n+1/2; n+3/2; -T)/(2n+1)
+    evaluated in high precision (mpmath)."""
+    import mpmath
+    mpmath.mp.dps = dps
+    out = np.zeros((ngrid, ncol))
+    for k in range(ngrid):
+        T = mpmath.mpf(k) * mpmath.mpf(step)
+        for n in range(ncol):
+            v = mpmath.hyp1f1(n + mpmath.mpf(1) / 2, n + mpmath.mpf(3) / 2, -T) / (2 * n + 1)
+            out[k, n] = float(v)
+    return out
+
+
+def _class_job(args):
+    ls, opts, want_reg = args
+    sys.setrecursionlimit(100000)
+    from paper_2605_10312_gb300.gen import emit_cuda, encode, program
+    prog = program.make(*ls, *opts)
+    enc = encode.encode(prog)
+    c = prog.counts()
+    rec = dict(ls=ls, opts=opts, nh=enc.nh, nslot=enc.nslot, L=enc.L, n1=int(enc.ph1.shape[0]),
+               n2=int(enc.ph2.shape[0]), kmax=enc.kmax, dims=enc.out_dims, flops_prim=float(c["per_prim_flops"]),
+               flops_p2=float(c["p2_flops"]), ph1=enc.ph1.tobytes(), ph2=enc.ph2.tobytes(),
+               size=c["vrr_instr"] + 1.5 * c["p2_instr"], counts=c)
+    if want_reg and rec["size"] <= REG_TIER_MAX:
+        rec["cuda"] = emit_cuda.emit_class(prog, "reg")
+        rec["kname"] = emit_cuda.kernel_name(ls, "reg")
+    return rec
+
+
+def generate(classes, opts=("prose", "dsa", "stepwise"), want_reg=True, jobs=None, log=print):
+    t0 = time.time()
+    jobs = jobs or max(1, os.cpu_count() or 1)
+    work = [(tuple(ls), tuple(opts), want_reg) for ls in classes]
+    # heaviest first so the pool ends evenly
+    work.sort(key=lambda w: -sum(w[0]) * 100 - w[0][0])
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(jobs) as pool:
+        recs = pool.map(_class_job, work, chunksize=1)
+    log("generated {} class programs in {:.1f}s".format(len(recs), time.time() - t0))
+    return recs
+
+
+def write_blob(path, recs, boys, c2s):
+    with open(path + ".tmp", "wb") as f:
+        f.write(b"ERIPRG01")
+        f.write(struct.pack("<I", boys.size))
+        f.write(np.ascontiguousarray(boys, dtype="<f8").tobytes())
+        f.write(struct.pack("<I", len(c2s)))
+        f.write(np.asarray(c2s, dtype="<f8").tobytes())
+        f.write(struct.pack("<I", len(recs)))
+        for r in recs:
+            o = r["opts"]
+            f.write(struct.pack("<8b", *r["ls"], AXIS[o[0]], SCHED[o[1]], SPH[o[2]], 1 if "cuda" in r else 0))
+            f.write(struct.pack("<10i", r["nh"], r["nslot"], r["L"], r["n1"], r["n2"], r["kmax"], *r["dims"]))
+            f.write(struct.pack("<2d", r["flops_prim"], r["flops_p2"]))
+            f.write(r["ph1"])
+            f.write(r["ph2"])
+    os.replace(path + ".tmp", path)
+
+
+def _registry(recs):
+    lines = ['#include "eri_common.cuh"', "struct EriRegEntry { int8_t ls[4]; const void* fn; };"]
+    regs = [r for r in recs if "cuda" in r]
+    for r in regs:
+        lines.append('extern "C" __global__ void {}(const EriLaunchArgs a);'.format(r["kname"]))
+    lines.append('extern "C" const EriRegEntry eri_reg_table[] = {')
+    for r in regs:
+        lines.append("  {{{{{}, {}, {}, {}}}, (const void*){}}},".format(*r["ls"], r["kname"]))
+    lines.append("  {{0, 0, 0, 0}, nullptr}};")
+    lines.append('extern "C" const int eri_reg_count = {};'.format(len(regs)))
+    return "\n".join(lines) + "\n"
+
+
+def _write_if_changed(path, text):
+    if os.path.exists(path) and open(path).read() == text:
+        return
+    with open(path, "w") as f:
+        f.write(text)
+
+
+def _compile(src, obj, extra=()):
+    key = hashlib.sha256()
+    for p in [src, os.path.join(CSRC, "eri_common.cuh"), os.path.join(ROOT, "include", "eri.h")]:
+        key.update(open(p, "rb").read())
+    key.update(" ".join(NVCC_ARCH + NVCC_FLAGS + list(extra)).encode())
+    stamp = obj + ".key"
+    h = key.hexdigest()
+    if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == h:
+        return 0.0
+    t = time.time()
+    cmd = [_nvcc()] + NVCC_ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for {}:\n{}".format(src, r.stderr[-4000:]))
+    open(stamp, "w").write(h)
+    return time.time() - t
+
+
+def build(force=False, jobs=None, log=print):
+    """Generate, compile and link liberi.so (and the fp_peak tool)."""
+    from paper_2605_10312_gb300.gen import encode, program
+    os.makedirs(GEN_DIR, exist_ok=True)
+    jobs = jobs or max(1, os.cpu_count() or 1)
+    t0 = time.time()
+    gen_key = hashlib.sha256()
+    for fn in sorted(os.listdir(os.path.join(HERE, "gen"))):
+        if fn.endswith(".py"):
+            gen_key.update(open(os.path.join(HERE, "gen", fn), "rb").read())
+    gen_key.update(open(__file__, "rb").read())
+    gen_key = gen_key.hexdigest()
+    blob = os.path.join(BUILD, "eri_programs.bin")
+    stamp = os.path.join(BUILD, "gen.key")
+    if force or not (os.path.exists(blob) and os.path.exists(stamp) and open(stamp).read() == gen_key):
+        recs = generate(program.all_classes(), jobs=jobs, log=log)
+        boys = boys_table()
+        write_blob(blob, recs, boys, encode.coef_table())
+        for r in recs:
+            if "cuda" in r:
+                _write_if_changed(os.path.join(GEN_DIR, r["kname"] + ".cu"), r["cuda"])
+        _write_if_changed(os.path.join(GEN_DIR, "eri_registry.cu"), _registry(recs))
+        # class table for the docs and the benchmark: per-class counts
+        with open(os.path.join(BUILD, "classes.tsv"), "w") as f:
+            f.write("la\tlb\tlc\tld\ttier\tvrr_nodes\tpeak_live\tnslot\tnh\tnout\tper_prim_flops\tp2_flops\n")
+            for r in sorted(recs, key=lambda r: r["ls"]):
+                c = r["counts"]
+                f.write("\t".join(str(x) for x in (*r["ls"], "reg" if "cuda" in r else "prog", c["vrr_nodes"],
+                                                   c["peak_live"], r["nslot"], c["nh"], c["nout"],
+                                                   c["per_prim_flops"], c["p2_flops"])) + "\n")
+        open(stamp, "w").write(gen_key)
+    units = [os.path.join(CSRC, "eri_runtime.cu"), os.path.join(CSRC, "eri_exec.cu"),
+             os.path.join(GEN_DIR, "eri_registry.cu")]
+    units += sorted(os.path.join(GEN_DIR, f) for f in os.listdir(GEN_DIR)
+                    if f.endswith("_reg.cu"))
+    objs = [os.path.join(BUILD, os.path.basename(u)[:-3] + ".o") for u in units]
+    # drop objects of classes no longer generated
+    keep = set(objs)
+    for f in os.listdir(BUILD):
+        p = os.path.join(BUILD, f)
+        if f.endswith("_reg.o") and p not in keep:
+            os.remove(p)
+    t1 = time.time()
+    with ThreadPoolExecutor(jobs) as ex:
+        times = list(ex.map(lambda so: _compile(*so), zip(units, objs)))
+    log("compiled {} units ({} rebuilt) in {:.1f}s".format(len(units), sum(1 for t in times if t > 0),
+                                                          time.time() - t1))
+    cmd = [_nvcc()] + NVCC_ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-ldl"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed:\n" + r.stderr[-4000:])
+    os.replace(LIB + ".tmp", LIB)
+    peak_src = os.path.join(CSRC, "fp_peak.cu")
+    peak_bin = os.path.join(BUILD, "fp_peak")
+    if not os.path.exists(peak_bin) or os.path.getmtime(peak_bin) < os.path.getmtime(peak_src):
+        subprocess.run([_nvcc()] + NVCC_ARCH + ["-O3", "-o", peak_bin, peak_src], check=True)
+    log("built {} in {:.1f}s".format(LIB, time.time() - t0))
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv)

@@ -1,0 +1,711 @@
+// Runtime behind the C ABI of include/eri.h: plan construction (validation,
+// per-quartet canonicalisation and orientation, shell-pair deduplication,
+// class bucketing, tier routing, device upload) and eri_compute (the pair
+// set-up kernel followed by one launch per class bucket).
+//
+// Class programs and the Boys table come from the generator's blob
+// (eri_programs*.bin next to this library); register-tier kernels are linked
+// in through the generated registry.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "eri.h"
+#include "eri_common.cuh"
+
+// ---------------------------------------------------------------------------
+// executor and registry (other translation units)
+// ---------------------------------------------------------------------------
+extern "C" cudaError_t eri_exec_launch(int shared, const EriLaunchArgs* a, const EriProgArgs* p, int grid,
+                                       int block, size_t smem, cudaStream_t stream);
+extern "C" cudaError_t eri_exec_set_smem(size_t bytes);
+
+struct EriRegEntry {
+  int8_t ls[4];
+  const void* fn;
+};
+extern "C" const EriRegEntry eri_reg_table[];
+extern "C" const int eri_reg_count;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_OR(expr, what)                                                               \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess) return fail(ERI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" const char* eri_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// program blob
+// ---------------------------------------------------------------------------
+namespace {
+
+struct ClassProg {
+  int ls[4];
+  int opts[3];  // axis rule, schedule, sph mode
+  int nh, nslot, L, n1, n2, kmax;
+  int dims[4];
+  double flops_prim, flops_p2;
+  std::vector<uint32_t> ph1, ph2;
+  // device copies (lazily uploaded)
+  uint4* d_ph1 = nullptr;
+  uint4* d_ph2 = nullptr;
+};
+
+struct Library {
+  bool loaded = false;
+  std::string err;
+  std::vector<double> boys, c2s;
+  std::map<std::vector<int>, std::unique_ptr<ClassProg>> progs;  // key: ls[4] + opts[3]
+  std::map<std::vector<int>, const void*> reg;                      // key: ls[4]
+  double* d_boys = nullptr;
+  double* d_c2s = nullptr;
+  int device = -1;
+  int nsm = 0;
+  size_t smem_optin = 0;
+  std::mutex mu;
+};
+
+Library& lib() {
+  static Library L;
+  return L;
+}
+
+std::string lib_dir() {
+  Dl_info info;
+  if (dladdr((void*)&eri_last_error, &info) && info.dli_fname) {
+    std::string p(info.dli_fname);
+    size_t k = p.rfind('/');
+    return k == std::string::npos ? std::string(".") : p.substr(0, k);
+  }
+  return ".";
+}
+
+template <typename T>
+bool rd(FILE* f, T* v, size_t n = 1) {
+  return fread(v, sizeof(T), n, f) == n;
+}
+
+bool load_blob(Library& L, const std::string& path, bool tables) {
+  FILE* f = fopen(path.c_str(), "rb");
+  if (!f) return false;
+  char magic[8];
+  uint32_t nb = 0, nc = 0, ncls = 0;
+  bool ok = rd(f, magic, 8) && memcmp(magic, "ERIPRG01", 8) == 0 && rd(f, &nb);
+  std::vector<double> boys(nb);
+  ok = ok && rd(f, boys.data(), nb) && rd(f, &nc);
+  std::vector<double> c2s(nc);
+  ok = ok && rd(f, c2s.data(), nc) && rd(f, &ncls);
+  for (uint32_t c = 0; ok && c < ncls; ++c) {
+    auto p = std::make_unique<ClassProg>();
+    int8_t hdr[8];
+    int32_t iv[10];
+    double fv[2];
+    ok = rd(f, hdr, 8) && rd(f, iv, 10) && rd(f, fv, 2);
+    if (!ok) break;
+    for (int k = 0; k < 4; ++k) p->ls[k] = hdr[k];
+    for (int k = 0; k < 3; ++k) p->opts[k] = hdr[4 + k];
+    p->nh = iv[0];
+    p->nslot = iv[1];
+    p->L = iv[2];
+    p->n1 = iv[3];
+    p->n2 = iv[4];
+    p->kmax = iv[5];
+    for (int k = 0; k < 4; ++k) p->dims[k] = iv[6 + k];
+    p->flops_prim = fv[0];
+    p->flops_p2 = fv[1];
+    p->ph1.resize((size_t)p->n1 * 4);
+    p->ph2.resize((size_t)p->n2 * 4);
+    ok = rd(f, p->ph1.data(), p->ph1.size()) && rd(f, p->ph2.data(), p->ph2.size());
+    if (!ok) break;
+    std::vector<int> key = {p->ls[0], p->ls[1], p->ls[2], p->ls[3], p->opts[0], p->opts[1], p->opts[2]};
+    L.progs[key] = std::move(p);
+  }
+  fclose(f);
+  if (ok && tables) {
+    L.boys = boys;
+    L.c2s = c2s;
+  }
+  return ok;
+}
+
+int ensure_library() {
+  Library& L = lib();
+  std::lock_guard<std::mutex> g(L.mu);
+  int dev = 0;
+  CUDA_OR(cudaGetDevice(&dev), "cudaGetDevice");
+  if (!L.loaded) {
+    std::string dir = lib_dir();
+    if (!load_blob(L, dir + "/eri_programs.bin", true))
+      return fail(ERI_ESTATE, "cannot read " + dir + "/eri_programs.bin (run the build)");
+    for (const char* extra : {"/eri_programs_ablation.bin"}) load_blob(L, dir + extra, false);
+    for (int i = 0; i < eri_reg_count; ++i) {
+      const EriRegEntry& e = eri_reg_table[i];
+      L.reg[{e.ls[0], e.ls[1], e.ls[2], e.ls[3]}] = e.fn;
+    }
+    L.loaded = true;
+  }
+  if (L.device != dev) {
+    if (L.device >= 0) return fail(ERI_EUNSUPPORTED, "the library serves one CUDA device per process");
+    CUDA_OR(cudaMalloc(&L.d_boys, L.boys.size() * sizeof(double)), "cudaMalloc boys table");
+    CUDA_OR(cudaMemcpy(L.d_boys, L.boys.data(), L.boys.size() * sizeof(double), cudaMemcpyHostToDevice),
+            "upload boys table");
+    CUDA_OR(cudaMalloc(&L.d_c2s, std::max<size_t>(1, L.c2s.size()) * sizeof(double)), "cudaMalloc c2s");
+    CUDA_OR(cudaMemcpy(L.d_c2s, L.c2s.data(), L.c2s.size() * sizeof(double), cudaMemcpyHostToDevice),
+            "upload c2s");
+    cudaDeviceProp prop;
+    CUDA_OR(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+    L.nsm = prop.multiProcessorCount;
+    L.smem_optin = prop.sharedMemPerBlockOptin;
+    CUDA_OR(eri_exec_set_smem(L.smem_optin), "cudaFuncSetAttribute");
+    L.device = dev;
+  }
+  return ERI_OK;
+}
+
+int upload_prog(ClassProg* p) {
+  Library& L = lib();
+  std::lock_guard<std::mutex> g(L.mu);
+  if (p->d_ph1) return ERI_OK;
+  CUDA_OR(cudaMalloc(&p->d_ph1, std::max<size_t>(1, p->ph1.size()) * 4), "cudaMalloc program");
+  CUDA_OR(cudaMalloc(&p->d_ph2, std::max<size_t>(1, p->ph2.size()) * 4), "cudaMalloc program");
+  CUDA_OR(cudaMemcpy(p->d_ph1, p->ph1.data(), p->ph1.size() * 4, cudaMemcpyHostToDevice), "upload program");
+  CUDA_OR(cudaMemcpy(p->d_ph2, p->ph2.data(), p->ph2.size() * 4, cudaMemcpyHostToDevice), "upload program");
+  return ERI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// device data the pair set-up kernel consumes
+// ---------------------------------------------------------------------------
+struct DevShell {
+  double ctr[3];
+  int32_t l, nprim, prim;
+  int32_t pad;
+};
+struct DevPairIn {
+  int32_t a, b;       // oriented shells: a is the recurrence centre
+  int32_t prim_off;   // first EriPairPrim
+  int32_t pad;
+};
+
+}  // namespace
+
+// FusionRCG Algorithm 2, "GaussianPairs", once per primitive pair: zeta,
+// P, P - A, and the pair factor sqrt(2) pi^(5/4) c_a N_a c_b N_b
+// exp(-a b |A-B|^2 / zeta) / zeta, so that the primitive-quartet prefactor
+// 2 pi^(5/2) / (zeta eta sqrt(zeta+eta)) K_AB K_CD is one product.
+__global__ void eri_pair_setup_kernel(const DevPairIn* __restrict__ pin, int npair, const DevShell* __restrict__ sh,
+                                      const double* __restrict__ ex, const double* __restrict__ co,
+                                      EriPairRec* __restrict__ pairs, EriPairPrim* __restrict__ pp) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npair) return;
+  const DevPairIn in = pin[p];
+  const DevShell A = sh[in.a], B = sh[in.b];
+  const double AB0 = A.ctr[0] - B.ctr[0], AB1 = A.ctr[1] - B.ctr[1], AB2 = A.ctr[2] - B.ctr[2];
+  const double ab2 = AB0 * AB0 + AB1 * AB1 + AB2 * AB2;
+  EriPairRec r;
+  r.prim_off = in.prim_off;
+  r.nprim = A.nprim * B.nprim;
+  r.AB[0] = AB0;
+  r.AB[1] = AB1;
+  r.AB[2] = AB2;
+  pairs[p] = r;
+  const double dfi[5] = {1.0, 1.0, 1.0 / 1.7320508075688772935, 1.0 / 3.8729833462074168852,
+                         1.0 / 10.246950765959598383};  // 1/sqrt((2l-1)!!)
+  const double C0 = 5.9149671727956128778;              // sqrt(2) pi^(5/4)
+  for (int i = 0; i < A.nprim; ++i) {
+    const double a = ex[A.prim + i];
+    const double xa = a * 0.63661977236758134308;  // 2a/pi
+    double na = sqrt(xa * sqrt(xa)) * dfi[A.l];
+    const double sa = sqrt(4.0 * a);
+    for (int k = 0; k < A.l; ++k) na *= sa;
+    for (int j = 0; j < B.nprim; ++j) {
+      const double b = ex[B.prim + j];
+      const double xb = b * 0.63661977236758134308;
+      double nb = sqrt(xb * sqrt(xb)) * dfi[B.l];
+      const double sb = sqrt(4.0 * b);
+      for (int k = 0; k < B.l; ++k) nb *= sb;
+      const double z = a + b;
+      const double iz = 1.0 / z;
+      EriPairPrim q;
+      q.zeta = z;
+      q.inv2z = 0.5 * iz;
+      for (int d = 0; d < 3; ++d) {
+        q.P[d] = (a * A.ctr[d] + b * B.ctr[d]) * iz;
+        q.PA[d] = q.P[d] - A.ctr[d];
+      }
+      q.K = C0 * co[A.prim + i] * na * co[B.prim + j] * nb * exp(-a * b * iz * ab2) * iz;
+      pp[in.prim_off + i * B.nprim + j] = q;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+namespace {
+enum Tier { TIER_REG = 1, TIER_SHARED = 2, TIER_GLOBAL = 3 };
+
+struct Bucket {
+  int ls[4];
+  int tier;
+  const void* reg_fn = nullptr;
+  ClassProg* prog = nullptr;
+  int64_t first = 0, count = 0;  // range in the sorted quartet records
+  int grid = 0, block = 128;
+  size_t smem = 0;
+  int group = 1;                 // lanes per shell quartet
+  double flops = 0;              // algorithmic FP64 flops of this launch
+};
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  ~DevBuf() { reset(); }
+  void reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  int alloc(size_t count, const char* what) {
+    n = count;
+    if (count == 0) return ERI_OK;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ERI_ENOMEM, std::string("cudaMalloc failed: ") + what);
+    }
+    return ERI_OK;
+  }
+  int upload(const std::vector<T>& v, const char* what) {
+    int rc = alloc(v.size(), what);
+    if (rc) return rc;
+    if (!v.empty()) CUDA_OR(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+    return ERI_OK;
+  }
+};
+}  // namespace
+
+struct eri_plan_s {
+  int64_t nq = 0;
+  std::vector<int64_t> offsets;  // nq + 1
+  std::vector<Bucket> buckets;
+  int npair = 0;
+  int64_t npprim = 0;
+  double flops = 0, nprimq = 0;
+  DevBuf<DevShell> shells;
+  DevBuf<double> exps, coefs;
+  DevBuf<DevPairIn> pin;
+  DevBuf<EriPairRec> pairs;
+  DevBuf<EriPairPrim> pprims;
+  DevBuf<EriQuartetRec> quartets;
+  DevBuf<double> scratch;
+  DevBuf<double> outbuf;
+  int64_t scratch_stride = 0;
+  double h2d_bytes = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> events;  // two per launch: pair set-up, then buckets
+  ~eri_plan_s() {
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+  }
+};
+
+static int nfun(int l, bool cart) { return cart ? (l + 1) * (l + 2) / 2 : 2 * l + 1; }
+
+extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
+                        int64_t nq, const eri_opts* opts_in, eri_plan_t** plan_out) {
+  if (!plan_out) return fail(ERI_EINVAL, "plan_out is NULL");
+  *plan_out = nullptr;
+  eri_opts opts;
+  memset(&opts, 0, sizeof opts);
+  if (opts_in) opts = *opts_in;
+  if (opts.axis_rule < 0 || opts.axis_rule > 2 || opts.schedule < 0 || opts.schedule > 1 || opts.sph_mode < 0 ||
+      opts.sph_mode > 2 || opts.tier < 0 || opts.tier > 3 || opts.orientation < 0 || opts.orientation > 1)
+    return fail(ERI_EINVAL, "option out of range");
+  if (nq < 0 || nshell < 0 || (nq > 0 && (!shells || !basis || !quartets)))
+    return fail(ERI_EINVAL, "NULL or negative argument");
+  if (nq > (int64_t)1 << 31) return fail(ERI_EINVAL, "too many quartets for one plan");
+  const bool cart = opts.sph_mode == 2;
+  // ---- validation
+  if (nshell > 0) {
+    if (!basis->centers || !basis->exponents || !basis->coefs || basis->ncenter < 0 || basis->nprim_total < 0)
+      return fail(ERI_EINVAL, "incomplete basis");
+  }
+  std::vector<double> maxexp(nshell, 0.0);
+  for (int s = 0; s < nshell; ++s) {
+    const eri_shell& S = shells[s];
+    if (S.l < 0) return fail(ERI_EINVAL, "shell " + std::to_string(s) + ": negative l");
+    if (S.l > ERI_MAX_L) return fail(ERI_EUNSUPPORTED, "shell " + std::to_string(s) + ": l > 4");
+    if (S.nprim < 1 || S.nprim > ERI_MAX_NPRIM) return fail(ERI_EINVAL, "shell " + std::to_string(s) + ": bad nprim");
+    if (S.center < 0 || S.center >= basis->ncenter) return fail(ERI_EINVAL, "shell " + std::to_string(s) + ": bad centre");
+    if (S.prim_offset < 0 || (int64_t)S.prim_offset + S.nprim > basis->nprim_total)
+      return fail(ERI_EINVAL, "shell " + std::to_string(s) + ": primitives out of range");
+    for (int k = 0; k < S.nprim; ++k) {
+      const double a = basis->exponents[S.prim_offset + k], c = basis->coefs[S.prim_offset + k];
+      if (!(a > 0) || !std::isfinite(a) || !std::isfinite(c))
+        return fail(ERI_EINVAL, "shell " + std::to_string(s) + ": non-positive or non-finite exponent/coefficient");
+      maxexp[s] = std::max(maxexp[s], a);
+    }
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(basis->centers[3 * S.center + d])) return fail(ERI_EINVAL, "non-finite centre");
+  }
+  for (int64_t q = 0; q < 4 * nq; ++q)
+    if (quartets[q] < 0 || quartets[q] >= nshell) return fail(ERI_EINVAL, "quartet index out of range");
+  int rc = nq > 0 ? ensure_library() : ERI_OK;
+  if (rc) return rc;
+  Library& L = lib();
+
+  auto plan = std::make_unique<eri_plan_s>();
+  plan->nq = nq;
+  plan->offsets.resize(nq + 1);
+  plan->offsets[0] = 0;
+  for (int64_t q = 0; q < nq; ++q) {
+    int64_t sz = 1;
+    for (int k = 0; k < 4; ++k) sz *= nfun(shells[quartets[4 * q + k]].l, cart);
+    plan->offsets[q + 1] = plan->offsets[q] + sz;
+  }
+  if (nq == 0) {
+    *plan_out = plan.release();
+    return ERI_OK;
+  }
+  // ---- orientation and class of every quartet
+  auto first_of_pair = [&](int s0, int s1) {
+    // returns true when s0 should be the recurrence centre
+    const int l0 = shells[s0].l, l1 = shells[s1].l;
+    if (opts.orientation == 1) return l0 >= l1;
+    if (maxexp[s0] != maxexp[s1]) return maxexp[s0] > maxexp[s1];
+    return l0 >= l1;
+  };
+  std::unordered_map<uint64_t, int> pair_id;
+  std::vector<DevPairIn> pin;
+  int64_t pprim = 0;
+  auto get_pair = [&](int a, int b) {
+    uint64_t key = ((uint64_t)(uint32_t)a << 32) | (uint32_t)b;
+    auto it = pair_id.find(key);
+    if (it != pair_id.end()) return it->second;
+    int id = (int)pin.size();
+    pin.push_back({a, b, (int32_t)pprim, 0});
+    pprim += (int64_t)shells[a].nprim * shells[b].nprim;
+    pair_id.emplace(key, id);
+    return id;
+  };
+  struct QInfo {
+    int cls;  // bucket key index
+    int kb, kk;
+    EriQuartetRec rec;
+  };
+  std::vector<QInfo> qi(nq);
+  std::map<std::vector<int>, int> cls_index;
+  std::vector<std::vector<int>> cls_keys;
+  for (int64_t q = 0; q < nq; ++q) {
+    const int32_t* s = quartets + 4 * q;
+    int pos[4] = {0, 1, 2, 3};  // pos[k] = user position of canonical index k
+    if (!first_of_pair(s[0], s[1])) std::swap(pos[0], pos[1]);
+    if (!first_of_pair(s[2], s[3])) std::swap(pos[2], pos[3]);
+    int lb0 = shells[s[pos[0]]].l, lb1 = shells[s[pos[1]]].l, lk0 = shells[s[pos[2]]].l, lk1 = shells[s[pos[3]]].l;
+    // bra-ket exchange so that the bra pair rank is not below the ket's
+    if (lb0 * 5 + lb1 < lk0 * 5 + lk1) {
+      std::swap(pos[0], pos[2]);
+      std::swap(pos[1], pos[3]);
+      std::swap(lb0, lk0);
+      std::swap(lb1, lk1);
+    }
+    int n[4];
+    for (int k = 0; k < 4; ++k) n[k] = nfun(shells[s[k]].l, cart);
+    const int ustride[4] = {n[1] * n[2] * n[3], n[2] * n[3], n[3], 1};
+    QInfo& x = qi[q];
+    x.rec.bra = get_pair(s[pos[0]], s[pos[1]]);
+    x.rec.ket = get_pair(s[pos[2]], s[pos[3]]);
+    x.rec.out_off = plan->offsets[q];
+    for (int k = 0; k < 4; ++k) x.rec.st[k] = ustride[pos[k]];
+    std::vector<int> key = {lb0, lb1, lk0, lk1};
+    auto it = cls_index.find(key);
+    if (it == cls_index.end()) {
+      it = cls_index.emplace(key, (int)cls_keys.size()).first;
+      cls_keys.push_back(key);
+    }
+    x.cls = it->second;
+    x.kb = shells[s[pos[0]]].nprim * shells[s[pos[1]]].nprim;
+    x.kk = shells[s[pos[2]]].nprim * shells[s[pos[3]]].nprim;
+  }
+  if (pprim > ((int64_t)1 << 31) - 1) return fail(ERI_EINVAL, "too many primitive pairs");
+  // ---- buckets: by class (heaviest first), then by contraction signature
+  std::vector<int64_t> order(nq);
+  for (int64_t q = 0; q < nq; ++q) order[q] = q;
+  std::vector<int> cls_rank(cls_keys.size());
+  {
+    std::vector<int> idx(cls_keys.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+      int sa = 0, sb = 0;
+      for (int k = 0; k < 4; ++k) {
+        sa += cls_keys[a][k];
+        sb += cls_keys[b][k];
+      }
+      return sa != sb ? sa > sb : cls_keys[a] > cls_keys[b];
+    });
+    for (size_t r = 0; r < idx.size(); ++r) cls_rank[idx[r]] = (int)r;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    if (qi[a].cls != qi[b].cls) return cls_rank[qi[a].cls] < cls_rank[qi[b].cls];
+    const int64_t ka = (int64_t)qi[a].kb * qi[a].kk, kb = (int64_t)qi[b].kb * qi[b].kk;
+    if (ka != kb) return ka > kb;
+    return qi[a].kb > qi[b].kb;
+  });
+  std::vector<EriQuartetRec> recs(nq);
+  for (int64_t i = 0; i < nq; ++i) recs[i] = qi[order[i]].rec;
+  // ---- launches: one per (class, group size); G lanes share a quartet and
+  // split its K4 primitive quartets, about three per lane
+  auto group_of = [](int64_t k4) {
+    int64_t want = std::min<int64_t>(32, std::max<int64_t>(1, (k4 + 2) / 3));
+    int g = 1;
+    while (g * 2 <= want) g *= 2;
+    return g;
+  };
+  size_t max_scratch_slots = 0;
+  int max_grid_global = 0;
+  for (int64_t i = 0; i < nq;) {
+    const int c = qi[order[i]].cls;
+    const int g = group_of((int64_t)qi[order[i]].kb * qi[order[i]].kk);
+    int64_t j = i;
+    double kprim = 0;
+    while (j < nq && qi[order[j]].cls == c && group_of((int64_t)qi[order[j]].kb * qi[order[j]].kk) == g) {
+      kprim += (double)qi[order[j]].kb * qi[order[j]].kk;
+      ++j;
+    }
+    Bucket b;
+    for (int k = 0; k < 4; ++k) b.ls[k] = cls_keys[c][k];
+    b.first = i;
+    b.count = j - i;
+    b.group = g;
+    std::vector<int> pkey = {b.ls[0], b.ls[1], b.ls[2], b.ls[3], opts.axis_rule, opts.schedule, opts.sph_mode};
+    auto pit = L.progs.find(pkey);
+    ClassProg* prog = pit == L.progs.end() ? nullptr : pit->second.get();
+    auto rit = L.reg.find({b.ls[0], b.ls[1], b.ls[2], b.ls[3]});
+    const bool default_opts = opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0;
+    const void* regfn = (rit != L.reg.end() && default_opts) ? rit->second : nullptr;
+    const size_t smem_need = prog ? (size_t)prog->nslot * 128 * sizeof(double) : 0;
+    int tier = opts.tier;
+    if (tier == 0) tier = regfn ? TIER_REG : (prog && smem_need <= L.smem_optin ? TIER_SHARED : TIER_GLOBAL);
+    if (tier == TIER_REG && !regfn)
+      return fail(ERI_EUNSUPPORTED, "no register-tier kernel for this class/options");
+    if ((tier == TIER_SHARED || tier == TIER_GLOBAL) && !prog)
+      return fail(ERI_EUNSUPPORTED, "no program for this class/options (build the variant)");
+    if (tier == TIER_SHARED && smem_need > L.smem_optin)
+      return fail(ERI_EUNSUPPORTED, "class does not fit the shared-memory tier");
+    b.tier = tier;
+    b.reg_fn = regfn;
+    b.prog = prog;
+    const int64_t blocks = (b.count * g + 127) / 128;
+    if (tier == TIER_REG) {
+      b.grid = (int)blocks;
+    } else if (tier == TIER_SHARED) {
+      b.smem = smem_need;
+      int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (L.smem_optin + 1024) / (smem_need + 1024)));
+      b.grid = (int)std::min<int64_t>(blocks, (int64_t)L.nsm * per_sm);
+    } else {
+      int per_sm = prog->nslot <= 4096 ? 4 : 2;
+      b.grid = (int)std::min<int64_t>(blocks, (int64_t)L.nsm * per_sm);
+      max_scratch_slots = std::max(max_scratch_slots, (size_t)prog->nslot);
+      max_grid_global = std::max(max_grid_global, b.grid);
+    }
+    if (prog) {
+      if (tier != TIER_REG && (rc = upload_prog(prog))) return rc;
+      b.flops = kprim * prog->flops_prim + (double)b.count * prog->flops_p2;
+      plan->flops += b.flops;
+    }
+    plan->nprimq += kprim;
+    plan->buckets.push_back(b);
+    i = j;
+  }
+  // ---- device data
+  std::vector<DevShell> dsh(nshell);
+  for (int s = 0; s < nshell; ++s) {
+    for (int d = 0; d < 3; ++d) dsh[s].ctr[d] = basis->centers[3 * shells[s].center + d];
+    dsh[s].l = shells[s].l;
+    dsh[s].nprim = shells[s].nprim;
+    dsh[s].prim = shells[s].prim_offset;
+    dsh[s].pad = 0;
+  }
+  std::vector<double> ex(basis->exponents, basis->exponents + basis->nprim_total);
+  std::vector<double> co(basis->coefs, basis->coefs + basis->nprim_total);
+  if ((rc = plan->shells.upload(dsh, "shells")) || (rc = plan->exps.upload(ex, "exponents")) ||
+      (rc = plan->coefs.upload(co, "coefficients")) || (rc = plan->pin.upload(pin, "pair list")) ||
+      (rc = plan->pairs.alloc(pin.size(), "pairs")) || (rc = plan->pprims.alloc(pprim, "primitive pairs")) ||
+      (rc = plan->quartets.upload(recs, "quartet records")))
+    return rc;
+  plan->npair = (int)pin.size();
+  plan->npprim = pprim;
+  plan->h2d_bytes = (double)(dsh.size() * sizeof(DevShell) + 2 * ex.size() * sizeof(double) +
+                             pin.size() * sizeof(DevPairIn) + recs.size() * sizeof(EriQuartetRec));
+  if (max_scratch_slots > 0) {
+    plan->scratch_stride = (int64_t)max_grid_global * 128;
+    if ((rc = plan->scratch.alloc((size_t)plan->scratch_stride * max_scratch_slots, "scratch"))) return rc;
+  }
+  *plan_out = plan.release();
+  return ERI_OK;
+}
+
+extern "C" int64_t eri_output_count(const eri_plan_t* plan) { return plan ? plan->offsets.back() : 0; }
+
+extern "C" int eri_output_offsets(const eri_plan_t* plan, int64_t* offsets) {
+  if (!plan || !offsets) return fail(ERI_EINVAL, "NULL argument");
+  memcpy(offsets, plan->offsets.data(), plan->offsets.size() * sizeof(int64_t));
+  return ERI_OK;
+}
+
+extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
+  if (!plan) return fail(ERI_EINVAL, "NULL plan");
+  if (plan->nq == 0) return ERI_OK;
+  if (!out) return fail(ERI_EINVAL, "NULL output");
+  if (((uintptr_t)out & 7) != 0) return fail(ERI_EINVAL, "output not 8-byte aligned");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  Library& L = lib();
+  const size_t nlaunch = 1 + plan->buckets.size();
+  if (plan->timing && plan->events.size() < 2 * nlaunch) {
+    for (size_t i = plan->events.size(); i < 2 * nlaunch; ++i) {
+      cudaEvent_t e;
+      CUDA_OR(cudaEventCreate(&e), "cudaEventCreate");
+      plan->events.push_back(e);
+    }
+  }
+  size_t li = 0;
+  auto mark = [&](int end) -> cudaError_t {
+    return plan->timing ? cudaEventRecord(plan->events[2 * li + end], stream) : cudaSuccess;
+  };
+  {
+    CUDA_OR(mark(0), "cudaEventRecord");
+    const int threads = 128;
+    const int blocks = (plan->npair + threads - 1) / threads;
+    eri_pair_setup_kernel<<<blocks, threads, 0, stream>>>(plan->pin.p, plan->npair, plan->shells.p, plan->exps.p,
+                                                          plan->coefs.p, plan->pairs.p, plan->pprims.p);
+    CUDA_OR(cudaGetLastError(), "pair set-up launch");
+    CUDA_OR(mark(1), "cudaEventRecord");
+    ++li;
+  }
+  for (const Bucket& b : plan->buckets) {
+    CUDA_OR(mark(0), "cudaEventRecord");
+    EriLaunchArgs a;
+    a.quartets = plan->quartets.p + b.first;
+    a.pairs = plan->pairs.p;
+    a.pprims = plan->pprims.p;
+    a.boys_tab = L.d_boys;
+    a.out = out;
+    a.scratch = plan->scratch.p;
+    a.scratch_stride = plan->scratch_stride;
+    a.nq = (int32_t)b.count;
+    a.group = b.group;
+    if (b.tier == TIER_REG) {
+      void* args[] = {&a};
+      CUDA_OR(cudaLaunchKernel(b.reg_fn, dim3(b.grid), dim3(b.block), args, 0, stream), "class kernel launch");
+    } else {
+      EriProgArgs p;
+      p.ph1 = b.prog->d_ph1;
+      p.ph2 = b.prog->d_ph2;
+      p.c2s = L.d_c2s;
+      p.n1 = b.prog->n1;
+      p.n2 = b.prog->n2;
+      p.nh = b.prog->nh;
+      p.L = b.prog->L;
+      CUDA_OR(eri_exec_launch(b.tier == TIER_SHARED, &a, &p, b.grid, b.block, b.smem, stream), "executor launch");
+    }
+    CUDA_OR(mark(1), "cudaEventRecord");
+    ++li;
+  }
+  return ERI_OK;
+}
+
+extern "C" int eri_plan_set_timing(eri_plan_t* plan, int enable) {
+  if (!plan) return fail(ERI_EINVAL, "NULL plan");
+  plan->timing = enable != 0;
+  return ERI_OK;
+}
+
+extern "C" int eri_plan_launch_count(const eri_plan_t* plan) {
+  return plan ? (int)(plan->nq ? 1 + plan->buckets.size() : 0) : 0;
+}
+
+extern "C" int eri_plan_launch_info(const eri_plan_t* plan, int i, int32_t* info, double* flops, float* ms) {
+  if (!plan || i < 0 || i >= eri_plan_launch_count(plan)) return fail(ERI_EINVAL, "bad launch index");
+  int32_t v[8] = {-1, -1, -1, -1, 0, 0, 0, 0};
+  double f = 0;
+  if (i == 0) {
+    v[5] = (plan->npair + 127) / 128;
+    v[6] = 128;
+    v[7] = plan->npair;
+  } else {
+    const Bucket& b = plan->buckets[i - 1];
+    for (int k = 0; k < 4; ++k) v[k] = b.ls[k];
+    v[4] = b.tier;
+    v[5] = b.grid;
+    v[6] = b.block;
+    v[7] = (int32_t)b.count;
+    f = b.flops;
+  }
+  if (info) memcpy(info, v, sizeof v);
+  if (flops) *flops = f;
+  if (ms) {
+    *ms = -1.0f;
+    if (plan->timing && plan->events.size() >= (size_t)(2 * i + 2)) {
+      cudaError_t e = cudaEventElapsedTime(ms, plan->events[2 * i], plan->events[2 * i + 1]);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ERI_ESTATE, std::string("launch timing not available: ") + cudaGetErrorString(e));
+      }
+    }
+  }
+  return ERI_OK;
+}
+
+extern "C" int eri_compute_host(eri_plan_t* plan, double* host_out, void* stream_) {
+  if (!plan) return fail(ERI_EINVAL, "NULL plan");
+  if (plan->nq == 0) return ERI_OK;
+  if (!host_out) return fail(ERI_EINVAL, "NULL output");
+  const size_t n = (size_t)plan->offsets.back();
+  if (plan->outbuf.n < n) {
+    plan->outbuf.reset();
+    int rc = plan->outbuf.alloc(n, "output buffer");
+    if (rc) return rc;
+  }
+  int rc = eri_compute(plan, plan->outbuf.p, stream_);
+  if (rc) return rc;
+  CUDA_OR(cudaMemcpyAsync(host_out, plan->outbuf.p, n * sizeof(double), cudaMemcpyDeviceToHost,
+                          (cudaStream_t)stream_),
+          "copy to host");
+  return ERI_OK;
+}
+
+extern "C" int eri_plan_stats(const eri_plan_t* plan, double* stats, int n) {
+  if (!plan || !stats || n < 0) return fail(ERI_EINVAL, "bad argument");
+  const double v[6] = {(double)plan->buckets.size(), plan->flops, (double)(plan->scratch.n * sizeof(double)),
+                       (double)plan->nq, plan->nprimq, plan->h2d_bytes};
+  for (int i = 0; i < n && i < 6; ++i) stats[i] = v[i];
+  return ERI_OK;
+}
+
+extern "C" int eri_plan_destroy(eri_plan_t* plan) {
+  if (!plan) return ERI_OK;
+  cudaDeviceSynchronize();
+  delete plan;
+  return ERI_OK;
+}

@@ -1,0 +1,197 @@
+"""Python binding of the C ABI in include/eri.h (argument marshalling only).
+
+Every step of the integral path runs in the library's CUDA kernels; PyTorch
+supplies device memory and streams.  Loading fails loudly when the library
+has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+ERI_OK = 0
+ERRORS = {-1: "EINVAL", -2: "EUNSUPPORTED", -3: "ENOMEM", -4: "ECUDA", -5: "EBUSY", -6: "ETIMEOUT", -7: "ESTATE"}
+AXIS_RULES = {"prose": 0, "literal": 1, "common": 2}
+SCHEDULES = {"dsa": 0, "level": 1}
+SPH_MODES = {"stepwise": 0, "materialize": 1, "cart": 2}
+TIERS = {"auto": 0, "reg": 1, "shared": 2, "global": 3}
+TIERS_INV = {0: "setup", 1: "reg", 2: "shared", 3: "global"}
+ORIENTATIONS = {"tight": 0, "l": 1}
+
+
+class EriError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("{} ({}): {}".format(ERRORS.get(code, code), code, msg))
+        self.code = code
+
+
+class _Shell(ctypes.Structure):
+    _fields_ = [("l", ctypes.c_int32), ("nprim", ctypes.c_int32), ("center", ctypes.c_int32),
+                ("prim_offset", ctypes.c_int32)]
+
+
+class _Basis(ctypes.Structure):
+    _fields_ = [("centers", ctypes.c_void_p), ("ncenter", ctypes.c_int32), ("exponents", ctypes.c_void_p),
+                ("coefs", ctypes.c_void_p), ("nprim_total", ctypes.c_int32)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("axis_rule", ctypes.c_int32), ("schedule", ctypes.c_int32), ("sph_mode", ctypes.c_int32),
+                ("tier", ctypes.c_int32), ("orientation", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+_lib = None
+
+
+def library(path: str = LIB):
+    """The loaded liberi.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("CUDA library {} is not built; run __graft_entry__.build()".format(path))
+        lib = ctypes.CDLL(path)
+        lib.eri_plan.restype = ctypes.c_int
+        lib.eri_plan.argtypes = [ctypes.POINTER(_Shell), ctypes.c_int32, ctypes.POINTER(_Basis), ctypes.c_void_p,
+                                 ctypes.c_int64, ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_void_p)]
+        lib.eri_output_count.restype = ctypes.c_int64
+        lib.eri_output_count.argtypes = [ctypes.c_void_p]
+        lib.eri_output_offsets.restype = ctypes.c_int
+        lib.eri_output_offsets.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_compute.restype = ctypes.c_int
+        lib.eri_compute.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_compute_host.restype = ctypes.c_int
+        lib.eri_compute_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_plan_stats.restype = ctypes.c_int
+        lib.eri_plan_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        lib.eri_plan_set_timing.restype = ctypes.c_int
+        lib.eri_plan_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.eri_plan_launch_count.restype = ctypes.c_int
+        lib.eri_plan_launch_count.argtypes = [ctypes.c_void_p]
+        lib.eri_plan_launch_info.restype = ctypes.c_int
+        lib.eri_plan_launch_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]
+        lib.eri_plan_destroy.restype = ctypes.c_int
+        lib.eri_plan_destroy.argtypes = [ctypes.c_void_p]
+        lib.eri_last_error.restype = ctypes.c_char_p
+        lib.eri_last_error.argtypes = []
+        _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != ERI_OK:
+        raise EriError(rc, library().eri_last_error().decode())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Plan:
+    """A device-resident plan for one quartet list (see eri_plan)."""
+
+    def __init__(self, basis, quartets, axis_rule="prose", schedule="dsa", sph_mode="stepwise", tier="auto",
+                 orientation="tight"):
+        lib = library()
+        q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
+        ns = int(basis.shell_l.shape[0])
+        sh = (_Shell * max(ns, 1))()
+        for i in range(ns):
+            sh[i].l = int(basis.shell_l[i])
+            sh[i].nprim = int(basis.shell_nprim[i])
+            sh[i].center = int(basis.shell_center[i])
+            sh[i].prim_offset = int(basis.shell_prim[i])
+        self._keep = [np.ascontiguousarray(basis.centers, dtype=np.float64),
+                      np.ascontiguousarray(basis.exps, dtype=np.float64),
+                      np.ascontiguousarray(basis.coefs, dtype=np.float64), q]
+        b = _Basis(self._keep[0].ctypes.data, int(self._keep[0].shape[0]), self._keep[1].ctypes.data,
+                   self._keep[2].ctypes.data, int(self._keep[1].shape[0]))
+        o = _Opts(AXIS_RULES[axis_rule], SCHEDULES[schedule], SPH_MODES[sph_mode], TIERS[tier],
+                  ORIENTATIONS[orientation])
+        h = ctypes.c_void_p()
+        _check(lib.eri_plan(sh, ns, ctypes.byref(b), q.ctypes.data, q.shape[0], ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.nq = q.shape[0]
+        self._keep = None
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            library().eri_plan_destroy(self._h)
+            self._h = None
+
+    @property
+    def output_count(self) -> int:
+        return int(library().eri_output_count(self._h))
+
+    def offsets(self) -> np.ndarray:
+        off = np.zeros(self.nq + 1, dtype=np.int64)
+        _check(library().eri_output_offsets(self._h, off.ctypes.data))
+        return off
+
+    def stats(self) -> dict:
+        s = np.zeros(6)
+        _check(library().eri_plan_stats(self._h, s.ctypes.data, 6))
+        return dict(launches=int(s[0]), flops=float(s[1]), scratch_bytes=float(s[2]), quartets=int(s[3]),
+                    primitive_quartets=float(s[4]), h2d_bytes=float(s[5]))
+
+    def set_timing(self, enable=True):
+        _check(library().eri_plan_set_timing(self._h, 1 if enable else 0))
+
+    def launches(self):
+        """Per-launch records of the last compute (call after the stream has
+        completed): class, tier, grid, block, quartets, flops, ms."""
+        lib = library()
+        out = []
+        for i in range(lib.eri_plan_launch_count(self._h)):
+            info = np.zeros(8, dtype=np.int32)
+            fl = ctypes.c_double()
+            ms = ctypes.c_float()
+            _check(lib.eri_plan_launch_info(self._h, i, info.ctypes.data, ctypes.byref(fl), ctypes.byref(ms)))
+            out.append(dict(cls=tuple(int(x) for x in info[:4]), tier=int(info[4]), grid=int(info[5]),
+                            block=int(info[6]), quartets=int(info[7]), flops=fl.value, ms=ms.value))
+        return out
+
+    def compute(self, out, stream=None):
+        """Write every block into ``out`` (a CUDA float64 tensor of at least
+        output_count elements), asynchronously on ``stream``."""
+        import torch
+        if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()):
+            raise TypeError("out must be a contiguous CUDA float64 tensor")
+        if out.numel() < self.output_count:
+            raise ValueError("out is too small")
+        _check(library().eri_compute(self._h, out.data_ptr(), _stream_handle(stream)))
+        return out
+
+    def compute_host(self, out, stream=None):
+        """Compute and copy every block into ``out`` (a contiguous CPU float64
+        tensor, ideally pinned); asynchronous on ``stream``."""
+        import torch
+        if not (isinstance(out, torch.Tensor) and not out.is_cuda and out.dtype == torch.float64
+                and out.is_contiguous()):
+            raise TypeError("out must be a contiguous CPU float64 tensor")
+        if out.numel() < self.output_count:
+            raise ValueError("out is too small")
+        _check(library().eri_compute_host(self._h, out.data_ptr(), _stream_handle(stream)))
+        return out
+
+
+def eri(basis, quartets, device="cuda", **opts):
+    """Convenience: plan, compute on the current stream, return (values, offsets)."""
+    import torch
+    p = Plan(basis, quartets, **opts)
+    out = torch.empty(max(1, p.output_count), dtype=torch.float64, device=device)
+    p.compute(out)
+    torch.cuda.current_stream().synchronize()
+    off = p.offsets()
+    p.close()
+    return out[: off[-1]], off

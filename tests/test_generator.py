@@ -1,0 +1,125 @@
+"""Host-side checks of the code generator (FusionRCG Sec. III-A, III-B, IV):
+graph construction under each axis rule, DSA scheduling, PeakLive, the
+lifetime slot allocator, the Phase-2 graph in every transform mode, and the
+encoded programs -- evaluated on the CPU against the oracle."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_10312_gb300 import synth
+from paper_2605_10312_gb300.gen import cart, encode, hrr, program, sph, vrr
+from gen_eval import evaluate, run_encoded
+from ref import blocks, within
+
+
+def test_cartesian_order():
+    assert cart.tuples(2) == ((2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2))
+    for l in range(9):
+        assert [cart.index(t) for t in cart.tuples(l)] == list(range(cart.ncart(l)))
+
+
+def test_generator_sph_matches_oracle():
+    # two independent derivations: solid-harmonic recurrence vs closed form
+    for l in range(5):
+        np.testing.assert_allclose(sph.matrix(l), oracle.cart2sph(l), atol=2e-15)
+
+
+@pytest.mark.parametrize("rule", vrr.AXIS_RULES)
+@pytest.mark.parametrize("ls", [(1, 1, 1, 1), (2, 2, 1, 1), (2, 1, 2, 2), (3, 0, 1, 2)])
+def test_vrr_graph_is_complete_and_acyclic(rule, ls):
+    g = vrr.build(*ls, rule=rule)
+    E, F = vrr.h_layout(*ls)
+    assert sorted(g.target.values()) == list(range(len(E) * len(F)))
+    for v, ts in enumerate(g.terms):
+        e, f, m = g.keys[v]
+        assert m <= sum(ls) - sum(e) - sum(f)
+        for _, p in ts:
+            assert p < v  # parents are created first
+        if not ts:
+            assert e == (0, 0, 0) and f == (0, 0, 0)
+
+
+def test_node_counts_by_axis_rule():
+    # (2,2,1,1): consumer-first 521, Algorithm 1 as printed 718, bra-first 671
+    got = {r: len(vrr.build(2, 2, 1, 1, r)) for r in vrr.AXIS_RULES}
+    assert got == {"prose": 521, "literal": 718, "common": 671}
+    assert len(vrr.build(1, 1, 1, 1)) == 146
+    assert len(vrr.build(2, 2, 2, 2)) == 2330
+
+
+@pytest.mark.parametrize("how", vrr.SCHEDULES)
+@pytest.mark.parametrize("ls", [(1, 1, 1, 1), (2, 2, 1, 1), (2, 2, 2, 2)])
+def test_schedule_and_slots(how, ls):
+    g = vrr.build(*ls)
+    order = vrr.schedule(g, how)
+    assert vrr.check_topological(g, order)
+    peak = vrr.peak_live(g, order)
+    slot, nslot = vrr.allocate_slots(g, order)
+    assert vrr.verify_slots(g, order, slot)
+    assert nslot <= peak
+
+
+def test_dsa_lowers_peak_live():
+    for ls in [(1, 1, 1, 1), (2, 2, 1, 1), (2, 2, 2, 2)]:
+        g = vrr.build(*ls)
+        assert vrr.peak_live(g, vrr.schedule(g, "dsa")) < vrr.peak_live(g, vrr.schedule(g, "level"))
+
+
+def test_dsa_score_by_brute_force():
+    """Eq. 7 scores against a direct set computation of Reach(v)."""
+    g = vrr.build(1, 1, 1, 0)
+    cons = [[] for _ in range(len(g))]
+    for v, ts in enumerate(g.terms):
+        for _, p in ts:
+            cons[p].append(v)
+    outd = [len(set(c)) for c in cons]
+    ind = [len(set(p for _, p in ts)) for ts in g.terms]
+    s = vrr.dsa_scores(g, window=64)
+    for v in range(len(g)):
+        reach, stack = set(), [v]
+        while stack:
+            w = stack.pop()
+            if w not in reach:
+                reach.add(w)
+                stack.extend(cons[w])
+        assert s[v] == sum(outd[w] - ind[w] for w in reach)
+
+
+def test_stepwise_saves_operations():
+    # Eq. 16 vs Eq. 17: the stepwise order needs fewer operations at high l
+    for ls in [(2, 2, 2, 2), (4, 4, 4, 4)]:
+        st = hrr.op_counts(hrr.build(*ls, "stepwise"))[0]
+        ma = hrr.op_counts(hrr.build(*ls, "materialize"))[0]
+        assert st < ma
+
+
+OPTS = [("prose", "dsa", "stepwise"), ("literal", "level", "materialize"), ("common", "dsa", "cart"),
+        ("prose", "level", "stepwise")]
+
+
+@pytest.mark.parametrize("opts", OPTS)
+@pytest.mark.parametrize("ls", [(0, 0, 0, 0), (1, 0, 0, 0), (1, 1, 1, 1), (2, 1, 0, 1), (0, 2, 1, 2), (3, 1, 2, 0),
+                                (2, 2, 2, 1)])
+def test_program_matches_oracle(ls, opts):
+    """The graph program (interpreted in numpy) and its encoded descriptor
+    stream both reproduce the oracle."""
+    prog = program.make(*ls, *opts)
+    basis, q = synth.class_sweep(ls, 3, kset=(1, 2), seed=9, box_angstrom=3.0, exp_range=(0.1, 30))
+    ref, off = blocks(basis, q, cart=(opts[2] == "cart"))
+    ref = ref.reshape(q.shape[0], -1)
+    a = evaluate(prog, basis, q)
+    b = run_encoded(encode.encode(prog), prog, basis, q)
+    assert within(a, ref).all()
+    assert within(b, ref).all()
+
+
+def test_all_classes_enumerated():
+    cls = program.all_classes()
+    assert len(cls) == 325 and len(set(cls)) == 325
+    # every ordered combination maps to one class by bra-ket exchange
+    for ls in itertools.product(range(5), repeat=4):
+        a, b = (ls[0], ls[1]), (ls[2], ls[3])
+        key = a + b if program.pair_rank(*a) >= program.pair_rank(*b) else b + a
+        assert key in cls

@@ -1,0 +1,68 @@
+"""Boundary behaviour of the CUDA path: host-buffer entry point, offsets,
+empty plans, tier routing and forced tiers."""
+import numpy as np
+import pytest
+
+from paper_2605_10312_gb300 import synth
+from ref import blocks, report, within
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eri():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2605_10312_gb300 import eri as m
+    m.library()
+    return m
+
+
+def test_compute_host_matches_device(eri):
+    import torch
+    basis, q = synth.class_sweep((2, 1, 1, 0), 500, kset=(1, 3), seed=9, box_angstrom=3.0)
+    p = eri.Plan(basis, q)
+    dev = torch.empty(p.output_count, dtype=torch.float64, device="cuda")
+    p.compute(dev)
+    host = torch.empty(p.output_count, dtype=torch.float64).pin_memory()
+    p.compute_host(host)
+    torch.cuda.synchronize()
+    assert torch.equal(dev.cpu(), host)
+    p.close()
+
+
+def test_empty_plan(eri):
+    import torch
+    basis, _ = synth.tiny_set()
+    p = eri.Plan(basis, np.zeros((0, 4), dtype=np.int32))
+    assert p.output_count == 0
+    p.compute(torch.empty(1, dtype=torch.float64, device="cuda"))
+    p.close()
+
+
+@pytest.mark.parametrize("tier,ls", [("reg", (1, 1, 1, 0)), ("shared", (1, 1, 1, 0)), ("global", (1, 1, 1, 0)),
+                                     ("shared", (2, 1, 2, 0)), ("global", (2, 2, 1, 1))])
+def test_forced_tiers_agree(eri, tier, ls):
+    """The same class through each tier that can hold it gives the oracle's
+    values (register tier only for the classes compiled straight-line)."""
+    basis, q = synth.class_sweep(ls, 300, kset=(1, 2), seed=19, box_angstrom=3.0)
+    ref, _ = blocks(basis, q)
+    for t in (tier, "auto"):
+        got, _ = eri.eri(basis, q, tier=t)
+        assert within(got.cpu().numpy(), ref).all(), (t, report(got.cpu().numpy(), ref))
+
+
+def test_orientation_option(eri):
+    """Higher-l-first orientation is also correct on a compact geometry."""
+    basis, q = synth.class_sweep((2, 2, 1, 1), 100, kset=(1, 2), seed=23, box_angstrom=2.0, exp_range=(0.2, 10.0))
+    got, _ = eri.eri(basis, q, orientation="l")
+    ref, _ = blocks(basis, q)
+    assert within(got.cpu().numpy(), ref).all(), report(got.cpu().numpy(), ref)
+
+
+def test_unsupported_tier_is_an_error(eri):
+    basis, q = synth.class_sweep((4, 4, 4, 4), 2, seed=3)
+    with pytest.raises(eri.EriError) as e:
+        eri.Plan(basis, q, tier="reg")
+    assert e.value.code == -2
