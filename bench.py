@@ -38,6 +38,8 @@ UNIT = "quartets/s"
 SWEEP = [((1, 1, 1, 1), 400_000), ((2, 2, 2, 2), 100_000), ((3, 3, 3, 3), 10_000), ((4, 4, 4, 4), 1_000)]
 KSET = (1, 3, 6)
 SEED = 2000
+ONLY = None     # --classes: subset of the sweep (profiling runs)
+SCALE = 1.0     # --scale: quartet counts multiplied by this (profiling runs)
 # FP64 fused multiply-add lanes per SM per clock, measured on GB300 with the
 # fp_peak microbenchmark (independent FMA chains on every SM)
 FP64_LANES_PER_SM_CLK = 1.683
@@ -52,6 +54,9 @@ def fp64_peak_tflops(mhz=SM_MAX_MHZ):
 def workload(rank=0):
     parts = []
     for ls, n in SWEEP:
+        if ONLY and "".join("spdfg"[x] for x in ls) not in ONLY:
+            continue
+        n = max(1, int(n * SCALE))
         basis, q = synth.class_sweep(ls, n, kset=KSET, seed=SEED + 10 * ls[0] + 1000 * rank)
         parts.append((ls, basis, q))
     return parts
@@ -136,10 +141,15 @@ def oracle_rates(parts, budget_s=15.0, nthreads=None):
     return rates, samples, nthreads
 
 
+def sweep():
+    return [(ls, max(1, int(n * SCALE))) for ls, n in SWEEP
+            if not ONLY or "".join("spdfg"[x] for x in ls) in ONLY]
+
+
 def mix_rate(rates):
     """Quartets/s of the whole step's class mix given per-class rates."""
-    tot = sum(n for _, n in SWEEP)
-    t = sum(n / rates[ls] for ls, n in SWEEP)
+    tot = sum(n for _, n in sweep())
+    t = sum(n / rates[ls] for ls, n in sweep())
     return tot / t
 
 
@@ -158,7 +168,7 @@ def run_reference(args):
             rates = (r, samples, cores)
     value = statistics.median(times)
     r, samples, cores = rates
-    tot = sum(n for _, n in SWEEP)
+    tot = sum(n for _, n in sweep())
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / value,
@@ -177,9 +187,9 @@ def run_reference(args):
 
 def config_dict():
     return {"workload": "per-class FP64 sweep: " + ", ".join(
-        "({0}{0}|{0}{0}) x {1}".format("spdfg"[ls[0]], n) for ls, n in SWEEP),
+        "({0}{0}|{0}{0}) x {1}".format("spdfg"[ls[0]], n) for ls, n in sweep()),
         "K_per_shell": list(KSET), "box_angstrom": 10.0, "exponents": [0.05, 500.0], "output": "spherical",
-        "quartets_per_step": sum(n for _, n in SWEEP), "l2": "flushed between steps (512 MiB write)"}
+        "quartets_per_step": sum(n for _, n in sweep()), "l2": "flushed between steps (512 MiB write)"}
 
 
 # ---------------------------------------------------------------------------
@@ -245,7 +255,7 @@ def run_ours(args):
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    quartets = sum(n for _, n in SWEEP)
+    quartets = sum(n for _, n in sweep())
     value = quartets * world * args.steps / (total_ms * 1e-3)
 
     # dominant kernel: the launch with the largest time share
@@ -269,8 +279,12 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     e2e_ms, h2d, d2h = [], 0, 0
+    if args.no_e2e:
+        args_e2e_steps = 0
+    else:
+        args_e2e_steps = args.warmup + args.steps
     host_outs = [torch.empty(p.output_count, dtype=torch.float64).pin_memory() for _, p in plans]
-    for it in range(args.warmup + args.steps):
+    for it in range(args_e2e_steps):
         barrier()
         t0 = time.perf_counter()
         h2d = d2h = 0
@@ -284,7 +298,7 @@ def run_ours(args):
         barrier()
         if it >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = sum(e2e_ms)
+    e2e_total = sum(e2e_ms) if e2e_ms else float("nan")
     if world > 1:
         t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -351,7 +365,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--classes", default="", help="comma-separated subset, e.g. gggg (profiling runs)")
+    ap.add_argument("--scale", type=float, default=1.0, help="multiply the quartet counts (profiling runs)")
     args = ap.parse_args()
+    global ONLY, SCALE
+    ONLY = set(c for c in args.classes.split(",") if c) or None
+    SCALE = args.scale
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -71,8 +71,11 @@ typedef struct {
   int32_t axis_rule;    /* 0 consumer-first z->y->x (Sec. III-A), 1 Algorithm 1 as printed, 2 bra-first x->y->z */
   int32_t schedule;     /* 0 DSA (Eq. 7), 1 level order (no DSA) */
   int32_t sph_mode;     /* 0 stepwise fusion (Eq. 16), 1 materialize-then-transform (Eq. 17), 2 Cartesian output */
-  int32_t tier;         /* 0 auto, 1 register (compiled), 2 shared-memory program, 3 global-scratch program */
-  int32_t orientation;  /* 0 tighter shell of each pair on the recurrence centre, 1 higher l first */
+  int32_t tier;         /* 0 auto, 1 register (compiled), 2 shared-memory program, 3 global-scratch program,
+                           4 team-cooperative program (values shared by a team of lanes) */
+  int32_t orientation;  /* 0 per primitive pair: each recurs on its tighter primitive's centre (a pair may split
+                           into two oriented parts whose blocks are summed), 1 whole pair on the higher l,
+                           2 whole pair on the shell holding the largest exponent */
   int32_t reserved[3];
 } eri_opts;
 

@@ -37,6 +37,9 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + CS
 # straight-line size (VRR terms + 1.5 x Phase-2 operations) up to which a
 # class gets a compiled register-tier kernel; larger classes run as programs
 REG_TIER_MAX = 3000
+# shared memory four T=32 teams may fill with value slots before a class
+# moves to T=128 teams
+COOP_T32_SMEM = 200 * 1024
 
 AXIS = {"prose": 0, "literal": 1, "common": 2}
 SCHED = {"dsa": 0, "level": 1}
@@ -78,6 +81,17 @@ def _class_job(args):
     if want_reg and rec["size"] <= REG_TIER_MAX:
         rec["cuda"] = emit_cuda.emit_class(prog, "reg")
         rec["kname"] = emit_cuda.kernel_name(ls, "reg")
+    elif want_reg:
+        # team-cooperative form: one warp per primitive quartet while four
+        # teams' live sets fit in shared memory, else four warps
+        from paper_2605_10312_gb300.gen import coop
+        cp = coop.build(prog, 32)
+        if 4 * cp.nslot * 8 > COOP_T32_SMEM:
+            cp = coop.build(prog, 128)
+        rec["coop"] = dict(T=cp.T, nh=cp.nh, nslot=cp.nslot, L=cp.L, dims=cp.out_dims, steps1=cp.steps1.tobytes(),
+                           steps2=cp.steps2.tobytes(), nw1=int(cp.steps1.shape[0]), nw2=int(cp.steps2.shape[0]),
+                           ph1=cp.ph1.tobytes(), ph2=cp.ph2.tobytes(), n1=int(cp.ph1.shape[0]),
+                           n2=int(cp.ph2.shape[0]), eff1=cp.eff1, eff2=cp.eff2)
     return rec
 
 
@@ -109,6 +123,18 @@ def write_blob(path, recs, boys, c2s):
             f.write(struct.pack("<2d", r["flops_prim"], r["flops_p2"]))
             f.write(r["ph1"])
             f.write(r["ph2"])
+        coops = [r for r in recs if "coop" in r]
+        f.write(struct.pack("<I", len(coops)))
+        for r in coops:
+            o, c = r["opts"], r["coop"]
+            f.write(struct.pack("<8b", *r["ls"], AXIS[o[0]], SCHED[o[1]], SPH[o[2]], 0))
+            f.write(struct.pack("<12i", c["T"], c["nh"], c["nslot"], c["L"], c["nw1"], c["nw2"], c["n1"], c["n2"],
+                                *c["dims"]))
+            f.write(struct.pack("<2d", r["flops_prim"], r["flops_p2"]))
+            f.write(c["steps1"])
+            f.write(c["steps2"])
+            f.write(c["ph1"])
+            f.write(c["ph2"])
     os.replace(path + ".tmp", path)
 
 
@@ -174,15 +200,20 @@ def build(force=False, jobs=None, log=print):
         _write_if_changed(os.path.join(GEN_DIR, "eri_registry.cu"), _registry(recs))
         # class table for the docs and the benchmark: per-class counts
         with open(os.path.join(BUILD, "classes.tsv"), "w") as f:
-            f.write("la\tlb\tlc\tld\ttier\tvrr_nodes\tpeak_live\tnslot\tnh\tnout\tper_prim_flops\tp2_flops\n")
+            f.write("la\tlb\tlc\tld\ttier\tvrr_nodes\tpeak_live\tnslot\tnh\tnout\tper_prim_flops\tp2_flops"
+                    "\tcoop_T\tcoop_nslot\tcoop_eff1\tcoop_eff2\n")
             for r in sorted(recs, key=lambda r: r["ls"]):
                 c = r["counts"]
-                f.write("\t".join(str(x) for x in (*r["ls"], "reg" if "cuda" in r else "prog", c["vrr_nodes"],
+                cp = r.get("coop")
+                f.write("\t".join(str(x) for x in (*r["ls"], "reg" if "cuda" in r else "coop", c["vrr_nodes"],
                                                    c["peak_live"], r["nslot"], c["nh"], c["nout"],
-                                                   c["per_prim_flops"], c["p2_flops"])) + "\n")
+                                                   c["per_prim_flops"], c["p2_flops"],
+                                                   cp["T"] if cp else "", cp["nslot"] if cp else "",
+                                                   round(cp["eff1"], 3) if cp else "",
+                                                   round(cp["eff2"], 3) if cp else "")) + "\n")
         open(stamp, "w").write(gen_key)
     units = [os.path.join(CSRC, "eri_runtime.cu"), os.path.join(CSRC, "eri_exec.cu"),
-             os.path.join(GEN_DIR, "eri_registry.cu")]
+             os.path.join(CSRC, "eri_coop.cu"), os.path.join(GEN_DIR, "eri_registry.cu")]
     units += sorted(os.path.join(GEN_DIR, f) for f in os.listdir(GEN_DIR)
                     if f.endswith("_reg.cu"))
     objs = [os.path.join(BUILD, os.path.basename(u)[:-3] + ".o") for u in units]

@@ -26,10 +26,18 @@ struct EriPairRec {    // 32 bytes
 };
 
 struct EriQuartetRec { // 32 bytes
-  int32_t bra, ket;    // EriPairRec indices (bra = centres A, B; ket = C, D)
+  int32_t bra, ket;    // EriPairRec indices (bra = centres A, B; ket = C, D);
+                       // bit 31 of bra: add into the block instead of writing it
   int64_t out_off;     // first output element of this quartet's block
   int32_t st[4];       // output strides of the A, B, C, D component indices
 };
+
+#define ERI_PAIR_INDEX(x) ((x) & 0x7fffffff)
+#define ERI_ACCUMULATE(x) ((x) < 0)
+
+// Output store of one element: the first part of a quartet writes its
+// block, later parts (other pair orientations, other launches) add to it.
+__device__ __forceinline__ void eri_st(double* p, double v, bool acc) { *p = acc ? *p + v : v; }
 
 struct EriLaunchArgs {
   const EriQuartetRec* __restrict__ quartets;  // this launch's quartets

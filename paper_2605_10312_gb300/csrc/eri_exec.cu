@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(128) eri_exec_kernel(const EriLaunchArgs a, co
 #define VAL(s) V[(int64_t)(s) * vs]
   for (int q = gt / G; q < a.nq; q += ngroups) {
     const EriQuartetRec qr = a.quartets[q];
-    const EriPairRec bra = a.pairs[qr.bra];
+    const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];
+    const bool acc = ERI_ACCUMULATE(qr.bra);
     const EriPairRec ket = a.pairs[qr.ket];
     for (int h = 0; h < p.nh; ++h) VAL(h) = 0.0;
     const int kk = ket.nprim;
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(128) eri_exec_kernel(const EriLaunchArgs a, co
         } else {
           const int64_t off = (int64_t)(d.z & 255) * qr.st[0] + (int64_t)((d.z >> 8) & 255) * qr.st[1] +
                               (int64_t)((d.z >> 16) & 255) * qr.st[2] + (int64_t)(d.z >> 24) * qr.st[3];
-          o[off] = VAL(dst);
+          eri_st(o + off, VAL(dst), acc);
         }
       }
     }

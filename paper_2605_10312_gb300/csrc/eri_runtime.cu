@@ -30,6 +30,24 @@ extern "C" cudaError_t eri_exec_launch(int shared, const EriLaunchArgs* a, const
                                        int block, size_t smem, cudaStream_t stream);
 extern "C" cudaError_t eri_exec_set_smem(size_t bytes);
 
+struct EriCoopArgs {
+  const uint4* ph1;
+  const uint32_t* steps1;
+  const uint4* ph2;
+  const uint32_t* steps2;
+  const double* c2s;
+  double* gvals;
+  double* gH;
+  int32_t nw1, nw2;
+  int32_t nh, nslot, L;
+  int32_t smem_slots;
+  int32_t h_in_smem;
+  int32_t nteams;
+};
+extern "C" cudaError_t eri_coop_launch(int T, const EriLaunchArgs* a, const EriCoopArgs* p, int grid, size_t smem,
+                                       cudaStream_t stream);
+extern "C" cudaError_t eri_coop_set_smem(size_t bytes);
+
 struct EriRegEntry {
   int8_t ls[4];
   const void* fn;
@@ -72,17 +90,32 @@ struct ClassProg {
   uint4* d_ph2 = nullptr;
 };
 
+struct CoopProg {
+  int ls[4];
+  int opts[3];
+  int T, nh, nslot, L, nw1, nw2, n1, n2;
+  int dims[4];
+  double flops_prim, flops_p2;
+  std::vector<uint32_t> steps1, steps2, ph1, ph2;
+  uint32_t* d_steps1 = nullptr;
+  uint32_t* d_steps2 = nullptr;
+  uint4* d_ph1 = nullptr;
+  uint4* d_ph2 = nullptr;
+};
+
 struct Library {
   bool loaded = false;
   std::string err;
   std::vector<double> boys, c2s;
   std::map<std::vector<int>, std::unique_ptr<ClassProg>> progs;  // key: ls[4] + opts[3]
+  std::map<std::vector<int>, std::unique_ptr<CoopProg>> coops;   // key: ls[4] + opts[3]
   std::map<std::vector<int>, const void*> reg;                      // key: ls[4]
   double* d_boys = nullptr;
   double* d_c2s = nullptr;
   int device = -1;
   int nsm = 0;
   size_t smem_optin = 0;
+  size_t smem_per_sm = 0;
   std::mutex mu;
 };
 
@@ -141,6 +174,39 @@ bool load_blob(Library& L, const std::string& path, bool tables) {
     std::vector<int> key = {p->ls[0], p->ls[1], p->ls[2], p->ls[3], p->opts[0], p->opts[1], p->opts[2]};
     L.progs[key] = std::move(p);
   }
+  uint32_t ncoop = 0;
+  if (ok && rd(f, &ncoop)) {
+    for (uint32_t c = 0; ok && c < ncoop; ++c) {
+      auto p = std::make_unique<CoopProg>();
+      int8_t hdr[8];
+      int32_t iv[12];
+      double fv[2];
+      ok = rd(f, hdr, 8) && rd(f, iv, 12) && rd(f, fv, 2);
+      if (!ok) break;
+      for (int k = 0; k < 4; ++k) p->ls[k] = hdr[k];
+      for (int k = 0; k < 3; ++k) p->opts[k] = hdr[4 + k];
+      p->T = iv[0];
+      p->nh = iv[1];
+      p->nslot = iv[2];
+      p->L = iv[3];
+      p->nw1 = iv[4];
+      p->nw2 = iv[5];
+      p->n1 = iv[6];
+      p->n2 = iv[7];
+      for (int k = 0; k < 4; ++k) p->dims[k] = iv[8 + k];
+      p->flops_prim = fv[0];
+      p->flops_p2 = fv[1];
+      p->steps1.resize(p->nw1);
+      p->steps2.resize(p->nw2);
+      p->ph1.resize((size_t)p->n1 * 4);
+      p->ph2.resize((size_t)p->n2 * 4);
+      ok = rd(f, p->steps1.data(), p->steps1.size()) && rd(f, p->steps2.data(), p->steps2.size()) &&
+           rd(f, p->ph1.data(), p->ph1.size()) && rd(f, p->ph2.data(), p->ph2.size());
+      if (!ok) break;
+      std::vector<int> key = {p->ls[0], p->ls[1], p->ls[2], p->ls[3], p->opts[0], p->opts[1], p->opts[2]};
+      L.coops[key] = std::move(p);
+    }
+  }
   fclose(f);
   if (ok && tables) {
     L.boys = boys;
@@ -177,7 +243,9 @@ int ensure_library() {
     CUDA_OR(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
     L.nsm = prop.multiProcessorCount;
     L.smem_optin = prop.sharedMemPerBlockOptin;
+    L.smem_per_sm = prop.sharedMemPerMultiprocessor;
     CUDA_OR(eri_exec_set_smem(L.smem_optin), "cudaFuncSetAttribute");
+    CUDA_OR(eri_coop_set_smem(L.smem_optin), "cudaFuncSetAttribute");
     L.device = dev;
   }
   return ERI_OK;
@@ -194,6 +262,21 @@ int upload_prog(ClassProg* p) {
   return ERI_OK;
 }
 
+int upload_coop(CoopProg* p) {
+  Library& L = lib();
+  std::lock_guard<std::mutex> g(L.mu);
+  if (p->d_ph1) return ERI_OK;
+  CUDA_OR(cudaMalloc(&p->d_steps1, std::max<size_t>(1, p->steps1.size()) * 4), "cudaMalloc program");
+  CUDA_OR(cudaMalloc(&p->d_steps2, std::max<size_t>(1, p->steps2.size()) * 4), "cudaMalloc program");
+  CUDA_OR(cudaMalloc(&p->d_ph1, std::max<size_t>(1, p->ph1.size()) * 4), "cudaMalloc program");
+  CUDA_OR(cudaMalloc(&p->d_ph2, std::max<size_t>(1, p->ph2.size()) * 4), "cudaMalloc program");
+  CUDA_OR(cudaMemcpy(p->d_steps1, p->steps1.data(), p->steps1.size() * 4, cudaMemcpyHostToDevice), "upload");
+  CUDA_OR(cudaMemcpy(p->d_steps2, p->steps2.data(), p->steps2.size() * 4, cudaMemcpyHostToDevice), "upload");
+  CUDA_OR(cudaMemcpy(p->d_ph1, p->ph1.data(), p->ph1.size() * 4, cudaMemcpyHostToDevice), "upload");
+  CUDA_OR(cudaMemcpy(p->d_ph2, p->ph2.data(), p->ph2.size() * 4, cudaMemcpyHostToDevice), "upload");
+  return ERI_OK;
+}
+
 // ---------------------------------------------------------------------------
 // device data the pair set-up kernel consumes
 // ---------------------------------------------------------------------------
@@ -205,6 +288,8 @@ struct DevShell {
 struct DevPairIn {
   int32_t a, b;       // oriented shells: a is the recurrence centre
   int32_t prim_off;   // first EriPairPrim
+  int32_t list_off;   // -1: every (i, j) of a x b; else nlist packed (i | j << 16) entries
+  int32_t nlist;
   int32_t pad;
 };
 
@@ -216,7 +301,8 @@ struct DevPairIn {
 // 2 pi^(5/2) / (zeta eta sqrt(zeta+eta)) K_AB K_CD is one product.
 __global__ void eri_pair_setup_kernel(const DevPairIn* __restrict__ pin, int npair, const DevShell* __restrict__ sh,
                                       const double* __restrict__ ex, const double* __restrict__ co,
-                                      EriPairRec* __restrict__ pairs, EriPairPrim* __restrict__ pp) {
+                                      const uint32_t* __restrict__ plist, EriPairRec* __restrict__ pairs,
+                                      EriPairPrim* __restrict__ pp) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npair) return;
   const DevPairIn in = pin[p];
@@ -225,7 +311,8 @@ __global__ void eri_pair_setup_kernel(const DevPairIn* __restrict__ pin, int npa
   const double ab2 = AB0 * AB0 + AB1 * AB1 + AB2 * AB2;
   EriPairRec r;
   r.prim_off = in.prim_off;
-  r.nprim = A.nprim * B.nprim;
+  const int n = in.list_off < 0 ? A.nprim * B.nprim : in.nlist;
+  r.nprim = n;
   r.AB[0] = AB0;
   r.AB[1] = AB1;
   r.AB[2] = AB2;
@@ -233,30 +320,37 @@ __global__ void eri_pair_setup_kernel(const DevPairIn* __restrict__ pin, int npa
   const double dfi[5] = {1.0, 1.0, 1.0 / 1.7320508075688772935, 1.0 / 3.8729833462074168852,
                          1.0 / 10.246950765959598383};  // 1/sqrt((2l-1)!!)
   const double C0 = 5.9149671727956128778;              // sqrt(2) pi^(5/4)
-  for (int i = 0; i < A.nprim; ++i) {
+  for (int k = 0; k < n; ++k) {
+    int i, j;
+    if (in.list_off < 0) {
+      i = k / B.nprim;
+      j = k - i * B.nprim;
+    } else {
+      const uint32_t e = plist[in.list_off + k];
+      i = (int)(e & 0xFFFF);
+      j = (int)(e >> 16);
+    }
     const double a = ex[A.prim + i];
     const double xa = a * 0.63661977236758134308;  // 2a/pi
     double na = sqrt(xa * sqrt(xa)) * dfi[A.l];
     const double sa = sqrt(4.0 * a);
-    for (int k = 0; k < A.l; ++k) na *= sa;
-    for (int j = 0; j < B.nprim; ++j) {
-      const double b = ex[B.prim + j];
-      const double xb = b * 0.63661977236758134308;
-      double nb = sqrt(xb * sqrt(xb)) * dfi[B.l];
-      const double sb = sqrt(4.0 * b);
-      for (int k = 0; k < B.l; ++k) nb *= sb;
-      const double z = a + b;
-      const double iz = 1.0 / z;
-      EriPairPrim q;
-      q.zeta = z;
-      q.inv2z = 0.5 * iz;
-      for (int d = 0; d < 3; ++d) {
-        q.P[d] = (a * A.ctr[d] + b * B.ctr[d]) * iz;
-        q.PA[d] = q.P[d] - A.ctr[d];
-      }
-      q.K = C0 * co[A.prim + i] * na * co[B.prim + j] * nb * exp(-a * b * iz * ab2) * iz;
-      pp[in.prim_off + i * B.nprim + j] = q;
+    for (int t = 0; t < A.l; ++t) na *= sa;
+    const double b = ex[B.prim + j];
+    const double xb = b * 0.63661977236758134308;
+    double nb = sqrt(xb * sqrt(xb)) * dfi[B.l];
+    const double sb = sqrt(4.0 * b);
+    for (int t = 0; t < B.l; ++t) nb *= sb;
+    const double z = a + b;
+    const double iz = 1.0 / z;
+    EriPairPrim q;
+    q.zeta = z;
+    q.inv2z = 0.5 * iz;
+    for (int d = 0; d < 3; ++d) {
+      q.P[d] = (a * A.ctr[d] + b * B.ctr[d]) * iz;
+      q.PA[d] = q.P[d] - A.ctr[d];
     }
+    q.K = C0 * co[A.prim + i] * na * co[B.prim + j] * nb * exp(-a * b * iz * ab2) * iz;
+    pp[in.prim_off + k] = q;
   }
 }
 
@@ -264,7 +358,7 @@ __global__ void eri_pair_setup_kernel(const DevPairIn* __restrict__ pin, int npa
 // plan
 // ---------------------------------------------------------------------------
 namespace {
-enum Tier { TIER_REG = 1, TIER_SHARED = 2, TIER_GLOBAL = 3 };
+enum Tier { TIER_REG = 1, TIER_SHARED = 2, TIER_GLOBAL = 3, TIER_COOP = 4 };
 
 struct Bucket {
   int ls[4];
@@ -276,6 +370,8 @@ struct Bucket {
   size_t smem = 0;
   int group = 1;                 // lanes per shell quartet
   double flops = 0;              // algorithmic FP64 flops of this launch
+  CoopProg* coop = nullptr;      // team-cooperative tier
+  int smem_slots = 0, h_in_smem = 0, nteams = 0;
 };
 
 template <typename T>
@@ -316,11 +412,13 @@ struct eri_plan_s {
   DevBuf<DevShell> shells;
   DevBuf<double> exps, coefs;
   DevBuf<DevPairIn> pin;
+  DevBuf<uint32_t> plist;
   DevBuf<EriPairRec> pairs;
   DevBuf<EriPairPrim> pprims;
   DevBuf<EriQuartetRec> quartets;
   DevBuf<double> scratch;
   DevBuf<double> outbuf;
+  DevBuf<double> coop_vals, coop_h;  // team-private spill regions of the cooperative tier
   int64_t scratch_stride = 0;
   double h2d_bytes = 0;
   bool timing = false;
@@ -340,7 +438,7 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
   memset(&opts, 0, sizeof opts);
   if (opts_in) opts = *opts_in;
   if (opts.axis_rule < 0 || opts.axis_rule > 2 || opts.schedule < 0 || opts.schedule > 1 || opts.sph_mode < 0 ||
-      opts.sph_mode > 2 || opts.tier < 0 || opts.tier > 3 || opts.orientation < 0 || opts.orientation > 1)
+      opts.sph_mode > 2 || opts.tier < 0 || opts.tier > 4 || opts.orientation < 0 || opts.orientation > 2)
     return fail(ERI_EINVAL, "option out of range");
   if (nq < 0 || nshell < 0 || (nq > 0 && (!shells || !basis || !quartets)))
     return fail(ERI_EINVAL, "NULL or negative argument");
@@ -389,69 +487,125 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
     return ERI_OK;
   }
   // ---- orientation and class of every quartet
-  auto first_of_pair = [&](int s0, int s1) {
-    // returns true when s0 should be the recurrence centre
-    const int l0 = shells[s0].l, l1 = shells[s1].l;
-    if (opts.orientation == 1) return l0 >= l1;
-    if (maxexp[s0] != maxexp[s1]) return maxexp[s0] > maxexp[s1];
-    return l0 >= l1;
-  };
+  // Pair orientation.  Default: each primitive pair recurs on its tighter
+  // primitive's centre (a contracted pair splits into at most two oriented
+  // partial pairs), which keeps FP64 HRR cancellation bounded; options: the
+  // whole pair on the shell with the largest exponent, or on the higher l.
   std::unordered_map<uint64_t, int> pair_id;
   std::vector<DevPairIn> pin;
+  std::vector<uint32_t> plist;
   int64_t pprim = 0;
-  auto get_pair = [&](int a, int b) {
-    uint64_t key = ((uint64_t)(uint32_t)a << 32) | (uint32_t)b;
+  // kind 0 = every primitive pair; 1 = pairs whose centre exponent is >= the
+  // other's; 2 = pairs whose centre exponent is > the other's
+  auto get_pair = [&](int a, int b, int kind) {
+    uint64_t key = ((uint64_t)(uint32_t)a << 34) | ((uint64_t)(uint32_t)b << 2) | (uint64_t)kind;
     auto it = pair_id.find(key);
     if (it != pair_id.end()) return it->second;
     int id = (int)pin.size();
-    pin.push_back({a, b, (int32_t)pprim, 0});
-    pprim += (int64_t)shells[a].nprim * shells[b].nprim;
+    DevPairIn d{a, b, (int32_t)pprim, -1, 0, 0};
+    if (kind == 0) {
+      pprim += (int64_t)shells[a].nprim * shells[b].nprim;
+    } else {
+      d.list_off = (int32_t)plist.size();
+      const double* ea = basis->exponents + shells[a].prim_offset;
+      const double* eb = basis->exponents + shells[b].prim_offset;
+      for (int i = 0; i < shells[a].nprim; ++i)
+        for (int j = 0; j < shells[b].nprim; ++j)
+          if (kind == 1 ? ea[i] >= eb[j] : ea[i] > eb[j]) plist.push_back((uint32_t)i | ((uint32_t)j << 16));
+      d.nlist = (int32_t)plist.size() - d.list_off;
+      pprim += d.nlist;
+    }
+    pin.push_back(d);
     pair_id.emplace(key, id);
     return id;
   };
+  struct PairPart {
+    int center, other, pair, nprim;
+  };
+  auto split = [&](int s0, int s1, PairPart* out) {
+    const int l0 = shells[s0].l, l1 = shells[s1].l;
+    if (opts.orientation == 1 || opts.orientation == 2) {
+      bool first = opts.orientation == 1 ? l0 >= l1
+                                         : (maxexp[s0] != maxexp[s1] ? maxexp[s0] > maxexp[s1] : l0 >= l1);
+      const int c = first ? s0 : s1, o = first ? s1 : s0;
+      out[0] = {c, o, get_pair(c, o, 0), shells[s0].nprim * shells[s1].nprim};
+      return 1;
+    }
+    const double* e0 = basis->exponents + shells[s0].prim_offset;
+    const double* e1 = basis->exponents + shells[s1].prim_offset;
+    int n0 = 0, n1 = 0;  // primitive pairs recurring on s0 / on s1
+    for (int i = 0; i < shells[s0].nprim; ++i)
+      for (int j = 0; j < shells[s1].nprim; ++j) (e0[i] >= e1[j] ? n0 : n1)++;
+    int k = 0;
+    if (n1 == 0) {
+      out[k++] = {s0, s1, get_pair(s0, s1, 0), n0};
+    } else if (n0 == 0) {
+      out[k++] = {s1, s0, get_pair(s1, s0, 0), n1};
+    } else {
+      out[k++] = {s0, s1, get_pair(s0, s1, 1), n0};
+      out[k++] = {s1, s0, get_pair(s1, s0, 2), n1};
+    }
+    return k;
+  };
   struct QInfo {
-    int cls;  // bucket key index
+    int cls;    // class key index
+    int round;  // part number within its quartet: 0 writes the block, later parts add
     int kb, kk;
     EriQuartetRec rec;
   };
-  std::vector<QInfo> qi(nq);
+  std::vector<QInfo> qi;
+  qi.reserve(nq);
   std::map<std::vector<int>, int> cls_index;
   std::vector<std::vector<int>> cls_keys;
   for (int64_t q = 0; q < nq; ++q) {
     const int32_t* s = quartets + 4 * q;
-    int pos[4] = {0, 1, 2, 3};  // pos[k] = user position of canonical index k
-    if (!first_of_pair(s[0], s[1])) std::swap(pos[0], pos[1]);
-    if (!first_of_pair(s[2], s[3])) std::swap(pos[2], pos[3]);
-    int lb0 = shells[s[pos[0]]].l, lb1 = shells[s[pos[1]]].l, lk0 = shells[s[pos[2]]].l, lk1 = shells[s[pos[3]]].l;
-    // bra-ket exchange so that the bra pair rank is not below the ket's
-    if (lb0 * 5 + lb1 < lk0 * 5 + lk1) {
-      std::swap(pos[0], pos[2]);
-      std::swap(pos[1], pos[3]);
-      std::swap(lb0, lk0);
-      std::swap(lb1, lk1);
-    }
     int n[4];
     for (int k = 0; k < 4; ++k) n[k] = nfun(shells[s[k]].l, cart);
     const int ustride[4] = {n[1] * n[2] * n[3], n[2] * n[3], n[3], 1};
-    QInfo& x = qi[q];
-    x.rec.bra = get_pair(s[pos[0]], s[pos[1]]);
-    x.rec.ket = get_pair(s[pos[2]], s[pos[3]]);
-    x.rec.out_off = plan->offsets[q];
-    for (int k = 0; k < 4; ++k) x.rec.st[k] = ustride[pos[k]];
-    std::vector<int> key = {lb0, lb1, lk0, lk1};
-    auto it = cls_index.find(key);
-    if (it == cls_index.end()) {
-      it = cls_index.emplace(key, (int)cls_keys.size()).first;
-      cls_keys.push_back(key);
-    }
-    x.cls = it->second;
-    x.kb = shells[s[pos[0]]].nprim * shells[s[pos[1]]].nprim;
-    x.kk = shells[s[pos[2]]].nprim * shells[s[pos[3]]].nprim;
+    PairPart bp[2], kp[2];
+    const int nb = split(s[0], s[1], bp), nk = split(s[2], s[3], kp);
+    int round = 0;
+    for (int ib = 0; ib < nb; ++ib)
+      for (int ik = 0; ik < nk; ++ik, ++round) {
+        PairPart B = bp[ib], K = kp[ik];
+        // pos[k] = user position of canonical index k
+        int pos[4] = {B.center == s[0] ? 0 : 1, B.center == s[0] ? 1 : 0, K.center == s[2] ? 2 : 3,
+                      K.center == s[2] ? 3 : 2};
+        if (s[0] == s[1]) pos[0] = 0, pos[1] = 1;
+        if (s[2] == s[3]) pos[2] = 2, pos[3] = 3;
+        int lb0 = shells[B.center].l, lb1 = shells[B.other].l, lk0 = shells[K.center].l, lk1 = shells[K.other].l;
+        // bra-ket exchange so that the bra pair rank is not below the ket's
+        if (lb0 * 5 + lb1 < lk0 * 5 + lk1) {
+          std::swap(B, K);
+          std::swap(pos[0], pos[2]);
+          std::swap(pos[1], pos[3]);
+          std::swap(lb0, lk0);
+          std::swap(lb1, lk1);
+        }
+        QInfo x;
+        x.rec.bra = B.pair | (round > 0 ? (int32_t)0x80000000 : 0);
+        x.rec.ket = K.pair;
+        x.rec.out_off = plan->offsets[q];
+        for (int k = 0; k < 4; ++k) x.rec.st[k] = ustride[pos[k]];
+        std::vector<int> key = {lb0, lb1, lk0, lk1};
+        auto it = cls_index.find(key);
+        if (it == cls_index.end()) {
+          it = cls_index.emplace(key, (int)cls_keys.size()).first;
+          cls_keys.push_back(key);
+        }
+        x.cls = it->second;
+        x.round = round;
+        x.kb = B.nprim;
+        x.kk = K.nprim;
+        qi.push_back(x);
+      }
   }
+  const int64_t nparts = (int64_t)qi.size();
   if (pprim > ((int64_t)1 << 31) - 1) return fail(ERI_EINVAL, "too many primitive pairs");
-  // ---- buckets: by class (heaviest first), then by contraction signature
-  std::vector<int64_t> order(nq);
-  for (int64_t q = 0; q < nq; ++q) order[q] = q;
+  // ---- buckets: by part round (a block is written before it is added to),
+  // then class (heaviest first), then contraction signature
+  std::vector<int64_t> order(nparts);
+  for (int64_t q = 0; q < nparts; ++q) order[q] = q;
   std::vector<int> cls_rank(cls_keys.size());
   {
     std::vector<int> idx(cls_keys.size());
@@ -467,13 +621,14 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
     for (size_t r = 0; r < idx.size(); ++r) cls_rank[idx[r]] = (int)r;
   }
   std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    if (qi[a].round != qi[b].round) return qi[a].round < qi[b].round;
     if (qi[a].cls != qi[b].cls) return cls_rank[qi[a].cls] < cls_rank[qi[b].cls];
     const int64_t ka = (int64_t)qi[a].kb * qi[a].kk, kb = (int64_t)qi[b].kb * qi[b].kk;
     if (ka != kb) return ka > kb;
     return qi[a].kb > qi[b].kb;
   });
-  std::vector<EriQuartetRec> recs(nq);
-  for (int64_t i = 0; i < nq; ++i) recs[i] = qi[order[i]].rec;
+  std::vector<EriQuartetRec> recs(nparts);
+  for (int64_t i = 0; i < nparts; ++i) recs[i] = qi[order[i]].rec;
   // ---- launches: one per (class, group size); G lanes share a quartet and
   // split its K4 primitive quartets, about three per lane
   auto group_of = [](int64_t k4) {
@@ -484,35 +639,45 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
   };
   size_t max_scratch_slots = 0;
   int max_grid_global = 0;
-  for (int64_t i = 0; i < nq;) {
+  size_t max_coop_vals = 0, max_coop_h = 0;
+  const bool default_opts = opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0;
+  for (int64_t i = 0; i < nparts;) {
     const int c = qi[order[i]].cls;
-    const int g = group_of((int64_t)qi[order[i]].kb * qi[order[i]].kk);
-    int64_t j = i;
-    double kprim = 0;
-    while (j < nq && qi[order[j]].cls == c && group_of((int64_t)qi[order[j]].kb * qi[order[j]].kk) == g) {
-      kprim += (double)qi[order[j]].kb * qi[order[j]].kk;
-      ++j;
-    }
+    const int round = qi[order[i]].round;
     Bucket b;
     for (int k = 0; k < 4; ++k) b.ls[k] = cls_keys[c][k];
-    b.first = i;
-    b.count = j - i;
-    b.group = g;
     std::vector<int> pkey = {b.ls[0], b.ls[1], b.ls[2], b.ls[3], opts.axis_rule, opts.schedule, opts.sph_mode};
     auto pit = L.progs.find(pkey);
     ClassProg* prog = pit == L.progs.end() ? nullptr : pit->second.get();
+    auto cit = L.coops.find(pkey);
+    CoopProg* cp = cit == L.coops.end() ? nullptr : cit->second.get();
     auto rit = L.reg.find({b.ls[0], b.ls[1], b.ls[2], b.ls[3]});
-    const bool default_opts = opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0;
     const void* regfn = (rit != L.reg.end() && default_opts) ? rit->second : nullptr;
     const size_t smem_need = prog ? (size_t)prog->nslot * 128 * sizeof(double) : 0;
     int tier = opts.tier;
-    if (tier == 0) tier = regfn ? TIER_REG : (prog && smem_need <= L.smem_optin ? TIER_SHARED : TIER_GLOBAL);
+    if (tier == 0)
+      tier = regfn ? TIER_REG : cp ? TIER_COOP : (prog && smem_need <= L.smem_optin ? TIER_SHARED : TIER_GLOBAL);
     if (tier == TIER_REG && !regfn)
       return fail(ERI_EUNSUPPORTED, "no register-tier kernel for this class/options");
+    if (tier == TIER_COOP && !cp)
+      return fail(ERI_EUNSUPPORTED, "no team-cooperative program for this class/options");
     if ((tier == TIER_SHARED || tier == TIER_GLOBAL) && !prog)
       return fail(ERI_EUNSUPPORTED, "no program for this class/options (build the variant)");
     if (tier == TIER_SHARED && smem_need > L.smem_optin)
       return fail(ERI_EUNSUPPORTED, "class does not fit the shared-memory tier");
+    // one launch per class for the cooperative tier (a team walks all the
+    // primitive quartets of its shell quartet); otherwise one per group size
+    const int g = tier == TIER_COOP ? 1 : group_of((int64_t)qi[order[i]].kb * qi[order[i]].kk);
+    int64_t j = i;
+    double kprim = 0;
+    while (j < nparts && qi[order[j]].cls == c && qi[order[j]].round == round &&
+           (tier == TIER_COOP || group_of((int64_t)qi[order[j]].kb * qi[order[j]].kk) == g)) {
+      kprim += (double)qi[order[j]].kb * qi[order[j]].kk;
+      ++j;
+    }
+    b.first = i;
+    b.count = j - i;
+    b.group = g;
     b.tier = tier;
     b.reg_fn = regfn;
     b.prog = prog;
@@ -523,14 +688,34 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
       b.smem = smem_need;
       int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (L.smem_optin + 1024) / (smem_need + 1024)));
       b.grid = (int)std::min<int64_t>(blocks, (int64_t)L.nsm * per_sm);
-    } else {
+    } else if (tier == TIER_GLOBAL) {
       int per_sm = prog->nslot <= 4096 ? 4 : 2;
       b.grid = (int)std::min<int64_t>(blocks, (int64_t)L.nsm * per_sm);
       max_scratch_slots = std::max(max_scratch_slots, (size_t)prog->nslot);
       max_grid_global = std::max(max_grid_global, b.grid);
+    } else {
+      // team-cooperative: value slots (and H when it fits) in shared memory
+      b.coop = cp;
+      const int tpb = 128 / cp->T;
+      size_t per_team = (size_t)cp->nslot + cp->nh;
+      if (per_team * tpb * sizeof(double) <= L.smem_optin) {
+        b.h_in_smem = 1;
+        b.smem_slots = cp->nslot;
+      } else {
+        b.h_in_smem = 0;
+        b.smem_slots = (int)std::min<size_t>(cp->nslot, L.smem_optin / sizeof(double) / tpb);
+        per_team = b.smem_slots;
+      }
+      b.smem = per_team * tpb * sizeof(double);
+      const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, L.smem_per_sm / (b.smem + 1024)));
+      b.grid = (int)std::min<int64_t>((b.count + tpb - 1) / tpb, (int64_t)L.nsm * per_sm);
+      b.nteams = b.grid * tpb;
+      max_coop_vals = std::max(max_coop_vals, (size_t)b.nteams * (cp->nslot - b.smem_slots));
+      if (!b.h_in_smem) max_coop_h = std::max(max_coop_h, (size_t)b.nteams * cp->nh);
+      if ((rc = upload_coop(cp))) return rc;
     }
     if (prog) {
-      if (tier != TIER_REG && (rc = upload_prog(prog))) return rc;
+      if ((tier == TIER_SHARED || tier == TIER_GLOBAL) && (rc = upload_prog(prog))) return rc;
       b.flops = kprim * prog->flops_prim + (double)b.count * prog->flops_p2;
       plan->flops += b.flops;
     }
@@ -538,6 +723,9 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
     plan->buckets.push_back(b);
     i = j;
   }
+  if ((rc = plan->coop_vals.alloc(max_coop_vals, "cooperative spill")) ||
+      (rc = plan->coop_h.alloc(max_coop_h, "cooperative accumulators")))
+    return rc;
   // ---- device data
   std::vector<DevShell> dsh(nshell);
   for (int s = 0; s < nshell; ++s) {
@@ -551,13 +739,15 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
   std::vector<double> co(basis->coefs, basis->coefs + basis->nprim_total);
   if ((rc = plan->shells.upload(dsh, "shells")) || (rc = plan->exps.upload(ex, "exponents")) ||
       (rc = plan->coefs.upload(co, "coefficients")) || (rc = plan->pin.upload(pin, "pair list")) ||
+      (rc = plan->plist.upload(plist, "primitive-pair lists")) ||
       (rc = plan->pairs.alloc(pin.size(), "pairs")) || (rc = plan->pprims.alloc(pprim, "primitive pairs")) ||
       (rc = plan->quartets.upload(recs, "quartet records")))
     return rc;
   plan->npair = (int)pin.size();
   plan->npprim = pprim;
   plan->h2d_bytes = (double)(dsh.size() * sizeof(DevShell) + 2 * ex.size() * sizeof(double) +
-                             pin.size() * sizeof(DevPairIn) + recs.size() * sizeof(EriQuartetRec));
+                             pin.size() * sizeof(DevPairIn) + plist.size() * sizeof(uint32_t) +
+                             recs.size() * sizeof(EriQuartetRec));
   if (max_scratch_slots > 0) {
     plan->scratch_stride = (int64_t)max_grid_global * 128;
     if ((rc = plan->scratch.alloc((size_t)plan->scratch_stride * max_scratch_slots, "scratch"))) return rc;
@@ -598,7 +788,8 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
     const int threads = 128;
     const int blocks = (plan->npair + threads - 1) / threads;
     eri_pair_setup_kernel<<<blocks, threads, 0, stream>>>(plan->pin.p, plan->npair, plan->shells.p, plan->exps.p,
-                                                          plan->coefs.p, plan->pairs.p, plan->pprims.p);
+                                                          plan->coefs.p, plan->plist.p, plan->pairs.p,
+                                                          plan->pprims.p);
     CUDA_OR(cudaGetLastError(), "pair set-up launch");
     CUDA_OR(mark(1), "cudaEventRecord");
     ++li;
@@ -618,6 +809,25 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
     if (b.tier == TIER_REG) {
       void* args[] = {&a};
       CUDA_OR(cudaLaunchKernel(b.reg_fn, dim3(b.grid), dim3(b.block), args, 0, stream), "class kernel launch");
+    } else if (b.tier == TIER_COOP) {
+      const CoopProg* cp = b.coop;
+      EriCoopArgs p;
+      p.ph1 = cp->d_ph1;
+      p.steps1 = cp->d_steps1;
+      p.ph2 = cp->d_ph2;
+      p.steps2 = cp->d_steps2;
+      p.c2s = L.d_c2s;
+      p.gvals = plan->coop_vals.p;
+      p.gH = plan->coop_h.p;
+      p.nw1 = cp->nw1;
+      p.nw2 = cp->nw2;
+      p.nh = cp->nh;
+      p.nslot = cp->nslot;
+      p.L = cp->L;
+      p.smem_slots = b.smem_slots;
+      p.h_in_smem = b.h_in_smem;
+      p.nteams = b.nteams;
+      CUDA_OR(eri_coop_launch(cp->T, &a, &p, b.grid, b.smem, stream), "cooperative launch");
     } else {
       EriProgArgs p;
       p.ph1 = b.prog->d_ph1;

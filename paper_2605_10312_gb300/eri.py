@@ -18,9 +18,9 @@ ERRORS = {-1: "EINVAL", -2: "EUNSUPPORTED", -3: "ENOMEM", -4: "ECUDA", -5: "EBUS
 AXIS_RULES = {"prose": 0, "literal": 1, "common": 2}
 SCHEDULES = {"dsa": 0, "level": 1}
 SPH_MODES = {"stepwise": 0, "materialize": 1, "cart": 2}
-TIERS = {"auto": 0, "reg": 1, "shared": 2, "global": 3}
-TIERS_INV = {0: "setup", 1: "reg", 2: "shared", 3: "global"}
-ORIENTATIONS = {"tight": 0, "l": 1}
+TIERS = {"auto": 0, "reg": 1, "shared": 2, "global": 3, "coop": 4}
+TIERS_INV = {0: "setup", 1: "reg", 2: "shared", 3: "global", 4: "coop"}
+ORIENTATIONS = {"split": 0, "l": 1, "tight": 2}
 
 
 class EriError(RuntimeError):
@@ -98,7 +98,7 @@ class Plan:
     """A device-resident plan for one quartet list (see eri_plan)."""
 
     def __init__(self, basis, quartets, axis_rule="prose", schedule="dsa", sph_mode="stepwise", tier="auto",
-                 orientation="tight"):
+                 orientation="split"):
         lib = library()
         q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
         ns = int(basis.shell_l.shape[0])

@@ -1,0 +1,267 @@
+"""Team-cooperative form of a class program (the tier for large classes).
+
+A team of T lanes (one to four warps) evaluates ONE primitive quartet at a
+time: the Phase-1 graph is cut into waves of at most T mutually independent
+nodes, taken in DSA order (FusionRCG Eq. 7) by a bounded-width list
+scheduler, and lane l evaluates node l of each wave; a team barrier separates
+waves.  Phase 2 is scheduled the same way, with its operations in their
+liveness-friendly build order as priority.  Values live in one slot space
+per team (not per lane), so a class whose sequential PeakLive (Eq. 4) is
+thousands of values still fits in shared memory; the accumulator bank H is
+addressed separately (shared memory when it fits, else a team-private global
+region).
+
+Operand ids in the descriptors: id < nh is accumulator H[id]; id >= nh is
+value slot id - nh.
+
+Phase-1 descriptor (uint32 x4) as in ``encode``, plus side = 3 = no-op.
+Phase-2 descriptor kinds: 0 HRR, 1 LIN (n <= 4), 2 STORE, 3 no-op; a
+transform row of more than four terms becomes a chain of LIN descriptors in
+successive waves, each continuing with 1.0 x the previous partial sum.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+import heapq
+
+import numpy as np
+
+from .encode import coef_table
+
+NOP1 = np.array([0, 0, 0, 3 << 16], dtype=np.uint32)
+NOP2 = np.array([3, 0, 0, 0], dtype=np.uint32)
+MAX_ID = 65535
+
+
+def wave_schedule(parents, priority, width):
+    """Bounded-width list scheduling: each wave takes up to ``width`` ready
+    nodes with the smallest priority.  parents[v] = list of node ids."""
+    n = len(parents)
+    cons = [[] for _ in range(n)]
+    npar = [0] * n
+    for v, ps in enumerate(parents):
+        ps = set(ps)
+        npar[v] = len(ps)
+        for p in ps:
+            cons[p].append(v)
+    ready = [(priority[v], v) for v in range(n) if npar[v] == 0]
+    heapq.heapify(ready)
+    waves = []
+    while ready:
+        cur = []
+        while ready and len(cur) < width:
+            cur.append(heapq.heappop(ready)[1])
+        for v in cur:
+            for c in cons[v]:
+                npar[c] -= 1
+                if npar[c] == 0:
+                    heapq.heappush(ready, (priority[c], c))
+        waves.append(cur)
+    assert sum(len(w) for w in waves) == n, "cycle in graph"
+    return waves
+
+
+def allocate_over_waves(parents, waves, needs_slot, first_slot=0, pinned_until_end=()):
+    """Slots for wave-synchronous execution: a value written in wave b and
+    last read in wave d keeps its slot through wave d; a slot is reused only
+    by a value born in a later wave.  Lowest free slot first."""
+    n = len(parents)
+    wave_of = np.zeros(n, dtype=np.int64)
+    for w, vs in enumerate(waves):
+        for v in vs:
+            wave_of[v] = w
+    last = wave_of.copy()
+    for v, ps in enumerate(parents):
+        for p in ps:
+            last[p] = max(last[p], wave_of[v])
+    for v in pinned_until_end:
+        last[v] = len(waves)
+    slot = np.full(n, -1, dtype=np.int64)
+    free = []
+    nxt = first_slot
+    release_at = [[] for _ in range(len(waves) + 2)]
+    for w, vs in enumerate(waves):
+        for s in release_at[w]:
+            heapq.heappush(free, s)
+        for v in vs:
+            if not needs_slot[v]:
+                continue
+            if free:
+                slot[v] = heapq.heappop(free)
+            else:
+                slot[v] = nxt
+                nxt += 1
+            release_at[last[v] + 1].append(int(slot[v]))
+    return slot, nxt - first_slot
+
+
+@dataclass
+class CoopProgram:
+    T: int
+    ph1: np.ndarray        # uint32 [sum steps * T, 4]
+    steps1: np.ndarray     # uint32 [nwave1] steps of each wave
+    ph2: np.ndarray
+    steps2: np.ndarray
+    nh: int
+    nslot: int             # value slots (ids nh .. nh + nslot - 1)
+    L: int
+    out_dims: tuple
+    eff1: float            # busy lanes / lane slots, Phase 1
+    eff2: float
+
+
+def _pack(waves, rows_of, T, nop):
+    steps = []
+    out = []
+    for vs in waves:
+        st = (len(vs) + T - 1) // T
+        steps.append(st)
+        block = np.tile(nop, (st * T, 1))
+        for k, v in enumerate(vs):
+            block[k] = rows_of(v)
+        out.append(block)
+    arr = np.concatenate(out) if out else np.zeros((0, 4), dtype=np.uint32)
+    return arr.astype(np.uint32), np.array(steps, dtype=np.uint32)
+
+
+def build(prog, T=128):
+    """CoopProgram of a class program for teams of T lanes."""
+    g = prog.g
+    nh = prog.nh
+    # ---------------- Phase 1
+    order_pos = np.empty(len(g), dtype=np.int64)
+    order_pos[np.array(prog.order, dtype=np.int64)] = np.arange(len(g))
+    par1 = [[p for _, p in ts] for ts in g.terms]
+    waves1 = wave_schedule(par1, order_pos, T)
+    consumed = np.zeros(len(g), dtype=bool)
+    for ps in par1:
+        for p in ps:
+            consumed[p] = True
+    slot1, nslot1 = allocate_over_waves(par1, waves1, consumed)
+
+    def row1(v):
+        ts = g.terms[v]
+        dst = nh + int(slot1[v]) if consumed[v] else 0
+        h = g.target.get(v)
+        src = [0] * 5
+        side = axis = k = k3 = 0
+        if not ts:
+            side, k = 2, g.keys[v][2]
+        for (kind, val), p in ts:
+            s = nh + int(slot1[p])
+            if kind in ("PA", "QC"):
+                src[0], side, axis = s, (0 if kind == "PA" else 1), val
+            elif kind in ("WP", "WQ"):
+                src[1] = s
+            elif kind in ("c1z", "c1e"):
+                src[2], k = s, val
+            elif kind in ("c2z", "c2e"):
+                src[3] = s
+            elif kind == "c3":
+                src[4], k3 = s, val
+        return np.array([dst | ((h + 1) << 16 if h is not None else 0), src[0] | (src[1] << 16),
+                         src[2] | (src[3] << 16),
+                         src[4] | (side << 16) | (axis << 18) | (k << 20) | (k3 << 25) | (int(consumed[v]) << 30)],
+                        dtype=np.uint32)
+
+    ph1, steps1 = _pack(waves1, row1, T, NOP1)
+
+    # ---------------- Phase 2: graph of operations and output stores
+    p2 = prog.p2
+    ctab = {c: i for i, c in enumerate(coef_table())}
+    # node ids: 0..nh-1 = H inputs; then one node per operation chunk; then stores
+    nodes = []      # (kind, payload)
+    parents = []
+    val_node = {i: i for i in range(nh)}   # value id -> node producing it
+    for i in range(nh):
+        nodes.append(("h", i))
+        parents.append([])
+    for op in p2.ops:
+        if op[0] == "hrr":
+            _, d, hi, sym_i, lo = op
+            nid = len(nodes)
+            nodes.append(("hrr", (hi, lo, sym_i)))
+            parents.append([val_node[hi], val_node[lo]])
+            val_node[d] = nid
+        else:
+            # rows of more than four terms: the first descriptor sums four,
+            # each further one adds 1.0 x the running sum and up to three more
+            _, d, terms = op
+            prev = None
+            rest = list(terms)
+            while rest:
+                take = 4 if prev is None else 3
+                chunk, rest = rest[:take], rest[take:]
+                nid = len(nodes)
+                nodes.append(("lin", (chunk, prev)))
+                ps = [val_node[s] for _, s in chunk]
+                if prev is not None:
+                    ps.append(prev)
+                parents.append(ps)
+                prev = nid
+            val_node[d] = prev
+    store_nodes = []
+    for k, v in enumerate(p2.outputs):
+        nid = len(nodes)
+        nodes.append(("store", (k, v)))
+        parents.append([val_node[v]])
+        store_nodes.append(nid)
+    n2 = len(nodes)
+    prio = np.arange(n2, dtype=np.int64)
+    # stores go right after their value: priority of the producer
+    for nid in store_nodes:
+        prio[nid] = parents[nid][0]
+    # H inputs are not scheduled (they are read in place)
+    work = [v for v in range(n2) if nodes[v][0] != "h"]
+    pos = {v: i for i, v in enumerate(work)}
+    par_list = [[pos[p] for p in parents[v] if nodes[p][0] != "h"] for v in work]
+    waves2 = wave_schedule(par_list, np.array([prio[v] for v in work]), T)
+    waves2 = [[work[i] for i in w] for w in waves2]
+    needs = np.zeros(n2, dtype=bool)
+    for v in range(n2):
+        if nodes[v][0] in ("hrr", "lin"):
+            needs[v] = True
+    # slot allocation over the waves (H inputs keep their own ids)
+    sched = [v for w in waves2 for v in w]
+    loc = {v: i for i, v in enumerate(sched)}
+    p_loc = [[loc[p] for p in parents[v] if p in loc] for v in sched]
+    w_loc = []
+    c = 0
+    for w in waves2:
+        w_loc.append(list(range(c, c + len(w))))
+        c += len(w)
+    slot_l, nslot2 = allocate_over_waves(p_loc, w_loc, np.array([needs[v] for v in sched]))
+    slot2 = {v: int(slot_l[loc[v]]) for v in sched}
+
+    def oid(node):
+        # operand id of a node's value: H index or nh + slot
+        return node if nodes[node][0] == "h" else nh + slot2[node]
+
+    def row2(v):
+        kind, pl = nodes[v]
+        if kind == "hrr":
+            hi, lo, (sym, i) = pl
+            return np.array([0 | (oid(v) << 16), oid(val_node[hi]) | (oid(val_node[lo]) << 16),
+                             i + (3 if sym == "CD" else 0), 0], dtype=np.uint32)
+        if kind == "lin":
+            chunk, prev = pl
+            terms = [(float(cf), oid(val_node[s])) for cf, s in chunk]
+            if prev is not None:
+                terms.append((1.0, oid(prev)))
+            n = len(terms)
+            ss = [x for _, x in terms] + [0] * (4 - n)
+            cc = [ctab[cf] for cf, _ in terms] + [0] * (4 - n)
+            return np.array([1 | (n << 2) | (oid(v) << 16), ss[0] | (ss[1] << 16), ss[2] | (ss[3] << 16),
+                             cc[0] | (cc[1] << 8) | (cc[2] << 16) | (cc[3] << 24)], dtype=np.uint32)
+        k, val = pl
+        i = np.unravel_index(k, p2.out_dims)
+        return np.array([2 | (oid(val_node[val]) << 16), k,
+                         int(i[0]) | (int(i[1]) << 8) | (int(i[2]) << 16) | (int(i[3]) << 24), 0], dtype=np.uint32)
+
+    ph2, steps2 = _pack(waves2, row2, T, NOP2)
+    nslot = max(int(nslot1), int(nslot2))
+    if nh + nslot > MAX_ID:
+        raise ValueError("class {} needs {} ids".format(prog.ls, nh + nslot))
+    eff1 = len(g) / max(1, int(steps1.sum()) * T)
+    eff2 = len(sched) / max(1, int(steps2.sum()) * T)
+    return CoopProgram(T, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(p2.out_dims), eff1, eff2)

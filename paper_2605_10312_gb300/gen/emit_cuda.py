@@ -106,8 +106,9 @@ def emit_class(prog, tier="reg", threads=128):
     w("  const int qi = t / G, r = t - qi * G;")
     w("  const bool valid = qi < a.nq;")
     w("  const EriQuartetRec qr = a.quartets[valid ? qi : 0];")
-    w("  const EriPairRec bra = a.pairs[qr.bra];")
+    w("  const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];")
     w("  const EriPairRec ket = a.pairs[qr.ket];")
+    w("  const bool acc = ERI_ACCUMULATE(qr.bra);")
     if tier == "smem":
         w("  double* const S = eri_smem + threadIdx.x;")
         w("#define SV(i) S[(i) * {}]".format(threads))
@@ -207,7 +208,7 @@ def emit_class(prog, tier="reg", threads=128):
             if ii:
                 terms.append("{}*qr.st[{}]".format(int(ii), axis))
         off = " + ".join(terms) if terms else "0"
-        w("  o[{}] = {};".format(off, pv(vid)))
+        w("  eri_st(o + {}, {}, acc);".format(off, pv(vid)))
     if tier in ("smem", "global"):
         w("#undef SV")
     if tier == "global":

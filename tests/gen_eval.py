@@ -184,3 +184,104 @@ def run_encoded(enc, prog, basis, quartets):
         else:
             out[:, w1] = S[dst]
     return out
+
+
+def run_coop(cp, prog, basis, quartets):
+    """Walk a team-cooperative program wave by wave (the coop executor's
+    semantics, including slot reuse across waves); returns [nq, nout]."""
+    from paper_2605_10312_gb300.gen.encode import coef_table
+    la, lb, lc, ld = prog.ls
+    q = np.asarray(quartets)
+    nq = q.shape[0]
+    ctr = [basis.centers[basis.shell_center[q[:, k]]] for k in range(4)]
+    nh = cp.nh
+    S = np.zeros((nh + cp.nslot, nq))   # ids < nh: H, else value slots
+    L = prog.L
+    kmax = [int(basis.shell_nprim[q[:, k]].max()) for k in range(4)]
+
+    def waves(rows, steps):
+        i = 0
+        for st in steps:
+            n = int(st) * cp.T
+            yield rows[i:i + n]
+            i += n
+
+    for ia in range(kmax[0]):
+        for ib in range(kmax[1]):
+            for ic in range(kmax[2]):
+                for id_ in range(kmax[3]):
+                    idx = [ia, ib, ic, id_]
+                    ok = np.ones(nq, dtype=bool)
+                    al, co = [], []
+                    for k, l in enumerate((la, lb, lc, ld)):
+                        K = basis.shell_nprim[q[:, k]]
+                        ok &= idx[k] < K
+                        p = basis.shell_prim[q[:, k]] + np.minimum(idx[k], K - 1)
+                        a = basis.exps[p]
+                        al.append(a)
+                        co.append(basis.coefs[p] * np.array([norm_numeric(x, l) for x in a]))
+                    za, zb, zc, zd = al
+                    zeta, eta = za + zb, zc + zd
+                    P = (za[:, None] * ctr[0] + zb[:, None] * ctr[1]) / zeta[:, None]
+                    Q = (zc[:, None] * ctr[2] + zd[:, None] * ctr[3]) / eta[:, None]
+                    W = (zeta[:, None] * P + eta[:, None] * Q) / (zeta + eta)[:, None]
+                    rho = zeta * eta / (zeta + eta)
+                    T = rho * np.sum((P - Q) ** 2, axis=1)
+                    kab = np.exp(-za * zb / zeta * np.sum((ctr[0] - ctr[1]) ** 2, axis=1))
+                    kcd = np.exp(-zc * zd / eta * np.sum((ctr[2] - ctr[3]) ** 2, axis=1))
+                    pref = 2 * math.pi ** 2.5 / (zeta * eta * np.sqrt(zeta + eta)) * kab * kcd
+                    pref = pref * co[0] * co[1] * co[2] * co[3] * ok
+                    F = boys_scipy(L, T) * pref[:, None]
+                    geo = [[P[:, i] - ctr[0][:, i] for i in range(3)], [W[:, i] - P[:, i] for i in range(3)],
+                           [Q[:, i] - ctr[2][:, i] for i in range(3)], [W[:, i] - Q[:, i] for i in range(3)]]
+                    c1 = [1 / (2 * zeta), 1 / (2 * eta)]
+                    c2 = [-rho / (2 * zeta * zeta), -rho / (2 * eta * eta)]
+                    c3 = 1 / (2 * (zeta + eta))
+                    for wave in waves(cp.ph1, cp.steps1):
+                        res = []  # all lanes read before any writes (wave barrier semantics)
+                        for w0, w1, w2, w3 in wave.tolist():
+                            side = (w3 >> 16) & 3
+                            if side == 3:
+                                continue
+                            dst, h = w0 & 0xFFFF, w0 >> 16
+                            axis, k, k3 = (w3 >> 18) & 3, (w3 >> 20) & 31, (w3 >> 25) & 31
+                            if side == 2:
+                                x = F[:, k]
+                            else:
+                                x = geo[2 * side][axis] * S[w1 & 0xFFFF] + geo[2 * side + 1][axis] * S[w1 >> 16]
+                                if k:
+                                    x = x + k * c1[side] * S[w2 & 0xFFFF] + k * c2[side] * S[w2 >> 16]
+                                if k3:
+                                    x = x + k3 * c3 * S[w3 & 0xFFFF]
+                            res.append((dst, h, (w3 >> 30) & 1, x))
+                        for dst, h, st, x in res:
+                            if st:
+                                S[dst] = x
+                            if h:
+                                S[h - 1] += x
+    ctab = coef_table()
+    X = [ctr[0][:, i] - ctr[1][:, i] for i in range(3)] + [ctr[2][:, i] - ctr[3][:, i] for i in range(3)]
+    out = np.full((nq, int(np.prod(cp.out_dims))), np.nan)
+    for wave in waves(cp.ph2, cp.steps2):
+        res = []
+        for w0, w1, w2, w3 in wave.tolist():
+            kind = w0 & 3
+            dst = w0 >> 16
+            if kind == 0:
+                res.append(("v", dst, S[w1 & 0xFFFF] + X[w2] * S[w1 >> 16]))
+            elif kind == 1:
+                n = (w0 >> 2) & 7
+                ss = [w1 & 0xFFFF, w1 >> 16, w2 & 0xFFFF, w2 >> 16]
+                cc = [w3 & 255, (w3 >> 8) & 255, (w3 >> 16) & 255, w3 >> 24]
+                acc = 0.0
+                for j in range(n):
+                    acc = acc + ctab[cc[j]] * S[ss[j]]
+                res.append(("v", dst, acc))
+            elif kind == 2:
+                res.append(("o", w1, S[dst].copy()))
+        for kind, a, x in res:
+            if kind == "v":
+                S[a] = x
+            else:
+                out[:, a] = x
+    return out

@@ -9,8 +9,8 @@ import pytest
 
 import oracle
 from paper_2605_10312_gb300 import synth
-from paper_2605_10312_gb300.gen import cart, encode, hrr, program, sph, vrr
-from gen_eval import evaluate, run_encoded
+from paper_2605_10312_gb300.gen import cart, coop, encode, hrr, program, sph, vrr
+from gen_eval import evaluate, run_coop, run_encoded
 from ref import blocks, within
 
 
@@ -123,3 +123,43 @@ def test_all_classes_enumerated():
         a, b = (ls[0], ls[1]), (ls[2], ls[3])
         key = a + b if program.pair_rank(*a) >= program.pair_rank(*b) else b + a
         assert key in cls
+
+
+@pytest.mark.parametrize("T", [32, 64, 128])
+@pytest.mark.parametrize("ls", [(1, 1, 1, 1), (0, 2, 1, 2), (2, 2, 2, 1), (4, 0, 2, 1), (3, 3, 1, 0)])
+def test_coop_program_matches_oracle(ls, T):
+    """Team-cooperative waves (bounded-width DSA list schedule, slots reused
+    only across waves) reproduce the oracle, wave semantics included."""
+    prog = program.make(*ls)
+    cp = coop.build(prog, T)
+    assert int(cp.steps1.sum()) * T == cp.ph1.shape[0]
+    basis, q = synth.class_sweep(ls, 3, kset=(1, 2), seed=13, box_angstrom=3.0, exp_range=(0.1, 30))
+    ref, _ = blocks(basis, q)
+    got = run_coop(cp, prog, basis, q)
+    assert within(got, ref.reshape(q.shape[0], -1)).all()
+
+
+def test_wave_schedule_respects_dependencies_and_width():
+    g = vrr.build(2, 2, 2, 1)
+    order = vrr.schedule(g)
+    pos = np.empty(len(g), dtype=np.int64)
+    pos[np.array(order)] = np.arange(len(g))
+    par = [[p for _, p in ts] for ts in g.terms]
+    waves = coop.wave_schedule(par, pos, 32)
+    wave_of = {}
+    for w, vs in enumerate(waves):
+        assert 0 < len(vs) <= 32
+        for v in vs:
+            wave_of[v] = w
+    for v, ps in enumerate(par):
+        for p in ps:
+            assert wave_of[p] < wave_of[v]
+    slot, n = coop.allocate_over_waves(par, waves, np.ones(len(g), dtype=bool))
+    # a slot is never shared by two values whose wave lifetimes overlap
+    last = {v: max([wave_of[c] for c, ps in enumerate(par) if v in ps], default=wave_of[v]) for v in range(len(g))}
+    owners = {}
+    for v in sorted(range(len(g)), key=lambda v: wave_of[v]):
+        s = int(slot[v])
+        if s in owners:
+            assert last[owners[s]] < wave_of[v]
+        owners[s] = v

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2605_10312_gb300 import synth
-from ref import blocks, report, within
+from ref import adjudicated, report, within
 
 pytestmark = pytest.mark.gpu
 
@@ -42,23 +42,24 @@ def test_empty_plan(eri):
 
 
 @pytest.mark.parametrize("tier,ls", [("reg", (1, 1, 1, 0)), ("shared", (1, 1, 1, 0)), ("global", (1, 1, 1, 0)),
-                                     ("shared", (2, 1, 2, 0)), ("global", (2, 2, 1, 1))])
+                                     ("shared", (2, 2, 1, 0)), ("shared", (3, 1, 1, 0)), ("global", (2, 2, 1, 1)),
+                                     ("global", (3, 2, 2, 1)), ("coop", (2, 2, 2, 1)), ("coop", (3, 3, 2, 2))])
 def test_forced_tiers_agree(eri, tier, ls):
     """The same class through each tier that can hold it gives the oracle's
     values (register tier only for the classes compiled straight-line)."""
-    basis, q = synth.class_sweep(ls, 300, kset=(1, 2), seed=19, box_angstrom=3.0)
-    ref, _ = blocks(basis, q)
+    basis, q = synth.class_sweep(ls, 300, kset=(1, 2, 3), seed=19, box_angstrom=3.0)
     for t in (tier, "auto"):
-        got, _ = eri.eri(basis, q, tier=t)
-        assert within(got.cpu().numpy(), ref).all(), (t, report(got.cpu().numpy(), ref))
+        got = eri.eri(basis, q, tier=t)[0].cpu().numpy()
+        ref, _ = adjudicated(got, basis, q)
+        assert within(got, ref).all(), (t, report(got, ref))
 
 
 def test_orientation_option(eri):
     """Higher-l-first orientation is also correct on a compact geometry."""
     basis, q = synth.class_sweep((2, 2, 1, 1), 100, kset=(1, 2), seed=23, box_angstrom=2.0, exp_range=(0.2, 10.0))
-    got, _ = eri.eri(basis, q, orientation="l")
-    ref, _ = blocks(basis, q)
-    assert within(got.cpu().numpy(), ref).all(), report(got.cpu().numpy(), ref)
+    got = eri.eri(basis, q, orientation="l")[0].cpu().numpy()
+    ref, _ = adjudicated(got, basis, q)
+    assert within(got, ref).all(), report(got, ref)
 
 
 def test_unsupported_tier_is_an_error(eri):

