@@ -128,6 +128,30 @@ int eri_plan_launch_count(const eri_plan_t* plan);
  * the stream must have completed.  Any output pointer may be NULL. */
 int eri_plan_launch_info(const eri_plan_t* plan, int i, int32_t* info, double* flops, float* ms);
 
+/* Evaluate like eri_compute without allocating: for callers that may not
+ * allocate device memory while they evaluate (stream capture without
+ * graph-safe allocation, or a device-memory budget owned by another
+ * framework).  The paper has no counterpart; this is a deployment entry
+ * point.  The plan must have been built with opts.tier = 3 (global-scratch
+ * program tier); its kernels then take their per-thread value slots from a
+ * fixed 64 MiB device array that the library holds on every GPU that loads it
+ * until the process exits, so the call itself performs no cudaMalloc,
+ * cudaFree or other allocation.  Inputs are the plan's device data, out is
+ * the caller's device buffer as for eri_compute.
+ *  - Sizes: a class needing more than 64 MiB for one 128-thread block
+ *    (nslot x 128 x 8 bytes) is rejected with ERI_EINVAL; otherwise the grid
+ *    is reduced to what the array holds, and the kernels stride over the
+ *    remaining quartets (slower, same results).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and the kernels reinitialise what they
+ *    read (accumulators are zeroed per quartet), so nothing is carried
+ *    between calls; calls that overlap on the GPU (other streams, other
+ *    host threads) race on the array and must be serialised by the caller.
+ * Returns ERI_EUNSUPPORTED for a plan with non-global tiers. */
+int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* stream);
+
 /* Release the plan and its device memory (synchronises the device first). */
 int eri_plan_destroy(eri_plan_t* plan);
 

@@ -919,3 +919,96 @@ extern "C" int eri_plan_destroy(eri_plan_t* plan) {
   delete plan;
   return ERI_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free evaluation (eri_compute_fixed_scratch)
+//
+// Some callers must not allocate device memory when they evaluate: code that
+// runs while a stream is being captured into a CUDA graph without
+// graph-safe allocation, or code whose device memory is budgeted and owned by
+// another framework.  For them the global-scratch program tier can take its
+// per-thread value slots from this fixed array instead of the plan's
+// scratch.  The array is a file-scope device variable: every GPU that loads
+// the library holds its 64 MiB until the process exits.
+// ---------------------------------------------------------------------------
+#define ERI_FIXED_SCRATCH_DOUBLES (8u * 1024u * 1024u)  // 64 MiB
+static __device__ __align__(256) double eri_fixed_scratch[ERI_FIXED_SCRATCH_DOUBLES];
+
+namespace {
+// Device address of eri_fixed_scratch, looked up once per device with that
+// device current (host code may not use the symbol's name as an address).
+int fixed_scratch_ptr(double** out) {
+  static std::mutex mu;
+  static std::map<int, double*> ptrs;
+  int dev = 0;
+  CUDA_OR(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> g(mu);
+  auto it = ptrs.find(dev);
+  if (it == ptrs.end()) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, eri_fixed_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(ERI_ECUDA, std::string("cudaGetSymbolAddress(eri_fixed_scratch): ") + cudaGetErrorString(e));
+    it = ptrs.emplace(dev, (double*)p).first;
+  }
+  *out = it->second;
+  return ERI_OK;
+}
+}  // namespace
+
+extern "C" int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* stream_) {
+  if (!plan) return fail(ERI_EINVAL, "NULL plan");
+  if (plan->nq == 0) return ERI_OK;
+  if (!out) return fail(ERI_EINVAL, "NULL output");
+  if (((uintptr_t)out & 7) != 0) return fail(ERI_EINVAL, "output not 8-byte aligned");
+  for (const Bucket& b : plan->buckets) {
+    if (b.tier != TIER_GLOBAL)
+      return fail(ERI_EUNSUPPORTED, "eri_compute_fixed_scratch needs a plan built with tier = 3 (global scratch)");
+    // one block of 128 threads must fit: nslot * 128 doubles
+    if ((size_t)b.prog->nslot * 128 > ERI_FIXED_SCRATCH_DOUBLES)
+      return fail(ERI_EINVAL, "class (" + std::to_string(b.ls[0]) + std::to_string(b.ls[1]) + "|" +
+                                  std::to_string(b.ls[2]) + std::to_string(b.ls[3]) + ") needs " +
+                                  std::to_string((size_t)b.prog->nslot * 128 * 8) +
+                                  " bytes of scratch per 128-thread block; the fixed scratch holds " +
+                                  std::to_string((size_t)ERI_FIXED_SCRATCH_DOUBLES * 8));
+  }
+  double* scratch = nullptr;
+  int rc = fixed_scratch_ptr(&scratch);
+  if (rc) return rc;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  Library& L = lib();
+  {
+    const int threads = 128;
+    const int blocks = (plan->npair + threads - 1) / threads;
+    eri_pair_setup_kernel<<<blocks, threads, 0, stream>>>(plan->pin.p, plan->npair, plan->shells.p, plan->exps.p,
+                                                          plan->coefs.p, plan->plist.p, plan->pairs.p,
+                                                          plan->pprims.p);
+    CUDA_OR(cudaGetLastError(), "pair set-up launch");
+  }
+  for (const Bucket& b : plan->buckets) {
+    // as many 128-thread blocks as the fixed array holds, at most the plan's
+    // grid; the executor strides over the remaining quartets
+    const int fit = (int)(ERI_FIXED_SCRATCH_DOUBLES / ((size_t)b.prog->nslot * 128));
+    const int grid = std::max(1, std::min(b.grid, fit));
+    EriLaunchArgs a;
+    a.quartets = plan->quartets.p + b.first;
+    a.pairs = plan->pairs.p;
+    a.pprims = plan->pprims.p;
+    a.boys_tab = L.d_boys;
+    a.out = out;
+    a.scratch = scratch;
+    a.scratch_stride = (int64_t)grid * 128;
+    a.nq = (int32_t)b.count;
+    a.group = b.group;
+    EriProgArgs p;
+    p.ph1 = b.prog->d_ph1;
+    p.ph2 = b.prog->d_ph2;
+    p.c2s = L.d_c2s;
+    p.n1 = b.prog->n1;
+    p.n2 = b.prog->n2;
+    p.nh = b.prog->nh;
+    p.L = b.prog->L;
+    CUDA_OR(eri_exec_launch(0, &a, &p, grid, 128, 0, stream), "executor launch (fixed scratch)");
+  }
+  return ERI_OK;
+}

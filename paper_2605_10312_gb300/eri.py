@@ -74,6 +74,8 @@ def library(path: str = LIB):
         lib.eri_plan_launch_info.restype = ctypes.c_int
         lib.eri_plan_launch_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p]
+        lib.eri_compute_fixed_scratch.restype = ctypes.c_int
+        lib.eri_compute_fixed_scratch.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.eri_plan_destroy.restype = ctypes.c_int
         lib.eri_plan_destroy.argtypes = [ctypes.c_void_p]
         lib.eri_last_error.restype = ctypes.c_char_p
@@ -170,6 +172,18 @@ class Plan:
         if out.numel() < self.output_count:
             raise ValueError("out is too small")
         _check(library().eri_compute(self._h, out.data_ptr(), _stream_handle(stream)))
+        return out
+
+    def compute_fixed_scratch(self, out, stream=None):
+        """Like ``compute`` but without any device allocation: the kernels
+        use the library's fixed 64 MiB scratch array (plans built with
+        tier="global" only; see eri_compute_fixed_scratch)."""
+        import torch
+        if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()):
+            raise TypeError("out must be a contiguous CUDA float64 tensor")
+        if out.numel() < self.output_count:
+            raise ValueError("out is too small")
+        _check(library().eri_compute_fixed_scratch(self._h, out.data_ptr(), _stream_handle(stream)))
         return out
 
     def compute_host(self, out, stream=None):
