@@ -357,6 +357,69 @@ def _traffic_for(rec):
     return ent["bytes_per_quartet"] * rec["quartets"]
 
 
+# ---------------------------------------------------------------------------
+# ablations of the paper's Sec. V-B on this generator and this GPU
+# ---------------------------------------------------------------------------
+ABLATION_N = {(1, 1, 1, 1): 100_000, (2, 1, 2, 1): 40_000, (2, 2, 2, 1): 20_000, (2, 2, 2, 2): 10_000,
+              (3, 3, 2, 2): 2_000, (3, 3, 3, 3): 1_000}
+
+
+def run_ablation(args):
+    """Axis rule, DSA, spherical fusion and tier ablations: one JSON line per
+    (class, variant) with throughput and the generator's graph metrics."""
+    import torch
+    from paper_2605_10312_gb300 import eri
+    from paper_2605_10312_gb300.build import ABLATION_CLASSES, ABLATION_OPTS
+    from paper_2605_10312_gb300.gen import hrr, program
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    default = ("prose", "dsa", "stepwise")
+
+    def timed(plan, out, reps=3):
+        for _ in range(2):
+            plan.compute(out, stream)
+        stream.synchronize()
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.compute(out, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    for ls in ABLATION_CLASSES:
+        n = max(1, int(ABLATION_N[ls] * SCALE))
+        basis, q = synth.class_sweep(ls, n, kset=(1, 3), seed=4000 + sum(ls))
+        rows = [(o, "coop") for o in [default] + ABLATION_OPTS]
+        rows += [(default, t) for t in ("reg", "shared", "global")]
+        for opts, tier in rows:
+            try:
+                # whole pairs, higher l first: every quartet stays in the
+                # generated class (la >= lb, lc >= ld)
+                plan = eri.Plan(basis, q, axis_rule=opts[0], schedule=opts[1], sph_mode=opts[2], tier=tier,
+                                orientation="l")
+            except eri.EriError as e:
+                print(json.dumps({"ablation": "".join(map(str, ls)), "opts": opts, "tier": tier,
+                                  "unavailable": str(e)}))
+                continue
+            out = torch.empty(max(1, plan.output_count), dtype=torch.float64, device="cuda")
+            ms = timed(plan, out)
+            prog = program.make(*ls, *opts)
+            c = prog.counts()
+            st = plan.stats()
+            print(json.dumps({"ablation": "".join(map(str, ls)), "opts": opts, "tier": tier, "quartets": n,
+                              "ms": ms, "quartets_per_s": n / (ms * 1e-3),
+                              "fp64_tflops": st["flops"] / (ms * 1e-3) / 1e12,
+                              "vrr_nodes": c["vrr_nodes"], "peak_live": c["peak_live"],
+                              "p2_ops": hrr.op_counts(prog.p2)[0], "flops_per_prim": c["per_prim_flops"]}),
+                  flush=True)
+            plan.close()
+            del out
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,12 +431,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--classes", default="", help="comma-separated subset, e.g. gggg (profiling runs)")
     ap.add_argument("--scale", type=float, default=1.0, help="multiply the quartet counts (profiling runs)")
+    ap.add_argument("--ablation", action="store_true", help="axis / DSA / spherical / tier ablations instead")
     args = ap.parse_args()
     global ONLY, SCALE
     ONLY = set(c for c in args.classes.split(",") if c) or None
     SCALE = args.scale
     if args.impl == "reference":
         return run_reference(args)
+    if args.ablation:
+        return run_ablation(args)
     return run_ours(args)
 
 

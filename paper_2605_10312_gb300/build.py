@@ -37,9 +37,12 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + CS
 # straight-line size (VRR terms + 1.5 x Phase-2 operations) up to which a
 # class gets a compiled register-tier kernel; larger classes run as programs
 REG_TIER_MAX = 3000
-# shared memory four T=32 teams may fill with value slots before a class
-# moves to T=128 teams
-COOP_T32_SMEM = 200 * 1024
+
+# classes and option variants of the paper's ablations (Sec. V-B): axis rule,
+# DSA off, materialize-then-transform, Cartesian output
+ABLATION_CLASSES = [(1, 1, 1, 1), (2, 1, 2, 1), (2, 2, 2, 1), (2, 2, 2, 2), (3, 3, 2, 2), (3, 3, 3, 3)]
+ABLATION_OPTS = [("common", "dsa", "stepwise"), ("literal", "dsa", "stepwise"), ("prose", "level", "stepwise"),
+                 ("prose", "dsa", "materialize"), ("prose", "dsa", "cart")]
 
 AXIS = {"prose": 0, "literal": 1, "common": 2}
 SCHED = {"dsa": 0, "level": 1}
@@ -68,7 +71,8 @@ def boys_table(ngrid=362, ncol=24, step=0.1, dps=32):
 
 
 def _class_job(args):
-    ls, opts, want_reg = args
+    ls, opts, want_reg = args[:3]
+    force_coop = len(args) > 3 and args[3]
     sys.setrecursionlimit(100000)
     from paper_2605_10312_gb300.gen import emit_cuda, encode, program
     prog = program.make(*ls, *opts)
@@ -81,13 +85,11 @@ def _class_job(args):
     if want_reg and rec["size"] <= REG_TIER_MAX:
         rec["cuda"] = emit_cuda.emit_class(prog, "reg")
         rec["kname"] = emit_cuda.kernel_name(ls, "reg")
-    elif want_reg:
+    if (want_reg and rec["size"] > REG_TIER_MAX) or force_coop:
         # team-cooperative form: one warp per primitive quartet while four
         # teams' live sets fit in shared memory, else four warps
         from paper_2605_10312_gb300.gen import coop
-        cp = coop.build(prog, 32)
-        if 4 * cp.nslot * 8 > COOP_T32_SMEM:
-            cp = coop.build(prog, 128)
+        cp = coop.choose(prog)
         rec["coop"] = dict(T=cp.T, nh=cp.nh, nslot=cp.nslot, L=cp.L, dims=cp.out_dims, steps1=cp.steps1.tobytes(),
                            steps2=cp.steps2.tobytes(), nw1=int(cp.steps1.shape[0]), nw2=int(cp.steps2.shape[0]),
                            ph1=cp.ph1.tobytes(), ph2=cp.ph2.tobytes(), n1=int(cp.ph1.shape[0]),
@@ -95,10 +97,10 @@ def _class_job(args):
     return rec
 
 
-def generate(classes, opts=("prose", "dsa", "stepwise"), want_reg=True, jobs=None, log=print):
+def generate(classes, opts=("prose", "dsa", "stepwise"), want_reg=True, jobs=None, log=print, extra=()):
     t0 = time.time()
     jobs = jobs or max(1, os.cpu_count() or 1)
-    work = [(tuple(ls), tuple(opts), want_reg) for ls in classes]
+    work = [(tuple(ls), tuple(opts), want_reg) for ls in classes] + list(extra)
     # heaviest first so the pool ends evenly
     work.sort(key=lambda w: -sum(w[0]) * 100 - w[0][0])
     ctx = mp.get_context("spawn")
@@ -191,9 +193,14 @@ def build(force=False, jobs=None, log=print):
     blob = os.path.join(BUILD, "eri_programs.bin")
     stamp = os.path.join(BUILD, "gen.key")
     if force or not (os.path.exists(blob) and os.path.exists(stamp) and open(stamp).read() == gen_key):
-        recs = generate(program.all_classes(), jobs=jobs, log=log)
+        # ablation variants (program and cooperative forms, no compiled kernel)
+        extra = [(tuple(ls), tuple(o), False, True) for ls in ABLATION_CLASSES for o in ABLATION_OPTS]
+        allrecs = generate(program.all_classes(), jobs=jobs, log=log, extra=extra)
+        recs = [r for r in allrecs if tuple(r["opts"]) == ("prose", "dsa", "stepwise")]
+        abl = [r for r in allrecs if tuple(r["opts"]) != ("prose", "dsa", "stepwise")]
         boys = boys_table()
         write_blob(blob, recs, boys, encode.coef_table())
+        write_blob(os.path.join(BUILD, "eri_programs_ablation.bin"), abl, boys, encode.coef_table())
         for r in recs:
             if "cuda" in r:
                 _write_if_changed(os.path.join(GEN_DIR, r["kname"] + ".cu"), r["cuda"])

@@ -32,12 +32,21 @@ struct EriQuartetRec { // 32 bytes
   int32_t st[4];       // output strides of the A, B, C, D component indices
 };
 
-#define ERI_PAIR_INDEX(x) ((x) & 0x7fffffff)
+#define ERI_PAIR_INDEX(x) ((x) & 0x3fffffff)
 #define ERI_ACCUMULATE(x) ((x) < 0)
+#define ERI_REDUCE(x) (((x) >> 30) & 1)
 
-// Output store of one element: the first part of a quartet writes its
-// block, later parts (other pair orientations, other launches) add to it.
+// Output store of one element.  The first part of a quartet writes its
+// block, later parts (other pair orientations, later launches) add to it;
+// chunks of one quartet that run concurrently in one launch reduce into a
+// block the launch zeroed first.
 __device__ __forceinline__ void eri_st(double* p, double v, bool acc) { *p = acc ? *p + v : v; }
+__device__ __forceinline__ void eri_st(double* p, double v, bool acc, bool red) {
+  if (red)
+    atomicAdd(p, v);
+  else
+    *p = acc ? *p + v : v;
+}
 
 struct EriLaunchArgs {
   const EriQuartetRec* __restrict__ quartets;  // this launch's quartets

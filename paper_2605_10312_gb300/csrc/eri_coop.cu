@@ -74,140 +74,261 @@ __device__ __forceinline__ void eri_team_sync() {
   }
 }
 
-template <int T>
-__global__ void __launch_bounds__(128) eri_coop_kernel(const EriLaunchArgs a, const EriCoopArgs p) {
+// Per-primitive-quartet coefficient row, computed by one lane for a batch of
+// primitive quartets and then read by the whole team:
+//   [0, 17)   base values pref * F_m(T), m = 0..16
+//   17 + 6 side + 3 j + axis   (P-A | W-P) for side 0, (Q-C | W-Q) for side 1
+//   29 + 8 side + k - 1        k / (2 zeta) (side 0), k / (2 eta) (side 1)
+//   45 + k - 1                 k / (2 (zeta + eta))
+//   53 + side                  -rho/zeta, -rho/eta
+#define ERI_COOP_NC 56
+#define ERI_COOP_BATCH 32
+
+__device__ __forceinline__ void eri_coop_row(const EriPairPrim& bp, const EriPairPrim& kp, int L,
+                                             const double* __restrict__ tab, double* row) {
+  EriPrimQuartet pq;
+  eri_prim_quartet(bp, kp, pq);
+  double F[ERI_BOYS_LMAX + 1];
+  eri_coop_boys(L, pq.T, F, tab);
+  for (int m = 0; m <= L; ++m) row[m] = pq.pref * F[m];
+  for (int i = 0; i < 3; ++i) {
+    row[17 + i] = bp.PA[i];
+    row[20 + i] = pq.WP[i];
+    row[23 + i] = kp.PA[i];
+    row[26 + i] = pq.WQ[i];
+  }
+  for (int k = 0; k < 8; ++k) {
+    row[29 + k] = (double)(k + 1) * bp.inv2z;
+    row[37 + k] = (double)(k + 1) * kp.inv2z;
+    row[45 + k] = (double)(k + 1) * (0.5 * pq.s);
+  }
+  row[53] = -pq.te;
+  row[54] = -pq.tz;
+}
+
+// Phase-1 nodes (see the generator's coop module for the descriptor).  A
+// lane's two nodes of a step belong to one wave and so never alias: all
+// operands are loaded before either result is stored, letting the two FMA
+// chains interleave.
+template <typename Ptr>
+__device__ __forceinline__ void eri_coop_load1(const uint4& d, const Ptr& ptr, double (&v)[5]) {
+  const int side = (d.w >> 16) & 3;
+  if (side >= 2) return;
+  v[0] = *ptr(d.y & 0xFFFF);
+  v[1] = *ptr(d.y >> 16);
+  if ((d.w >> 20) & 31) {
+    v[2] = *ptr(d.z & 0xFFFF);
+    v[3] = *ptr(d.z >> 16);
+  }
+  if ((d.w >> 25) & 31) v[4] = *ptr(d.w & 0xFFFF);
+}
+
+__device__ __forceinline__ double eri_coop_eval1(const uint4& d, const double* row, const double (&v)[5]) {
+  const int side = (d.w >> 16) & 3;
+  const int k = (d.w >> 20) & 31;
+  if (side == 2) return row[k];
+  const int axis = (d.w >> 18) & 3;
+  const int k3 = (d.w >> 25) & 31;
+  const int cb = 17 + 6 * side + axis;
+  double x = row[cb] * v[0];
+  x = fma(row[cb + 3], v[1], x);
+  if (k) x = fma(row[28 + 8 * side + k], fma(row[53 + side], v[3], v[2]), x);
+  if (k3) x = fma(row[44 + k3], v[4], x);
+  return x;
+}
+
+template <bool HSM, typename Ptr>
+__device__ __forceinline__ void eri_coop_store1(const uint4& d, double x, const Ptr& ptr, double* Hs) {
+  if (((d.w >> 16) & 3) == 3) return;
+  if (d.w & (1u << 30)) *ptr(d.x & 0xFFFF) = x;
+  const unsigned h = d.x >> 16;
+  if (h) {
+    // each target has one owner lane per wave: shared-memory H is updated
+    // in place, global H by a fire-and-forget reduction
+    if (HSM)
+      Hs[h - 1] += x;
+    else
+      atomicAdd(Hs + (h - 1), x);
+  }
+}
+
+template <bool HSM, typename Ptr>
+__device__ __forceinline__ void eri_coop_node2(const uint4& da, const uint4& db, const double* row, const Ptr& ptr,
+                                               double* Hs) {
+  double va[5], vb[5];
+  eri_coop_load1(da, ptr, va);
+  eri_coop_load1(db, ptr, vb);
+  const double xa = eri_coop_eval1(da, row, va);
+  const double xb = eri_coop_eval1(db, row, vb);
+  eri_coop_store1<HSM>(da, xa, ptr, Hs);
+  eri_coop_store1<HSM>(db, xb, ptr, Hs);
+}
+
+// Phase-2 operations and stores, two per lane per step (never aliasing
+// within a wave): operands first, then results.
+template <typename Ptr>
+__device__ __forceinline__ void eri_coop_load2(const uint4& d, const Ptr& ptr, double (&v)[4]) {
+  const int kind = d.x & 3;
+  if (kind == 0) {
+    v[0] = *ptr(d.y & 0xFFFF);
+    v[1] = *ptr(d.y >> 16);
+  } else if (kind == 1) {
+    const int nt = (d.x >> 2) & 7;
+    v[0] = *ptr(d.y & 0xFFFF);
+    if (nt > 1) v[1] = *ptr(d.y >> 16);
+    if (nt > 2) v[2] = *ptr(d.z & 0xFFFF);
+    if (nt > 3) v[3] = *ptr(d.z >> 16);
+  } else if (kind == 2) {
+    v[0] = *ptr(d.x >> 16);
+  }
+}
+
+template <typename Ptr>
+__device__ __forceinline__ void eri_coop_exec2(const uint4& d, const double (&v)[4], const EriPairRec& bra,
+                                               const EriPairRec& ket, const EriQuartetRec& qr, double* o, bool acc,
+                                               bool red, const double* __restrict__ c2s, const Ptr& ptr) {
+  const int kind = d.x & 3;
+  const unsigned dst = d.x >> 16;
+  if (kind == 0) {
+    const int ax = d.z;
+    const double X = ax < 3 ? eri_coop_pick3(ax, bra.AB[0], bra.AB[1], bra.AB[2])
+                            : eri_coop_pick3(ax - 3, ket.AB[0], ket.AB[1], ket.AB[2]);
+    *ptr(dst) = fma(X, v[1], v[0]);
+  } else if (kind == 1) {
+    const int nt = (d.x >> 2) & 7;
+    double x = __ldg(c2s + (d.w & 255)) * v[0];
+    if (nt > 1) x = fma(__ldg(c2s + ((d.w >> 8) & 255)), v[1], x);
+    if (nt > 2) x = fma(__ldg(c2s + ((d.w >> 16) & 255)), v[2], x);
+    if (nt > 3) x = fma(__ldg(c2s + (d.w >> 24)), v[3], x);
+    *ptr(dst) = x;
+  } else if (kind == 2) {
+    const int64_t off = (int64_t)(d.z & 255) * qr.st[0] + (int64_t)((d.z >> 8) & 255) * qr.st[1] +
+                        (int64_t)((d.z >> 16) & 255) * qr.st[2] + (int64_t)(d.z >> 24) * qr.st[3];
+    eri_st(o + off, v[0], acc, red);
+  }
+}
+
+// HSM: the accumulators H share the team's shared-memory region with the
+// value slots ([H | slots], operand id = offset); otherwise H is a
+// team-private global region and slots follow at id - nh.
+template <int T, bool HSM>
+__global__ void __launch_bounds__(128, 4) eri_coop_kernel(const EriLaunchArgs a, const EriCoopArgs p) {
   extern __shared__ double eri_coop_smem[];
   const int tb = threadIdx.x / T;           // team within the block
   const int l = threadIdx.x - tb * T;       // lane within the team
-  const int team = blockIdx.x * (128 / T) + tb;
-  const int per_team = p.smem_slots + (p.h_in_smem ? p.nh : 0);
-  double* const Vs = eri_coop_smem + (size_t)tb * per_team;
-  double* const Hs = p.h_in_smem ? Vs + p.smem_slots : p.gH + (size_t)team * p.nh;
-  double* const Vg = p.gvals + (size_t)team * (p.nslot - p.smem_slots);
-  const unsigned nh = (unsigned)p.nh, ns = (unsigned)p.smem_slots;
-  // operand id -> address (per lane; ids differ between lanes)
+  const int team = blockIdx.x * (blockDim.x / T) + tb;
+  const int per_team = ERI_COOP_BATCH * ERI_COOP_NC + (HSM ? p.nh : 0) + p.smem_slots;
+  double* const rows = eri_coop_smem + (size_t)tb * per_team;
+  double* const S = rows + ERI_COOP_BATCH * ERI_COOP_NC;   // HSM: H then slots; else slots
+  double* const Hs = HSM ? S : p.gH + (size_t)team * p.nh;
+  const unsigned nh = (unsigned)p.nh;
+  const unsigned lim = HSM ? nh + (unsigned)p.smem_slots : (unsigned)p.smem_slots;
+  double* const Vg = p.gvals + (size_t)team * (p.nslot - p.smem_slots) - lim;
+  // operand id -> address
   auto ptr = [&](unsigned id) -> double* {
-    if (id < nh) return Hs + id;
-    id -= nh;
-    return id < ns ? Vs + id : Vg + (id - ns);
+    if (!HSM) {
+      if (id < nh) return Hs + id;
+      id -= nh;
+    }
+    return id < lim ? S + id : Vg + id;
   };
   for (int q = team; q < a.nq; q += p.nteams) {
     const EriQuartetRec qr = a.quartets[q];
     const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];
     const bool acc = ERI_ACCUMULATE(qr.bra);
+    const bool red = ERI_REDUCE(qr.bra);
     const EriPairRec ket = a.pairs[qr.ket];
     for (int h = l; h < p.nh; h += T) Hs[h] = 0.0;
-    eri_team_sync<T>();
     const int kk = ket.nprim;
-    for (int i = 0, j = 0; i < bra.nprim;) {
-      const EriPairPrim bp = a.pprims[bra.prim_off + i];
-      const EriPairPrim kp = a.pprims[ket.prim_off + j];
-      if (++j == kk) {
-        j = 0;
-        ++i;
+    const int k4 = bra.nprim * kk;
+    for (int b0 = 0; b0 < k4; b0 += ERI_COOP_BATCH) {
+      const int nb = min(ERI_COOP_BATCH, k4 - b0);
+      if (l < nb) {
+        const int pidx = b0 + l;
+        const int i = pidx / kk, j = pidx - (pidx / kk) * kk;
+        eri_coop_row(a.pprims[bra.prim_off + i], a.pprims[ket.prim_off + j], p.L, a.boys_tab,
+                     rows + l * ERI_COOP_NC);
       }
-      EriPrimQuartet pq;
-      eri_prim_quartet(bp, kp, pq);
-      double F[ERI_BOYS_LMAX + 1];
-      eri_coop_boys(p.L, pq.T, F, a.boys_tab);
-      double c1b[8], c1k[8], c3[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        c1b[k] = (double)(k + 1) * bp.inv2z;
-        c1k[k] = (double)(k + 1) * kp.inv2z;
-        c3[k] = (double)(k + 1) * (0.5 * pq.s);
-      }
-      const double roz = -pq.te, roe = -pq.tz;
-      const uint4* d1 = p.ph1 + l;
-      for (int w = 0; w < p.nw1; ++w) {
-        const int steps = (int)__ldg(p.steps1 + w);
-        for (int s = 0; s < steps; ++s, d1 += T) {
-          const uint4 d = __ldg(d1);
-          const int side = (d.w >> 16) & 3;
-          if (side == 3) continue;
-          const int k = (d.w >> 20) & 31;
-          double x;
-          if (side == 2) {
-            x = pq.pref * F[k];
-          } else {
-            const int axis = (d.w >> 18) & 3;
-            const int k3 = (d.w >> 25) & 31;
-            const double cg = side ? eri_coop_pick3(axis, kp.PA[0], kp.PA[1], kp.PA[2])
-                                   : eri_coop_pick3(axis, bp.PA[0], bp.PA[1], bp.PA[2]);
-            const double cw = side ? eri_coop_pick3(axis, pq.WQ[0], pq.WQ[1], pq.WQ[2])
-                                   : eri_coop_pick3(axis, pq.WP[0], pq.WP[1], pq.WP[2]);
-            x = cg * *ptr(d.y & 0xFFFF);
-            x = fma(cw, *ptr(d.y >> 16), x);
-            if (k) {
-              const double ck = side ? eri_coop_pick8(k, c1k) : eri_coop_pick8(k, c1b);
-              const double t = fma(side ? roe : roz, *ptr(d.z >> 16), *ptr(d.z & 0xFFFF));
-              x = fma(ck, t, x);
-            }
-            if (k3) x = fma(eri_coop_pick8(k3, c3), *ptr(d.w & 0xFFFF), x);
+      eri_team_sync<T>();
+      for (int pi = 0; pi < nb; ++pi) {
+        const double* const row = rows + pi * ERI_COOP_NC;
+        // a step gives each lane two descriptors (independent nodes of the
+        // same wave); they are loaded two steps ahead -- the stream ends in
+        // two no-op steps -- so the L2 latency overlaps the previous step
+        const uint4* dp = p.ph1 + 2 * l;
+        uint4 da = __ldg(dp), db = __ldg(dp + 1);
+        uint4 dna = __ldg(dp + 2 * T), dnb = __ldg(dp + 2 * T + 1);
+        for (int w = 0; w < p.nw1; ++w) {
+          const int steps = (int)__ldg(p.steps1 + w);
+          for (int s = 0; s < steps; ++s) {
+            const uint4 dnna = __ldg(dp + 4 * T), dnnb = __ldg(dp + 4 * T + 1);
+            dp += 2 * T;
+            eri_coop_node2<HSM>(da, db, row, ptr, Hs);
+            da = dna;
+            db = dnb;
+            dna = dnna;
+            dnb = dnnb;
           }
-          if (d.w & (1u << 30)) *ptr(d.x & 0xFFFF) = x;
-          const unsigned h = d.x >> 16;
-          if (h) Hs[h - 1] += x;
+          eri_team_sync<T>();
         }
-        eri_team_sync<T>();
       }
     }
     // Phase 2 and the stores, once per shell quartet
     double* const o = a.out + qr.out_off;
-    const uint4* d2 = p.ph2 + l;
+    const uint4* dp = p.ph2 + 2 * l;
+    uint4 da = __ldg(dp), db = __ldg(dp + 1);
+    uint4 dna = __ldg(dp + 2 * T), dnb = __ldg(dp + 2 * T + 1);
     for (int w = 0; w < p.nw2; ++w) {
       const int steps = (int)__ldg(p.steps2 + w);
-      for (int s = 0; s < steps; ++s, d2 += T) {
-        const uint4 d = __ldg(d2);
-        const int kind = d.x & 3;
-        if (kind == 3) continue;
-        const unsigned dst = d.x >> 16;
-        if (kind == 0) {
-          const int ax = d.z;
-          const double X = ax < 3 ? eri_coop_pick3(ax, bra.AB[0], bra.AB[1], bra.AB[2])
-                                  : eri_coop_pick3(ax - 3, ket.AB[0], ket.AB[1], ket.AB[2]);
-          *ptr(dst) = fma(X, *ptr(d.y >> 16), *ptr(d.y & 0xFFFF));
-        } else if (kind == 1) {
-          const int nt = (d.x >> 2) & 7;
-          double x = __ldg(p.c2s + (d.w & 255)) * *ptr(d.y & 0xFFFF);
-          if (nt > 1) x = fma(__ldg(p.c2s + ((d.w >> 8) & 255)), *ptr(d.y >> 16), x);
-          if (nt > 2) x = fma(__ldg(p.c2s + ((d.w >> 16) & 255)), *ptr(d.z & 0xFFFF), x);
-          if (nt > 3) x = fma(__ldg(p.c2s + (d.w >> 24)), *ptr(d.z >> 16), x);
-          *ptr(dst) = x;
-        } else {
-          const int64_t off = (int64_t)(d.z & 255) * qr.st[0] + (int64_t)((d.z >> 8) & 255) * qr.st[1] +
-                              (int64_t)((d.z >> 16) & 255) * qr.st[2] + (int64_t)(d.z >> 24) * qr.st[3];
-          eri_st(o + off, *ptr(dst), acc);
-        }
+      for (int s = 0; s < steps; ++s) {
+        const uint4 dnna = __ldg(dp + 4 * T), dnnb = __ldg(dp + 4 * T + 1);
+        dp += 2 * T;
+        double va[4], vb[4];
+        eri_coop_load2(da, ptr, va);
+        eri_coop_load2(db, ptr, vb);
+        eri_coop_exec2(da, va, bra, ket, qr, o, acc, red, p.c2s, ptr);
+        eri_coop_exec2(db, vb, bra, ket, qr, o, acc, red, p.c2s, ptr);
+        da = dna;
+        db = dnb;
+        dna = dnna;
+        dnb = dnnb;
       }
       eri_team_sync<T>();
     }
   }
 }
 
-extern "C" cudaError_t eri_coop_launch(int T, const EriLaunchArgs* a, const EriCoopArgs* p, int grid, size_t smem,
-                                       cudaStream_t stream) {
+extern "C" cudaError_t eri_coop_launch(int T, const EriLaunchArgs* a, const EriCoopArgs* p, int grid, int block,
+                                       size_t smem, cudaStream_t stream) {
+  const bool hsm = p->h_in_smem != 0;
+#define ERI_COOP_CASE(TT)                                                  \
+  case TT:                                                                 \
+    if (hsm)                                                               \
+      eri_coop_kernel<TT, true><<<grid, block, smem, stream>>>(*a, *p);    \
+    else                                                                   \
+      eri_coop_kernel<TT, false><<<grid, block, smem, stream>>>(*a, *p);   \
+    break;
   switch (T) {
-    case 32:
-      eri_coop_kernel<32><<<grid, 128, smem, stream>>>(*a, *p);
-      break;
-    case 64:
-      eri_coop_kernel<64><<<grid, 128, smem, stream>>>(*a, *p);
-      break;
-    case 128:
-      eri_coop_kernel<128><<<grid, 128, smem, stream>>>(*a, *p);
-      break;
+    ERI_COOP_CASE(32)
+    ERI_COOP_CASE(64)
+    ERI_COOP_CASE(128)
     default:
       return cudaErrorInvalidValue;
   }
+#undef ERI_COOP_CASE
   return cudaGetLastError();
 }
 
+// shared memory a team needs besides its H and value slots
+extern "C" size_t eri_coop_rows_bytes(void) { return (size_t)ERI_COOP_BATCH * ERI_COOP_NC * sizeof(double); }
+
 extern "C" cudaError_t eri_coop_set_smem(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(eri_coop_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(eri_coop_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(eri_coop_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return e;
+  const void* fns[] = {(const void*)eri_coop_kernel<32, true>,  (const void*)eri_coop_kernel<32, false>,
+                       (const void*)eri_coop_kernel<64, true>,  (const void*)eri_coop_kernel<64, false>,
+                       (const void*)eri_coop_kernel<128, true>, (const void*)eri_coop_kernel<128, false>};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }

@@ -17,6 +17,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -44,9 +45,10 @@ struct EriCoopArgs {
   int32_t h_in_smem;
   int32_t nteams;
 };
-extern "C" cudaError_t eri_coop_launch(int T, const EriLaunchArgs* a, const EriCoopArgs* p, int grid, size_t smem,
-                                       cudaStream_t stream);
+extern "C" cudaError_t eri_coop_launch(int T, const EriLaunchArgs* a, const EriCoopArgs* p, int grid, int block,
+                                       size_t smem, cudaStream_t stream);
 extern "C" cudaError_t eri_coop_set_smem(size_t bytes);
+extern "C" size_t eri_coop_rows_bytes(void);
 
 struct EriRegEntry {
   int8_t ls[4];
@@ -288,7 +290,9 @@ struct DevShell {
 struct DevPairIn {
   int32_t a, b;       // oriented shells: a is the recurrence centre
   int32_t prim_off;   // first EriPairPrim
-  int32_t list_off;   // -1: every (i, j) of a x b; else nlist packed (i | j << 16) entries
+  int32_t list_off;   // -1: every (i, j) of a x b; -2: alias of nlist primitive pairs already
+                      // written at prim_off (a chunk of another pair); else nlist packed
+                      // (i | j << 16) entries of the primitive-pair list
   int32_t nlist;
   int32_t pad;
 };
@@ -311,12 +315,13 @@ __global__ void eri_pair_setup_kernel(const DevPairIn* __restrict__ pin, int npa
   const double ab2 = AB0 * AB0 + AB1 * AB1 + AB2 * AB2;
   EriPairRec r;
   r.prim_off = in.prim_off;
-  const int n = in.list_off < 0 ? A.nprim * B.nprim : in.nlist;
+  const int n = in.list_off == -1 ? A.nprim * B.nprim : in.nlist;
   r.nprim = n;
   r.AB[0] = AB0;
   r.AB[1] = AB1;
   r.AB[2] = AB2;
   pairs[p] = r;
+  if (in.list_off == -2) return;  // a chunk: its primitive pairs belong to another record
   const double dfi[5] = {1.0, 1.0, 1.0 / 1.7320508075688772935, 1.0 / 3.8729833462074168852,
                          1.0 / 10.246950765959598383};  // 1/sqrt((2l-1)!!)
   const double C0 = 5.9149671727956128778;              // sqrt(2) pi^(5/4)
@@ -421,6 +426,7 @@ struct eri_plan_s {
   DevBuf<double> coop_vals, coop_h;  // team-private spill regions of the cooperative tier
   int64_t scratch_stride = 0;
   double h2d_bytes = 0;
+  bool zero_out = false;  // chunks reduce into their block: eri_compute zeroes the output first
   bool timing = false;
   std::vector<cudaEvent_t> events;  // two per launch: pair set-up, then buckets
   ~eri_plan_s() {
@@ -522,6 +528,34 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
   struct PairPart {
     int center, other, pair, nprim;
   };
+  // Chunks: a shell quartet of the team-cooperative tier evaluates its
+  // primitive quartets one after another, so a deep contraction is cut into
+  // chunks of about kCoopChunk primitive quartets (sub-ranges of the bra
+  // pair's primitive pairs) that different teams run concurrently.
+  const int kCoopChunk = 32;
+  const bool default_opts0 = opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0;
+  auto is_coop = [&](int la, int lb, int lc, int ld) {
+    std::vector<int> key = {la, lb, lc, ld, opts.axis_rule, opts.schedule, opts.sph_mode};
+    if (L.coops.find(key) == L.coops.end()) return false;
+    if (opts.tier == TIER_COOP) return true;
+    if (opts.tier != 0) return false;
+    return !(default_opts0 && L.reg.count({la, lb, lc, ld}));
+  };
+  std::map<std::tuple<int, int, int>, int> alias_id;
+  auto get_alias = [&](int parent, int start, int count) {
+    auto key = std::make_tuple(parent, start, count);
+    auto it = alias_id.find(key);
+    if (it != alias_id.end()) return it->second;
+    DevPairIn d = pin[parent];
+    d.prim_off += start;
+    d.list_off = -2;
+    d.nlist = count;
+    const int id = (int)pin.size();
+    pin.push_back(d);
+    alias_id.emplace(key, id);
+    return id;
+  };
+  bool any_reduce = false;
   auto split = [&](int s0, int s1, PairPart* out) {
     const int l0 = shells[s0].l, l1 = shells[s1].l;
     if (opts.orientation == 1 || opts.orientation == 2) {
@@ -582,25 +616,36 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
           std::swap(lb0, lk0);
           std::swap(lb1, lk1);
         }
-        QInfo x;
-        x.rec.bra = B.pair | (round > 0 ? (int32_t)0x80000000 : 0);
-        x.rec.ket = K.pair;
-        x.rec.out_off = plan->offsets[q];
-        for (int k = 0; k < 4; ++k) x.rec.st[k] = ustride[pos[k]];
         std::vector<int> key = {lb0, lb1, lk0, lk1};
         auto it = cls_index.find(key);
         if (it == cls_index.end()) {
           it = cls_index.emplace(key, (int)cls_keys.size()).first;
           cls_keys.push_back(key);
         }
-        x.cls = it->second;
-        x.round = round;
-        x.kb = B.nprim;
-        x.kk = K.nprim;
-        qi.push_back(x);
+        int cb = B.nprim, nchunk = 1;
+        if ((int64_t)B.nprim * K.nprim > kCoopChunk && is_coop(lb0, lb1, lk0, lk1)) {
+          cb = std::max(1, kCoopChunk / K.nprim);
+          nchunk = (B.nprim + cb - 1) / cb;
+        }
+        for (int c = 0; c < nchunk; ++c) {
+          const int start = c * cb, cnt = std::min(cb, B.nprim - start);
+          QInfo x;
+          const int bpair = nchunk > 1 ? get_alias(B.pair, start, cnt) : B.pair;
+          x.rec.bra = bpair | (round > 0 ? (int32_t)0x80000000 : 0) | (nchunk > 1 ? 0x40000000 : 0);
+          x.rec.ket = K.pair;
+          x.rec.out_off = plan->offsets[q];
+          for (int k = 0; k < 4; ++k) x.rec.st[k] = ustride[pos[k]];
+          x.cls = it->second;
+          x.round = round;
+          x.kb = cnt;
+          x.kk = K.nprim;
+          qi.push_back(x);
+        }
+        if (nchunk > 1) any_reduce = true;
       }
   }
   const int64_t nparts = (int64_t)qi.size();
+  plan->zero_out = any_reduce;
   if (pprim > ((int64_t)1 << 31) - 1) return fail(ERI_EINVAL, "too many primitive pairs");
   // ---- buckets: by part round (a block is written before it is added to),
   // then class (heaviest first), then contraction signature
@@ -631,8 +676,17 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
   for (int64_t i = 0; i < nparts; ++i) recs[i] = qi[order[i]].rec;
   // ---- launches: one per (class, group size); G lanes share a quartet and
   // split its K4 primitive quartets, about three per lane
-  auto group_of = [](int64_t k4) {
+  // G = lanes per quartet: about three primitive quartets per lane, but no
+  // more lanes than needed to give the launch ~16 warps per SM (every extra
+  // lane costs a share of the accumulator reduction)
+  std::map<std::tuple<int, int, int64_t>, int64_t> k4_count;
+  for (const QInfo& x : qi) ++k4_count[std::make_tuple(x.round, x.cls, (int64_t)x.kb * x.kk)];
+  const int64_t lanes_target = (int64_t)L.nsm * 512;
+  auto group_of = [&](const QInfo& x) {
+    const int64_t k4 = (int64_t)x.kb * x.kk;
+    const int64_t cnt = k4_count[std::make_tuple(x.round, x.cls, k4)];
     int64_t want = std::min<int64_t>(32, std::max<int64_t>(1, (k4 + 2) / 3));
+    want = std::min<int64_t>(want, std::max<int64_t>(1, lanes_target / std::max<int64_t>(1, cnt)));
     int g = 1;
     while (g * 2 <= want) g *= 2;
     return g;
@@ -667,11 +721,11 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
       return fail(ERI_EUNSUPPORTED, "class does not fit the shared-memory tier");
     // one launch per class for the cooperative tier (a team walks all the
     // primitive quartets of its shell quartet); otherwise one per group size
-    const int g = tier == TIER_COOP ? 1 : group_of((int64_t)qi[order[i]].kb * qi[order[i]].kk);
+    const int g = tier == TIER_COOP ? 1 : group_of(qi[order[i]]);
     int64_t j = i;
     double kprim = 0;
     while (j < nparts && qi[order[j]].cls == c && qi[order[j]].round == round &&
-           (tier == TIER_COOP || group_of((int64_t)qi[order[j]].kb * qi[order[j]].kk) == g)) {
+           (tier == TIER_COOP || group_of(qi[order[j]]) == g)) {
       kprim += (double)qi[order[j]].kb * qi[order[j]].kk;
       ++j;
     }
@@ -694,21 +748,39 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
       max_scratch_slots = std::max(max_scratch_slots, (size_t)prog->nslot);
       max_grid_global = std::max(max_grid_global, b.grid);
     } else {
-      // team-cooperative: value slots (and H when it fits) in shared memory
+      // team-cooperative: value slots (and H when it fits) in shared memory.
+      // Pick the block shape (teams per block) and the H placement that keep
+      // the most warps resident per SM, up to 16.
       b.coop = cp;
-      const int tpb = 128 / cp->T;
-      size_t per_team = (size_t)cp->nslot + cp->nh;
-      if (per_team * tpb * sizeof(double) <= L.smem_optin) {
-        b.h_in_smem = 1;
-        b.smem_slots = cp->nslot;
-      } else {
-        b.h_in_smem = 0;
-        b.smem_slots = (int)std::min<size_t>(cp->nslot, L.smem_optin / sizeof(double) / tpb);
-        per_team = b.smem_slots;
+      const size_t smem_sm = L.smem_per_sm, reserve = 1024;
+      int best_warps = -1;
+      const size_t rows = eri_coop_rows_bytes() / sizeof(double);
+      for (int h_in = 1; h_in >= 0; --h_in) {
+        for (int tpb = 128 / cp->T; tpb >= 1; tpb /= 2) {
+          size_t slots = cp->nslot;
+          size_t per_team = rows + slots + (h_in ? (size_t)cp->nh : 0);
+          if (per_team * tpb * sizeof(double) > L.smem_optin) {
+            if (h_in) continue;
+            if ((rows + 64) * tpb * sizeof(double) > L.smem_optin) continue;
+            slots = std::min<size_t>(cp->nslot, L.smem_optin / sizeof(double) / tpb - rows);
+            per_team = rows + slots;
+          }
+          const size_t bsm = per_team * tpb * sizeof(double);
+          const int bps = (int)std::min<size_t>(16 * 32 / (tpb * cp->T), std::max<size_t>(1, smem_sm / (bsm + reserve)));
+          const int warps = bps * tpb * cp->T / 32;
+          // prefer H in shared memory at equal residency
+          if (warps > best_warps) {
+            best_warps = warps;
+            b.h_in_smem = h_in;
+            b.smem_slots = (int)slots;
+            b.smem = bsm;
+            b.block = tpb * cp->T;
+            b.grid = bps;  // blocks per SM for now
+          }
+        }
       }
-      b.smem = per_team * tpb * sizeof(double);
-      const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, L.smem_per_sm / (b.smem + 1024)));
-      b.grid = (int)std::min<int64_t>((b.count + tpb - 1) / tpb, (int64_t)L.nsm * per_sm);
+      const int tpb = b.block / cp->T;
+      b.grid = (int)std::min<int64_t>((b.count + tpb - 1) / tpb, (int64_t)L.nsm * b.grid);
       b.nteams = b.grid * tpb;
       max_coop_vals = std::max(max_coop_vals, (size_t)b.nteams * (cp->nslot - b.smem_slots));
       if (!b.h_in_smem) max_coop_h = std::max(max_coop_h, (size_t)b.nteams * cp->nh);
@@ -783,6 +855,8 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
   auto mark = [&](int end) -> cudaError_t {
     return plan->timing ? cudaEventRecord(plan->events[2 * li + end], stream) : cudaSuccess;
   };
+  if (plan->zero_out)
+    CUDA_OR(cudaMemsetAsync(out, 0, (size_t)plan->offsets.back() * sizeof(double), stream), "zero output");
   {
     CUDA_OR(mark(0), "cudaEventRecord");
     const int threads = 128;
@@ -827,7 +901,7 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
       p.smem_slots = b.smem_slots;
       p.h_in_smem = b.h_in_smem;
       p.nteams = b.nteams;
-      CUDA_OR(eri_coop_launch(cp->T, &a, &p, b.grid, b.smem, stream), "cooperative launch");
+      CUDA_OR(eri_coop_launch(cp->T, &a, &p, b.grid, b.block, b.smem, stream), "cooperative launch");
     } else {
       EriProgArgs p;
       p.ph1 = b.prog->d_ph1;

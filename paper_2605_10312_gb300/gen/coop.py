@@ -95,6 +95,9 @@ def allocate_over_waves(parents, waves, needs_slot, first_slot=0, pinned_until_e
     return slot, nxt - first_slot
 
 
+ILP = 2  # nodes per lane per step: two independent chains per lane
+
+
 @dataclass
 class CoopProgram:
     T: int
@@ -110,17 +113,26 @@ class CoopProgram:
     eff2: float
 
 
+PREFETCH_STEPS = 2  # no-op steps after the last wave: the executor loads ahead
+
+
 def _pack(waves, rows_of, T, nop):
+    """A step is ILP * T descriptors: lane l takes descriptors ILP*l .. ILP*l +
+    ILP - 1 of the step, so a wave of n nodes spreads over the lanes first."""
+    W = ILP * T
     steps = []
     out = []
     for vs in waves:
-        st = (len(vs) + T - 1) // T
+        st = (len(vs) + W - 1) // W
         steps.append(st)
-        block = np.tile(nop, (st * T, 1))
+        block = np.tile(nop, (st * W, 1))
         for k, v in enumerate(vs):
-            block[k] = rows_of(v)
+            s, r = divmod(k, W)
+            lane, j = r % T, r // T       # fill every lane's first node before second nodes
+            block[s * W + lane * ILP + j] = rows_of(v)
         out.append(block)
-    arr = np.concatenate(out) if out else np.zeros((0, 4), dtype=np.uint32)
+    out.append(np.tile(nop, (PREFETCH_STEPS * W, 1)))
+    arr = np.concatenate(out)
     return arr.astype(np.uint32), np.array(steps, dtype=np.uint32)
 
 
@@ -132,7 +144,7 @@ def build(prog, T=128):
     order_pos = np.empty(len(g), dtype=np.int64)
     order_pos[np.array(prog.order, dtype=np.int64)] = np.arange(len(g))
     par1 = [[p for _, p in ts] for ts in g.terms]
-    waves1 = wave_schedule(par1, order_pos, T)
+    waves1 = wave_schedule(par1, order_pos, ILP * T)
     consumed = np.zeros(len(g), dtype=bool)
     for ps in par1:
         for p in ps:
@@ -215,7 +227,7 @@ def build(prog, T=128):
     work = [v for v in range(n2) if nodes[v][0] != "h"]
     pos = {v: i for i, v in enumerate(work)}
     par_list = [[pos[p] for p in parents[v] if nodes[p][0] != "h"] for v in work]
-    waves2 = wave_schedule(par_list, np.array([prio[v] for v in work]), T)
+    waves2 = wave_schedule(par_list, np.array([prio[v] for v in work]), ILP * T)
     waves2 = [[work[i] for i in w] for w in waves2]
     needs = np.zeros(n2, dtype=bool)
     for v in range(n2):
@@ -262,6 +274,31 @@ def build(prog, T=128):
     nslot = max(int(nslot1), int(nslot2))
     if nh + nslot > MAX_ID:
         raise ValueError("class {} needs {} ids".format(prog.ls, nh + nslot))
-    eff1 = len(g) / max(1, int(steps1.sum()) * T)
-    eff2 = len(sched) / max(1, int(steps2.sum()) * T)
+    eff1 = len(g) / max(1, int(steps1.sum()) * T * ILP)
+    eff2 = len(sched) / max(1, int(steps2.sum()) * T * ILP)
+    assert ph1.shape[0] == (int(steps1.sum()) + PREFETCH_STEPS) * T * ILP
     return CoopProgram(T, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(p2.out_dims), eff1, eff2)
+
+
+ROWS_BYTES = 32 * 56 * 8     # coefficient rows of one team (executor constant)
+SMEM_PER_SM = 228 * 1024
+
+
+def choose(prog, sizes=(32, 64, 128)):
+    """Team size with the most useful FP64 lanes per SM: resident warps
+    (shared memory for the team's rows, value slots and, when it fits, H;
+    at most 16 warps) times the lane efficiency of the waves."""
+    best, best_cp = -1.0, None
+    for T in sizes:
+        cp = build(prog, T)
+        vals = cp.nslot * 8 + ROWS_BYTES
+        with_h = vals + cp.nh * 8
+        per_team = with_h if with_h * (128 // T) <= 227 * 1024 or with_h <= 227 * 1024 else vals
+        if per_team > 227 * 1024:
+            continue
+        teams = max(1, min(SMEM_PER_SM // (per_team + 1024), 16 * 32 // T))
+        warps = teams * T // 32
+        score = min(warps, 16) * min(1.0, 0.5 * (cp.eff1 + cp.eff2) + 0.5 * cp.eff1)
+        if score > best:
+            best, best_cp = score, cp
+    return best_cp

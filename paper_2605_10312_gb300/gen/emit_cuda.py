@@ -174,12 +174,47 @@ def emit_class(prog, tier="reg", threads=128):
         w("    " + ("{ " + line + " }" if tier != "reg" else line))
     w("  }")
     if tier != "global":
+        # group reduction of the accumulators: reduce-scatter (each round
+        # halves the vector a lane keeps, so a lane adds about nh values in
+        # all) then all-gather back, instead of nh * log2(G) butterfly adds
         w("  if (G > 1) {")
         w("    const unsigned m = eri_group_mask(G);")
-        w("    for (int off = G >> 1; off > 0; off >>= 1) {")
-        for i in range(nh):
-            w("      h{0} += __shfl_xor_sync(m, h{0}, off);".format(i))
-        w("    }")
+        w("    const int lane = threadIdx.x & 31;")
+        names = [hname(i) for i in range(nh)]
+        w("    int off = G >> 1;")
+        # reduce-scatter rounds, vector halves stay in the low names
+        vec = list(names)
+        rounds = []
+        for _ in range(5):
+            rounds.append(list(vec))
+            n = len(vec)
+            half = n // 2
+            w("    if (off > 0) {")
+            w("      const bool up = (lane & off) != 0;")
+            for i in range(half):
+                lo, hi = vec[i], vec[half + i]
+                w("      {{ const double snd = up ? {0} : {1}; const double kp = up ? {1} : {0}; "
+                  "{0} = kp + __shfl_xor_sync(m, snd, off); }}".format(lo, hi))
+            if n % 2:
+                x = vec[n - 1]
+                w("      {0} += __shfl_xor_sync(m, {0}, off);".format(x))
+            w("      off >>= 1;")
+            w("    }")
+            vec = vec[:half] + ([vec[n - 1]] if n % 2 else [])
+        # all-gather: undo the reduce-scatter rounds, last first; round k
+        # used offset G >> (k + 1)
+        for k in range(4, -1, -1):
+            v = rounds[k]
+            n = len(v)
+            half = n // 2
+            w("    if ((G >> {0}) > 0) {{".format(k + 1))
+            w("      const int o2 = G >> {};".format(k + 1))
+            w("      const bool up = (lane & o2) != 0;")
+            for i in range(half):
+                lo, hi = v[i], v[half + i]
+                w("      {{ const double mine = {0}; const double oth = __shfl_xor_sync(m, mine, o2); "
+                  "{0} = up ? oth : mine; {1} = up ? mine : oth; }}".format(lo, hi))
+            w("    }")
         w("  }")
     w("  if (!valid || r != 0) return;")
     # Phase 2

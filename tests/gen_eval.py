@@ -199,10 +199,12 @@ def run_coop(cp, prog, basis, quartets):
     L = prog.L
     kmax = [int(basis.shell_nprim[q[:, k]].max()) for k in range(4)]
 
+    from paper_2605_10312_gb300.gen.coop import ILP
+
     def waves(rows, steps):
         i = 0
         for st in steps:
-            n = int(st) * cp.T
+            n = int(st) * cp.T * ILP
             yield rows[i:i + n]
             i += n
 

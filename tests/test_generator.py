@@ -132,7 +132,7 @@ def test_coop_program_matches_oracle(ls, T):
     only across waves) reproduce the oracle, wave semantics included."""
     prog = program.make(*ls)
     cp = coop.build(prog, T)
-    assert int(cp.steps1.sum()) * T == cp.ph1.shape[0]
+    assert (int(cp.steps1.sum()) + coop.PREFETCH_STEPS) * T * coop.ILP == cp.ph1.shape[0]
     basis, q = synth.class_sweep(ls, 3, kset=(1, 2), seed=13, box_angstrom=3.0, exp_range=(0.1, 30))
     ref, _ = blocks(basis, q)
     got = run_coop(cp, prog, basis, q)
