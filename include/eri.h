@@ -152,6 +152,26 @@ int eri_plan_launch_info(const eri_plan_t* plan, int i, int32_t* info, double* f
  * Returns ERI_EUNSUPPORTED for a plan with non-global tiers. */
 int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* stream);
 
+/* Schwarz factors.  For a plan whose every quartet is of the form (ab|ab),
+ * after eri_compute wrote its blocks to `blocks` (device): bounds[q] =
+ * sqrt(max_i |(ab|ab)_ii|) (device, nq doubles), the factor Q_ab of the
+ * Cauchy-Schwarz bound |(ab|cd)| <= Q_ab Q_cd used to screen quartet lists.
+ * Asynchronous on stream.  ERI_EINVAL for other plans. */
+int eri_schwarz(const eri_plan_t* plan, const double* blocks, double* bounds, void* stream);
+
+/* Preferred tier for a class (la lb | lc ld) when a plan asks for tier 0:
+ * written by the autotuner (paper_2605_10312_gb300.tune); 0 clears the
+ * entry.  A preference a class cannot honour falls back to the static rule.
+ * Applies to plans built afterwards, process-wide. */
+int eri_set_class_tier(int la, int lb, int lc, int ld, int tier);
+
+/* Capture eri_compute(plan, out, stream) into a CUDA graph held by the plan
+ * (stream must not be the legacy default stream; launch timing is off in the
+ * graph), and replay it with eri_plan_graph_launch: all of the plan's class
+ * launches go out as one graph launch. */
+int eri_plan_graph_capture(eri_plan_t* plan, double* out, void* stream);
+int eri_plan_graph_launch(eri_plan_t* plan, void* stream);
+
 /* Release the plan and its device memory (synchronises the device first). */
 int eri_plan_destroy(eri_plan_t* plan);
 

@@ -23,7 +23,7 @@ struct EriCoopArgs {
   const uint4* __restrict__ ph2;      // Phase-2 descriptors
   const uint32_t* __restrict__ steps2;
   const double* __restrict__ c2s;     // transform coefficient table
-  double* __restrict__ gvals;         // [team][nslot - smem_slots] value slots beyond shared memory
+  double* __restrict__ gvals;         // unused: every value slot is in shared memory
   double* __restrict__ gH;            // [team][nh] when H is not in shared memory
   int32_t nw1, nw2;
   int32_t nh, nslot, L;
@@ -106,62 +106,51 @@ __device__ __forceinline__ void eri_coop_row(const EriPairPrim& bp, const EriPai
   row[54] = -pq.tz;
 }
 
-// Phase-1 nodes (see the generator's coop module for the descriptor).  A
-// lane's two nodes of a step belong to one wave and so never alias: all
-// operands are loaded before either result is stored, letting the two FMA
-// chains interleave.
-template <typename Ptr>
-__device__ __forceinline__ void eri_coop_load1(const uint4& d, const Ptr& ptr, double (&v)[5]) {
-  const int side = (d.w >> 16) & 3;
-  if (side >= 2) return;
-  v[0] = *ptr(d.y & 0xFFFF);
-  v[1] = *ptr(d.y >> 16);
-  if ((d.w >> 20) & 31) {
-    v[2] = *ptr(d.z & 0xFFFF);
-    v[3] = *ptr(d.z >> 16);
+// Phase-1 nodes (descriptor: see the generator's coop module).  Operands
+// are value slots in the team's shared memory; a lane's two nodes of a step
+// belong to one wave and never alias, so both nodes' operands are loaded
+// before either result is stored and the two FMA chains interleave.
+struct EriCoopOps {
+  double a, b, c, d, e;
+};
+
+__device__ __forceinline__ void eri_coop_load1(const uint4& d, const double* V, EriCoopOps& v) {
+  const unsigned meta = d.w >> 16;
+  if (meta & 0xC000u) return;  // no-op or base node
+  v.a = V[d.y & 0xFFFF];
+  v.b = V[d.y >> 16];
+  if (meta & (31u << 4)) {
+    v.c = V[d.z & 0xFFFF];
+    v.d = V[d.z >> 16];
   }
-  if ((d.w >> 25) & 31) v[4] = *ptr(d.w & 0xFFFF);
+  if (meta & (15u << 9)) v.e = V[d.w & 0xFFFF];
 }
 
-__device__ __forceinline__ double eri_coop_eval1(const uint4& d, const double* row, const double (&v)[5]) {
-  const int side = (d.w >> 16) & 3;
-  const int k = (d.w >> 20) & 31;
-  if (side == 2) return row[k];
-  const int axis = (d.w >> 18) & 3;
-  const int k3 = (d.w >> 25) & 31;
-  const int cb = 17 + 6 * side + axis;
-  double x = row[cb] * v[0];
-  x = fma(row[cb + 3], v[1], x);
-  if (k) x = fma(row[28 + 8 * side + k], fma(row[53 + side], v[3], v[2]), x);
-  if (k3) x = fma(row[44 + k3], v[4], x);
+__device__ __forceinline__ double eri_coop_eval1(const uint4& d, const double* row, const EriCoopOps& v) {
+  const unsigned meta = d.w >> 16;
+  const unsigned k = (meta >> 4) & 31;
+  if (meta & 0x4000u) return row[k];  // base node: pref * F_m
+  const unsigned cgo = meta & 15, k3 = (meta >> 9) & 15, side = (meta >> 13) & 1;
+  double x = row[17 + cgo] * v.a;
+  x = fma(row[20 + cgo], v.b, x);
+  if (k) x = fma(row[28 + 8 * side + k], fma(row[53 + side], v.d, v.c), x);
+  if (k3) x = fma(row[44 + k3], v.e, x);
   return x;
 }
 
-template <bool HSM, typename Ptr>
-__device__ __forceinline__ void eri_coop_store1(const uint4& d, double x, const Ptr& ptr, double* Hs) {
-  if (((d.w >> 16) & 3) == 3) return;
-  if (d.w & (1u << 30)) *ptr(d.x & 0xFFFF) = x;
-  const unsigned h = d.x >> 16;
+template <bool HSM>
+__device__ __forceinline__ void eri_coop_store1(const uint4& d, double x, double* V, double* H) {
+  if ((d.w >> 16) & 0x8000u) return;
+  const unsigned dst = d.x & 0xFFFF, h = d.x >> 16;
+  if (dst != 0xFFFF) V[dst] = x;
   if (h) {
     // each target has one owner lane per wave: shared-memory H is updated
     // in place, global H by a fire-and-forget reduction
     if (HSM)
-      Hs[h - 1] += x;
+      H[h - 1] += x;
     else
-      atomicAdd(Hs + (h - 1), x);
+      atomicAdd(H + (h - 1), x);
   }
-}
-
-template <bool HSM, typename Ptr>
-__device__ __forceinline__ void eri_coop_node2(const uint4& da, const uint4& db, const double* row, const Ptr& ptr,
-                                               double* Hs) {
-  double va[5], vb[5];
-  eri_coop_load1(da, ptr, va);
-  eri_coop_load1(db, ptr, vb);
-  const double xa = eri_coop_eval1(da, row, va);
-  const double xb = eri_coop_eval1(db, row, vb);
-  eri_coop_store1<HSM>(da, xa, ptr, Hs);
-  eri_coop_store1<HSM>(db, xb, ptr, Hs);
 }
 
 // Phase-2 operations and stores, two per lane per step (never aliasing
@@ -217,21 +206,14 @@ __global__ void __launch_bounds__(128, 4) eri_coop_kernel(const EriLaunchArgs a,
   const int tb = threadIdx.x / T;           // team within the block
   const int l = threadIdx.x - tb * T;       // lane within the team
   const int team = blockIdx.x * (blockDim.x / T) + tb;
-  const int per_team = ERI_COOP_BATCH * ERI_COOP_NC + (HSM ? p.nh : 0) + p.smem_slots;
+  const int per_team = ERI_COOP_BATCH * ERI_COOP_NC + (HSM ? p.nh : 0) + p.nslot;
   double* const rows = eri_coop_smem + (size_t)tb * per_team;
-  double* const S = rows + ERI_COOP_BATCH * ERI_COOP_NC;   // HSM: H then slots; else slots
-  double* const Hs = HSM ? S : p.gH + (size_t)team * p.nh;
+  double* const Hsm = rows + ERI_COOP_BATCH * ERI_COOP_NC;           // H when HSM
+  double* const V = Hsm + (HSM ? p.nh : 0);                         // value slots (shared)
+  double* const Hs = HSM ? Hsm : p.gH + (size_t)team * p.nh;
   const unsigned nh = (unsigned)p.nh;
-  const unsigned lim = HSM ? nh + (unsigned)p.smem_slots : (unsigned)p.smem_slots;
-  double* const Vg = p.gvals + (size_t)team * (p.nslot - p.smem_slots) - lim;
-  // operand id -> address
-  auto ptr = [&](unsigned id) -> double* {
-    if (!HSM) {
-      if (id < nh) return Hs + id;
-      id -= nh;
-    }
-    return id < lim ? S + id : Vg + id;
-  };
+  // Phase-2 operand id -> address: H below nh, value slots above
+  auto ptr = [&](unsigned id) -> double* { return id < nh ? Hs + id : V + (id - nh); };
   for (int q = team; q < a.nq; q += p.nteams) {
     const EriQuartetRec qr = a.quartets[q];
     const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];
@@ -263,7 +245,18 @@ __global__ void __launch_bounds__(128, 4) eri_coop_kernel(const EriLaunchArgs a,
           for (int s = 0; s < steps; ++s) {
             const uint4 dnna = __ldg(dp + 4 * T), dnnb = __ldg(dp + 4 * T + 1);
             dp += 2 * T;
-            eri_coop_node2<HSM>(da, db, row, ptr, Hs);
+            EriCoopOps va, vb;
+            eri_coop_load1(da, V, va);
+            eri_coop_load1(db, V, vb);
+            const double xa = eri_coop_eval1(da, row, va);
+            const double xb = eri_coop_eval1(db, row, vb);
+            if (HSM) {
+              eri_coop_store1<true>(da, xa, V, Hsm);
+              eri_coop_store1<true>(db, xb, V, Hsm);
+            } else {
+              eri_coop_store1<false>(da, xa, V, Hs);
+              eri_coop_store1<false>(db, xb, V, Hs);
+            }
             da = dna;
             db = dnb;
             dna = dnna;

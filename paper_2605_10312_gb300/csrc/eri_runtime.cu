@@ -427,14 +427,20 @@ struct eri_plan_s {
   int64_t scratch_stride = 0;
   double h2d_bytes = 0;
   bool zero_out = false;  // chunks reduce into their block: eri_compute zeroes the output first
+  std::vector<int32_t> nab;          // (ab|ab) plans: components of ab per quartet (else empty)
+  DevBuf<int64_t> d_offsets;
+  DevBuf<int32_t> d_nab;
+  cudaGraphExec_t graph_exec = nullptr;
   bool timing = false;
   std::vector<cudaEvent_t> events;  // two per launch: pair set-up, then buckets
   ~eri_plan_s() {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
   }
 };
 
 static int nfun(int l, bool cart) { return cart ? (l + 1) * (l + 2) / 2 : 2 * l + 1; }
+int preferred_tier(const int ls[4]);
 
 extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
                         int64_t nq, const eri_opts* opts_in, eri_plan_t** plan_out) {
@@ -709,8 +715,14 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
     const void* regfn = (rit != L.reg.end() && default_opts) ? rit->second : nullptr;
     const size_t smem_need = prog ? (size_t)prog->nslot * 128 * sizeof(double) : 0;
     int tier = opts.tier;
-    if (tier == 0)
-      tier = regfn ? TIER_REG : cp ? TIER_COOP : (prog && smem_need <= L.smem_optin ? TIER_SHARED : TIER_GLOBAL);
+    if (tier == 0) {
+      // the autotuner's choice when it is feasible, else the static rule
+      const int pt = preferred_tier(b.ls);
+      const bool ok = (pt == TIER_REG && regfn) || (pt == TIER_COOP && cp) ||
+                      (pt == TIER_SHARED && prog && smem_need <= L.smem_optin) || (pt == TIER_GLOBAL && prog);
+      tier = ok ? pt
+                : regfn ? TIER_REG : cp ? TIER_COOP : (prog && smem_need <= L.smem_optin ? TIER_SHARED : TIER_GLOBAL);
+    }
     if (tier == TIER_REG && !regfn)
       return fail(ERI_EUNSUPPORTED, "no register-tier kernel for this class/options");
     if (tier == TIER_COOP && !cp)
@@ -757,14 +769,9 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
       const size_t rows = eri_coop_rows_bytes() / sizeof(double);
       for (int h_in = 1; h_in >= 0; --h_in) {
         for (int tpb = 128 / cp->T; tpb >= 1; tpb /= 2) {
-          size_t slots = cp->nslot;
-          size_t per_team = rows + slots + (h_in ? (size_t)cp->nh : 0);
-          if (per_team * tpb * sizeof(double) > L.smem_optin) {
-            if (h_in) continue;
-            if ((rows + 64) * tpb * sizeof(double) > L.smem_optin) continue;
-            slots = std::min<size_t>(cp->nslot, L.smem_optin / sizeof(double) / tpb - rows);
-            per_team = rows + slots;
-          }
+          // every value slot lives in shared memory; H too when it fits
+          const size_t per_team = rows + cp->nslot + (h_in ? (size_t)cp->nh : 0);
+          if (per_team * tpb * sizeof(double) > L.smem_optin) continue;
           const size_t bsm = per_team * tpb * sizeof(double);
           const int bps = (int)std::min<size_t>(16 * 32 / (tpb * cp->T), std::max<size_t>(1, smem_sm / (bsm + reserve)));
           const int warps = bps * tpb * cp->T / 32;
@@ -772,13 +779,15 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
           if (warps > best_warps) {
             best_warps = warps;
             b.h_in_smem = h_in;
-            b.smem_slots = (int)slots;
+            b.smem_slots = cp->nslot;
             b.smem = bsm;
             b.block = tpb * cp->T;
             b.grid = bps;  // blocks per SM for now
           }
         }
       }
+      if (best_warps < 0)
+        return fail(ERI_EUNSUPPORTED, "class does not fit the team-cooperative tier's shared memory");
       const int tpb = b.block / cp->T;
       b.grid = (int)std::min<int64_t>((b.count + tpb - 1) / tpb, (int64_t)L.nsm * b.grid);
       b.nteams = b.grid * tpb;
@@ -817,6 +826,21 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
     return rc;
   plan->npair = (int)pin.size();
   plan->npprim = pprim;
+  {
+    // a plan whose every quartet is (ab|ab) can also produce Schwarz bounds
+    bool diag = true;
+    std::vector<int32_t> nab(nq);
+    for (int64_t q = 0; q < nq && diag; ++q) {
+      const int32_t* s4 = quartets + 4 * q;
+      diag = s4[0] == s4[2] && s4[1] == s4[3];
+      nab[q] = nfun(shells[s4[0]].l, cart) * nfun(shells[s4[1]].l, cart);
+    }
+    if (diag) {
+      plan->nab = nab;
+      std::vector<int64_t> offs(plan->offsets.begin(), plan->offsets.end() - 1);
+      if ((rc = plan->d_offsets.upload(offs, "offsets")) || (rc = plan->d_nab.upload(nab, "pair sizes"))) return rc;
+    }
+  }
   plan->h2d_bytes = (double)(dsh.size() * sizeof(DevShell) + 2 * ex.size() * sizeof(double) +
                              pin.size() * sizeof(DevPairIn) + plist.size() * sizeof(uint32_t) +
                              recs.size() * sizeof(EriQuartetRec));
@@ -1084,5 +1108,90 @@ extern "C" int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* st
     p.L = b.prog->L;
     CUDA_OR(eri_exec_launch(0, &a, &p, grid, 128, 0, stream), "executor launch (fixed scratch)");
   }
+  return ERI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Schwarz bounds, tier table, CUDA-graph replay
+// ---------------------------------------------------------------------------
+// Q_q = sqrt(max_i |block_q[i, i]|) over the (ab|ab)-shaped block of quartet
+// q (the diagonal of the n_ab x n_ab matrix): the Schwarz factor of pair ab,
+// |(ab|cd)| <= Q_ab Q_cd.
+__global__ void eri_schwarz_kernel(const double* __restrict__ blocks, const int64_t* __restrict__ off,
+                                   const int32_t* __restrict__ nab, int64_t nq, double* __restrict__ q) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const double* b = blocks + off[i];
+  const int n = nab[i];
+  double m = 0.0;
+  for (int k = 0; k < n; ++k) m = fmax(m, fabs(b[(int64_t)k * n + k]));
+  q[i] = sqrt(m);
+}
+
+extern "C" int eri_schwarz(const eri_plan_t* plan, const double* blocks, double* bounds, void* stream_) {
+  if (!plan || !blocks || !bounds) return fail(ERI_EINVAL, "NULL argument");
+  const int64_t nq = plan->nq;
+  if (nq == 0) return ERI_OK;
+  if (plan->nab.empty()) return fail(ERI_EINVAL, "plan is not made of (ab|ab) quartets");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  const int threads = 256;
+  eri_schwarz_kernel<<<(unsigned)((nq + threads - 1) / threads), threads, 0, stream>>>(
+      blocks, plan->d_offsets.p, plan->d_nab.p, nq, bounds);
+  CUDA_OR(cudaGetLastError(), "schwarz launch");
+  return ERI_OK;
+}
+
+namespace {
+std::mutex g_tier_mu;
+std::map<std::vector<int>, int> g_tier_table;  // class -> preferred tier (autotuner)
+}  // namespace
+
+extern "C" int eri_set_class_tier(int la, int lb, int lc, int ld, int tier) {
+  if (la < 0 || lb < 0 || lc < 0 || ld < 0 || la > ERI_MAX_L || lb > ERI_MAX_L || lc > ERI_MAX_L ||
+      ld > ERI_MAX_L || tier < 0 || tier > 4)
+    return fail(ERI_EINVAL, "bad class or tier");
+  std::lock_guard<std::mutex> g(g_tier_mu);
+  if (tier == 0)
+    g_tier_table.erase({la, lb, lc, ld});
+  else
+    g_tier_table[{la, lb, lc, ld}] = tier;
+  return ERI_OK;
+}
+
+int preferred_tier(const int ls[4]) {
+  std::lock_guard<std::mutex> g(g_tier_mu);
+  auto it = g_tier_table.find({ls[0], ls[1], ls[2], ls[3]});
+  return it == g_tier_table.end() ? 0 : it->second;
+}
+
+extern "C" int eri_plan_graph_capture(eri_plan_t* plan, double* out, void* stream_) {
+  if (!plan) return fail(ERI_EINVAL, "NULL plan");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (stream == nullptr) return fail(ERI_EINVAL, "capture needs a non-default stream");
+  if (plan->graph_exec) {
+    cudaGraphExecDestroy(plan->graph_exec);
+    plan->graph_exec = nullptr;
+  }
+  const bool timing = plan->timing;
+  plan->timing = false;
+  CUDA_OR(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  const int rc = eri_compute(plan, out, stream_);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(stream, &graph);
+  plan->timing = timing;
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(ERI_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&plan->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(ERI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return ERI_OK;
+}
+
+extern "C" int eri_plan_graph_launch(eri_plan_t* plan, void* stream_) {
+  if (!plan || !plan->graph_exec) return fail(ERI_ESTATE, "no captured graph (call eri_plan_graph_capture)");
+  CUDA_OR(cudaGraphLaunch(plan->graph_exec, (cudaStream_t)stream_), "cudaGraphLaunch");
   return ERI_OK;
 }

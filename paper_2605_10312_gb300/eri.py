@@ -76,6 +76,14 @@ def library(path: str = LIB):
                                              ctypes.c_void_p]
         lib.eri_compute_fixed_scratch.restype = ctypes.c_int
         lib.eri_compute_fixed_scratch.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_schwarz.restype = ctypes.c_int
+        lib.eri_schwarz.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_set_class_tier.restype = ctypes.c_int
+        lib.eri_set_class_tier.argtypes = [ctypes.c_int] * 5
+        lib.eri_plan_graph_capture.restype = ctypes.c_int
+        lib.eri_plan_graph_capture.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_plan_graph_launch.restype = ctypes.c_int
+        lib.eri_plan_graph_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         lib.eri_plan_destroy.restype = ctypes.c_int
         lib.eri_plan_destroy.argtypes = [ctypes.c_void_p]
         lib.eri_last_error.restype = ctypes.c_char_p
@@ -186,6 +194,20 @@ class Plan:
         _check(library().eri_compute_fixed_scratch(self._h, out.data_ptr(), _stream_handle(stream)))
         return out
 
+    def schwarz(self, blocks, bounds, stream=None):
+        """Schwarz factors Q_ab of an (ab|ab) plan from its computed blocks
+        (both CUDA float64 tensors)."""
+        _check(library().eri_schwarz(self._h, blocks.data_ptr(), bounds.data_ptr(), _stream_handle(stream)))
+        return bounds
+
+    def capture(self, out, stream):
+        """Capture compute(out) on ``stream`` (not the default stream) into a
+        CUDA graph; replay with ``replay``."""
+        _check(library().eri_plan_graph_capture(self._h, out.data_ptr(), _stream_handle(stream)))
+
+    def replay(self, stream=None):
+        _check(library().eri_plan_graph_launch(self._h, _stream_handle(stream)))
+
     def compute_host(self, out, stream=None):
         """Compute and copy every block into ``out`` (a contiguous CPU float64
         tensor, ideally pinned); asynchronous on ``stream``."""
@@ -197,6 +219,13 @@ class Plan:
             raise ValueError("out is too small")
         _check(library().eri_compute_host(self._h, out.data_ptr(), _stream_handle(stream)))
         return out
+
+
+def set_class_tier(ls, tier):
+    """Process-wide preferred tier for class ls = (la, lb, lc, ld) (see the
+    autotuner); tier name or 0 to clear."""
+    t = TIERS[tier] if isinstance(tier, str) else int(tier)
+    _check(library().eri_set_class_tier(*[int(x) for x in ls], t))
 
 
 def eri(basis, quartets, device="cuda", **opts):

@@ -11,10 +11,16 @@ thousands of values still fits in shared memory; the accumulator bank H is
 addressed separately (shared memory when it fits, else a team-private global
 region).
 
-Operand ids in the descriptors: id < nh is accumulator H[id]; id >= nh is
-value slot id - nh.
-
-Phase-1 descriptor (uint32 x4) as in ``encode``, plus side = 3 = no-op.
+Phase-1 descriptor (uint16 x8): dst slot (0xFFFF: not kept), h = target + 1
+(0: none), operand slots s0..s4, and meta:
+  bits 0-3   6 side + axis  (coefficient rows of P-A / W-P or Q-C / W-Q)
+  bits 4-8   k (second Obara-Saika term; for a base node the Boys order m)
+  bits 9-12  k3 (cross term)
+  bit 13     side (0 bra, 1 ket)
+  bit 14     base node [00|00]^(m)
+  bit 15     no-op
+Phase-2 operand ids: id < nh is accumulator H[id]; id >= nh is value slot
+id - nh.
 Phase-2 descriptor kinds: 0 HRR, 1 LIN (n <= 4), 2 STORE, 3 no-op; a
 transform row of more than four terms becomes a chain of LIN descriptors in
 successive waves, each continuing with 1.0 x the previous partial sum.
@@ -28,7 +34,7 @@ import numpy as np
 
 from .encode import coef_table
 
-NOP1 = np.array([0, 0, 0, 3 << 16], dtype=np.uint32)
+NOP1 = np.array([0xFFFF, 0, 0, 0x8000 << 16], dtype=np.uint32)
 NOP2 = np.array([3, 0, 0, 0], dtype=np.uint32)
 MAX_ID = 65535
 
@@ -153,28 +159,30 @@ def build(prog, T=128):
 
     def row1(v):
         ts = g.terms[v]
-        dst = nh + int(slot1[v]) if consumed[v] else 0
+        dst = int(slot1[v]) if consumed[v] else 0xFFFF
         h = g.target.get(v)
         src = [0] * 5
-        side = axis = k = k3 = 0
+        meta = 0
         if not ts:
-            side, k = 2, g.keys[v][2]
+            meta = (1 << 14) | (g.keys[v][2] << 4)
         for (kind, val), p in ts:
-            s = nh + int(slot1[p])
+            s_ = int(slot1[p])
             if kind in ("PA", "QC"):
-                src[0], side, axis = s, (0 if kind == "PA" else 1), val
+                side = 0 if kind == "PA" else 1
+                src[0] = s_
+                meta |= (6 * side + val) | (side << 13)
             elif kind in ("WP", "WQ"):
-                src[1] = s
+                src[1] = s_
             elif kind in ("c1z", "c1e"):
-                src[2], k = s, val
+                src[2] = s_
+                meta |= val << 4
             elif kind in ("c2z", "c2e"):
-                src[3] = s
+                src[3] = s_
             elif kind == "c3":
-                src[4], k3 = s, val
+                src[4] = s_
+                meta |= val << 9
         return np.array([dst | ((h + 1) << 16 if h is not None else 0), src[0] | (src[1] << 16),
-                         src[2] | (src[3] << 16),
-                         src[4] | (side << 16) | (axis << 18) | (k << 20) | (k3 << 25) | (int(consumed[v]) << 30)],
-                        dtype=np.uint32)
+                         src[2] | (src[3] << 16), src[4] | (meta << 16)], dtype=np.uint32)
 
     ph1, steps1 = _pack(waves1, row1, T, NOP1)
 
@@ -272,7 +280,7 @@ def build(prog, T=128):
 
     ph2, steps2 = _pack(waves2, row2, T, NOP2)
     nslot = max(int(nslot1), int(nslot2))
-    if nh + nslot > MAX_ID:
+    if nslot >= 0xFFFF or nh + nslot > MAX_ID:
         raise ValueError("class {} needs {} ids".format(prog.ls, nh + nslot))
     eff1 = len(g) / max(1, int(steps1.sum()) * T * ILP)
     eff2 = len(sched) / max(1, int(steps2.sum()) * T * ILP)

@@ -1,0 +1,34 @@
+"""Schwarz screening on the device (the batched mixed-class workload).
+
+The Schwarz factor of a shell pair, Q_ab = sqrt(max |(ab|ab)|), is computed
+from the pair's own diagonal block, evaluated by the ERI kernels, and reduced
+on the device (eri_schwarz); quartets with Q_ab Q_cd below the threshold are
+dropped (|(ab|cd)| <= Q_ab Q_cd).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import eri, synth
+
+
+def pair_bounds(basis, pairs=None, stream=None):
+    """(pairs [npair, 2], Q [npair]) for every unique shell pair (a >= b)."""
+    import torch
+    if pairs is None:
+        pairs = synth.shell_pairs(basis.nshell)
+    diag = np.ascontiguousarray(np.concatenate([pairs, pairs], axis=1).astype(np.int32))
+    p = eri.Plan(basis, diag)
+    blocks = torch.empty(max(1, p.output_count), dtype=torch.float64, device="cuda")
+    bounds = torch.empty(max(1, diag.shape[0]), dtype=torch.float64, device="cuda")
+    p.compute(blocks, stream)
+    p.schwarz(blocks, bounds, stream)
+    q = bounds[: diag.shape[0]].cpu().numpy()
+    p.close()
+    return pairs, q
+
+
+def screened(basis, threshold=1e-10, stream=None):
+    """Unique quartets of the basis surviving Schwarz screening, [n, 4]."""
+    pairs, q = pair_bounds(basis, stream=stream)
+    return synth.screened_quartets(q, pairs, threshold)

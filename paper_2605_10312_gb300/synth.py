@@ -221,3 +221,100 @@ def with_centers(basis: Basis, centers: np.ndarray) -> Basis:
               basis.shell_center, basis.shell_prim, basis.exps, basis.coefs, dict(basis.meta))
     b.validate()
     return b
+
+
+# ---------------------------------------------------------------------------
+# Workload: water clusters (batched mixed-class and serving workloads)
+# ---------------------------------------------------------------------------
+# shell layouts per element: (l, K) in order; K runs from 6 for the first s
+# shell down to 1 for the polarisation shells
+WATER_LAYOUTS = {
+    "dz": {"O": [(0, 6), (0, 3), (0, 1), (1, 3), (1, 1), (2, 1)],
+           "H": [(0, 3), (0, 1), (1, 1)]},
+    "tz": {"O": [(0, 6), (0, 3), (0, 1), (0, 1), (1, 3), (1, 1), (1, 1), (2, 1), (2, 1), (3, 1)],
+           "H": [(0, 3), (0, 1), (0, 1), (1, 1), (1, 1), (2, 1)]},
+}
+
+
+def water_positions(nwater: int, rng: np.random.Generator, density=0.02, min_oo=2.8, roh=0.96, angle=104.5):
+    """Random sequential insertion of rigid waters (O-H 0.96 A, H-O-H 104.5
+    deg, uniform random orientation) with O-O >= 2.8 A in a cube sized for
+    `density` molecules per cubic Angstrom.  Returns [3 * nwater, 3] Angstrom,
+    ordered O, H, H per molecule."""
+    side = (nwater / density) ** (1.0 / 3.0)
+    oxy = []
+    tries = 0
+    while len(oxy) < nwater:
+        tries += 1
+        if tries > 1000 * nwater:
+            raise RuntimeError("could not place the waters")
+        p = rng.uniform(0.0, side, size=3)
+        if all(np.linalg.norm(p - o) >= min_oo for o in oxy):
+            oxy.append(p)
+    half = np.deg2rad(angle) / 2.0
+    h1 = roh * np.array([np.sin(half), 0.0, np.cos(half)])
+    h2 = roh * np.array([-np.sin(half), 0.0, np.cos(half)])
+    out = []
+    for o in oxy:
+        R = random_rotation(rng)
+        out.extend([o, o + R @ h1, o + R @ h2])
+    return np.array(out)
+
+
+def element_basis(rng: np.random.Generator, layout):
+    """One synthetic basis per element: exponents log-uniform in [0.05, 500]
+    sorted tight to diffuse within each shell, coefficients uniform in
+    [0.1, 1]."""
+    out = {}
+    for el in ("O", "H"):
+        shells = []
+        for l, k in layout[el]:
+            exps = np.sort(log_uniform(rng, 0.05, 500.0, k))[::-1]
+            shells.append((l, exps, rng.uniform(0.1, 1.0, size=k)))
+        out[el] = shells
+    return out
+
+
+def water_cluster(nwater: int, seed: int = 3, layout: str = "dz"):
+    """Cluster of `nwater` waters with the per-element shell layout
+    (`dz`: O 3s 2p 1d, H 2s 1p; `tz`: O 4s 3p 2d 1f, H 3s 2p 1d).  Returns a
+    Basis (atoms O, H, H per molecule) with meta['atoms']."""
+    rng = np.random.default_rng(seed)
+    pos = water_positions(nwater, rng) * ANGSTROM_TO_BOHR
+    eb = element_basis(rng, WATER_LAYOUTS[layout])
+    bb = _BasisBuilder()
+    for i, p in enumerate(pos):
+        el = "O" if i % 3 == 0 else "H"
+        c = bb.add_center(p)
+        for l, exps, coefs in eb[el]:
+            bb.add_shell(l, c, exps, coefs)
+    return bb.build(workload="water_cluster", nwater=nwater, seed=seed, layout=layout, atoms=3 * nwater)
+
+
+def shell_pairs(nshell: int) -> np.ndarray:
+    """Unique shell pairs (a >= b), [npair, 2]."""
+    a, b = np.tril_indices(nshell)
+    return np.stack([a, b], axis=1).astype(np.int32)
+
+
+def screened_quartets(pair_bound: np.ndarray, pairs: np.ndarray, threshold: float) -> np.ndarray:
+    """Unique quartets (pair P >= pair Q) whose Schwarz bound
+    Q_P Q_Q >= threshold, given per-pair bounds; [n, 4] int32.  Pure
+    bookkeeping on bounds computed elsewhere."""
+    order = np.argsort(-pair_bound, kind="stable")
+    qb = pair_bound[order]
+    out = []
+    for i in range(order.size):
+        if qb[i] * qb[0] < threshold:
+            break
+        # partners j <= i in the sorted order with qb[i] qb[j] >= threshold:
+        # a prefix, since qb is sorted descending
+        n = int(np.searchsorted(-qb[: i + 1], -threshold / qb[i], side="right")) if qb[i] > 0 else 0
+        if n == 0:
+            continue
+        P = pairs[order[i]]
+        Q = pairs[order[:n]]
+        out.append(np.concatenate([np.broadcast_to(P, (n, 2)), Q], axis=1))
+    if not out:
+        return np.zeros((0, 4), dtype=np.int32)
+    return np.ascontiguousarray(np.concatenate(out).astype(np.int32))

@@ -242,23 +242,25 @@ def run_coop(cp, prog, basis, quartets):
                     for wave in waves(cp.ph1, cp.steps1):
                         res = []  # all lanes read before any writes (wave barrier semantics)
                         for w0, w1, w2, w3 in wave.tolist():
-                            side = (w3 >> 16) & 3
-                            if side == 3:
+                            meta = w3 >> 16
+                            if meta & 0x8000:
                                 continue
                             dst, h = w0 & 0xFFFF, w0 >> 16
-                            axis, k, k3 = (w3 >> 18) & 3, (w3 >> 20) & 31, (w3 >> 25) & 31
-                            if side == 2:
-                                x = F[:, k]
+                            V = lambda s_: S[nh + s_]
+                            if meta & 0x4000:
+                                x = F[:, (meta >> 4) & 31]
                             else:
-                                x = geo[2 * side][axis] * S[w1 & 0xFFFF] + geo[2 * side + 1][axis] * S[w1 >> 16]
+                                cgo, k, k3, side = meta & 15, (meta >> 4) & 31, (meta >> 9) & 15, (meta >> 13) & 1
+                                axis = cgo - 6 * side
+                                x = geo[2 * side][axis] * V(w1 & 0xFFFF) + geo[2 * side + 1][axis] * V(w1 >> 16)
                                 if k:
-                                    x = x + k * c1[side] * S[w2 & 0xFFFF] + k * c2[side] * S[w2 >> 16]
+                                    x = x + k * c1[side] * V(w2 & 0xFFFF) + k * c2[side] * V(w2 >> 16)
                                 if k3:
-                                    x = x + k3 * c3 * S[w3 & 0xFFFF]
-                            res.append((dst, h, (w3 >> 30) & 1, x))
-                        for dst, h, st, x in res:
-                            if st:
-                                S[dst] = x
+                                    x = x + k3 * c3 * V(w3 & 0xFFFF)
+                            res.append((dst, h, x))
+                        for dst, h, x in res:
+                            if dst != 0xFFFF:
+                                S[nh + dst] = x
                             if h:
                                 S[h - 1] += x
     ctab = coef_table()
