@@ -90,7 +90,7 @@ def _class_job(args):
         # teams' live sets fit in shared memory, else four warps
         from paper_2605_10312_gb300.gen import coop
         cp = coop.choose(prog)
-        rec["coop"] = dict(T=cp.T, nh=cp.nh, nslot=cp.nslot, L=cp.L, dims=cp.out_dims, steps1=cp.steps1.tobytes(),
+        rec["coop"] = dict(T=cp.T, ilp=cp.ilp, nh=cp.nh, nslot=cp.nslot, L=cp.L, dims=cp.out_dims, steps1=cp.steps1.tobytes(),
                            steps2=cp.steps2.tobytes(), nw1=int(cp.steps1.shape[0]), nw2=int(cp.steps2.shape[0]),
                            ph1=cp.ph1.tobytes(), ph2=cp.ph2.tobytes(), n1=int(cp.ph1.shape[0]),
                            n2=int(cp.ph2.shape[0]), eff1=cp.eff1, eff2=cp.eff2)
@@ -129,7 +129,7 @@ def write_blob(path, recs, boys, c2s):
         f.write(struct.pack("<I", len(coops)))
         for r in coops:
             o, c = r["opts"], r["coop"]
-            f.write(struct.pack("<8b", *r["ls"], AXIS[o[0]], SCHED[o[1]], SPH[o[2]], 0))
+            f.write(struct.pack("<8b", *r["ls"], AXIS[o[0]], SCHED[o[1]], SPH[o[2]], c["ilp"]))
             f.write(struct.pack("<12i", c["T"], c["nh"], c["nslot"], c["L"], c["nw1"], c["nw2"], c["n1"], c["n2"],
                                 *c["dims"]))
             f.write(struct.pack("<2d", r["flops_prim"], r["flops_p2"]))
@@ -208,14 +208,15 @@ def build(force=False, jobs=None, log=print):
         # class table for the docs and the benchmark: per-class counts
         with open(os.path.join(BUILD, "classes.tsv"), "w") as f:
             f.write("la\tlb\tlc\tld\ttier\tvrr_nodes\tpeak_live\tnslot\tnh\tnout\tper_prim_flops\tp2_flops"
-                    "\tcoop_T\tcoop_nslot\tcoop_eff1\tcoop_eff2\n")
+                    "\tcoop_T\tcoop_ilp\tcoop_nslot\tcoop_eff1\tcoop_eff2\n")
             for r in sorted(recs, key=lambda r: r["ls"]):
                 c = r["counts"]
                 cp = r.get("coop")
                 f.write("\t".join(str(x) for x in (*r["ls"], "reg" if "cuda" in r else "coop", c["vrr_nodes"],
                                                    c["peak_live"], r["nslot"], c["nh"], c["nout"],
                                                    c["per_prim_flops"], c["p2_flops"],
-                                                   cp["T"] if cp else "", cp["nslot"] if cp else "",
+                                                   cp["T"] if cp else "", cp["ilp"] if cp else "",
+                                                   cp["nslot"] if cp else "",
                                                    round(cp["eff1"], 3) if cp else "",
                                                    round(cp["eff2"], 3) if cp else "")) + "\n")
         open(stamp, "w").write(gen_key)

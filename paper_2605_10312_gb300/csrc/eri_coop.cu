@@ -200,8 +200,8 @@ __device__ __forceinline__ void eri_coop_exec2(const uint4& d, const double (&v)
 // HSM: the accumulators H share the team's shared-memory region with the
 // value slots ([H | slots], operand id = offset); otherwise H is a
 // team-private global region and slots follow at id - nh.
-template <int T, bool HSM>
-__global__ void __launch_bounds__(128, 4) eri_coop_kernel(const EriLaunchArgs a, const EriCoopArgs p) {
+template <int T, bool HSM, int ILP>
+__global__ void __launch_bounds__(128, ILP == 4 ? 2 : 4) eri_coop_kernel(const EriLaunchArgs a, const EriCoopArgs p) {
   extern __shared__ double eri_coop_smem[];
   const int tb = threadIdx.x / T;           // team within the block
   const int l = threadIdx.x - tb * T;       // lane within the team
@@ -234,33 +234,41 @@ __global__ void __launch_bounds__(128, 4) eri_coop_kernel(const EriLaunchArgs a,
       eri_team_sync<T>();
       for (int pi = 0; pi < nb; ++pi) {
         const double* const row = rows + pi * ERI_COOP_NC;
-        // a step gives each lane two descriptors (independent nodes of the
+        // a step gives each lane ILP descriptors (independent nodes of the
         // same wave); they are loaded two steps ahead -- the stream ends in
         // two no-op steps -- so the L2 latency overlaps the previous step
-        const uint4* dp = p.ph1 + 2 * l;
-        uint4 da = __ldg(dp), db = __ldg(dp + 1);
-        uint4 dna = __ldg(dp + 2 * T), dnb = __ldg(dp + 2 * T + 1);
+        const uint4* dp = p.ph1 + ILP * l;
+        uint4 d[ILP], dn[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+          d[u] = __ldg(dp + u);
+          dn[u] = __ldg(dp + ILP * T + u);
+        }
         for (int w = 0; w < p.nw1; ++w) {
           const int steps = (int)__ldg(p.steps1 + w);
           for (int s = 0; s < steps; ++s) {
-            const uint4 dnna = __ldg(dp + 4 * T), dnnb = __ldg(dp + 4 * T + 1);
-            dp += 2 * T;
-            EriCoopOps va, vb;
-            eri_coop_load1(da, V, va);
-            eri_coop_load1(db, V, vb);
-            const double xa = eri_coop_eval1(da, row, va);
-            const double xb = eri_coop_eval1(db, row, vb);
-            if (HSM) {
-              eri_coop_store1<true>(da, xa, V, Hsm);
-              eri_coop_store1<true>(db, xb, V, Hsm);
-            } else {
-              eri_coop_store1<false>(da, xa, V, Hs);
-              eri_coop_store1<false>(db, xb, V, Hs);
+            uint4 dnn[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) dnn[u] = __ldg(dp + 2 * ILP * T + u);
+            dp += ILP * T;
+            EriCoopOps v[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) eri_coop_load1(d[u], V, v[u]);
+            double x[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) x[u] = eri_coop_eval1(d[u], row, v[u]);
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+              if (HSM)
+                eri_coop_store1<true>(d[u], x[u], V, Hsm);
+              else
+                eri_coop_store1<false>(d[u], x[u], V, Hs);
             }
-            da = dna;
-            db = dnb;
-            dna = dnna;
-            dnb = dnnb;
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+              d[u] = dn[u];
+              dn[u] = dnn[u];
+            }
           }
           eri_team_sync<T>();
         }
@@ -268,47 +276,60 @@ __global__ void __launch_bounds__(128, 4) eri_coop_kernel(const EriLaunchArgs a,
     }
     // Phase 2 and the stores, once per shell quartet
     double* const o = a.out + qr.out_off;
-    const uint4* dp = p.ph2 + 2 * l;
-    uint4 da = __ldg(dp), db = __ldg(dp + 1);
-    uint4 dna = __ldg(dp + 2 * T), dnb = __ldg(dp + 2 * T + 1);
+    const uint4* dp = p.ph2 + ILP * l;
+    uint4 d[ILP], dn[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      d[u] = __ldg(dp + u);
+      dn[u] = __ldg(dp + ILP * T + u);
+    }
     for (int w = 0; w < p.nw2; ++w) {
       const int steps = (int)__ldg(p.steps2 + w);
       for (int s = 0; s < steps; ++s) {
-        const uint4 dnna = __ldg(dp + 4 * T), dnnb = __ldg(dp + 4 * T + 1);
-        dp += 2 * T;
-        double va[4], vb[4];
-        eri_coop_load2(da, ptr, va);
-        eri_coop_load2(db, ptr, vb);
-        eri_coop_exec2(da, va, bra, ket, qr, o, acc, red, p.c2s, ptr);
-        eri_coop_exec2(db, vb, bra, ket, qr, o, acc, red, p.c2s, ptr);
-        da = dna;
-        db = dnb;
-        dna = dnna;
-        dnb = dnnb;
+        uint4 dnn[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) dnn[u] = __ldg(dp + 2 * ILP * T + u);
+        dp += ILP * T;
+        double v[ILP][4];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) eri_coop_load2(d[u], ptr, v[u]);
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) eri_coop_exec2(d[u], v[u], bra, ket, qr, o, acc, red, p.c2s, ptr);
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+          d[u] = dn[u];
+          dn[u] = dnn[u];
+        }
       }
       eri_team_sync<T>();
     }
   }
 }
 
-extern "C" cudaError_t eri_coop_launch(int T, const EriLaunchArgs* a, const EriCoopArgs* p, int grid, int block,
-                                       size_t smem, cudaStream_t stream) {
+extern "C" cudaError_t eri_coop_launch(int T, int ilp, const EriLaunchArgs* a, const EriCoopArgs* p, int grid,
+                                       int block, size_t smem, cudaStream_t stream) {
   const bool hsm = p->h_in_smem != 0;
-#define ERI_COOP_CASE(TT)                                                  \
-  case TT:                                                                 \
-    if (hsm)                                                               \
-      eri_coop_kernel<TT, true><<<grid, block, smem, stream>>>(*a, *p);    \
-    else                                                                   \
-      eri_coop_kernel<TT, false><<<grid, block, smem, stream>>>(*a, *p);   \
-    break;
-  switch (T) {
-    ERI_COOP_CASE(32)
-    ERI_COOP_CASE(64)
-    ERI_COOP_CASE(128)
-    default:
-      return cudaErrorInvalidValue;
+#define ERI_COOP_GO(TT, II)                                                    \
+  do {                                                                         \
+    if (hsm)                                                                   \
+      eri_coop_kernel<TT, true, II><<<grid, block, smem, stream>>>(*a, *p);    \
+    else                                                                       \
+      eri_coop_kernel<TT, false, II><<<grid, block, smem, stream>>>(*a, *p);   \
+  } while (0)
+  if (ilp == 2) {
+    if (T == 32) ERI_COOP_GO(32, 2);
+    else if (T == 64) ERI_COOP_GO(64, 2);
+    else if (T == 128) ERI_COOP_GO(128, 2);
+    else return cudaErrorInvalidValue;
+  } else if (ilp == 4) {
+    if (T == 32) ERI_COOP_GO(32, 4);
+    else if (T == 64) ERI_COOP_GO(64, 4);
+    else if (T == 128) ERI_COOP_GO(128, 4);
+    else return cudaErrorInvalidValue;
+  } else {
+    return cudaErrorInvalidValue;
   }
-#undef ERI_COOP_CASE
+#undef ERI_COOP_GO
   return cudaGetLastError();
 }
 
@@ -316,9 +337,13 @@ extern "C" cudaError_t eri_coop_launch(int T, const EriLaunchArgs* a, const EriC
 extern "C" size_t eri_coop_rows_bytes(void) { return (size_t)ERI_COOP_BATCH * ERI_COOP_NC * sizeof(double); }
 
 extern "C" cudaError_t eri_coop_set_smem(size_t bytes) {
-  const void* fns[] = {(const void*)eri_coop_kernel<32, true>,  (const void*)eri_coop_kernel<32, false>,
-                       (const void*)eri_coop_kernel<64, true>,  (const void*)eri_coop_kernel<64, false>,
-                       (const void*)eri_coop_kernel<128, true>, (const void*)eri_coop_kernel<128, false>};
+  const void* fns[] = {
+      (const void*)eri_coop_kernel<32, true, 2>,  (const void*)eri_coop_kernel<32, false, 2>,
+      (const void*)eri_coop_kernel<64, true, 2>,  (const void*)eri_coop_kernel<64, false, 2>,
+      (const void*)eri_coop_kernel<128, true, 2>, (const void*)eri_coop_kernel<128, false, 2>,
+      (const void*)eri_coop_kernel<32, true, 4>,  (const void*)eri_coop_kernel<32, false, 4>,
+      (const void*)eri_coop_kernel<64, true, 4>,  (const void*)eri_coop_kernel<64, false, 4>,
+      (const void*)eri_coop_kernel<128, true, 4>, (const void*)eri_coop_kernel<128, false, 4>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

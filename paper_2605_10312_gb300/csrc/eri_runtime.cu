@@ -45,8 +45,8 @@ struct EriCoopArgs {
   int32_t h_in_smem;
   int32_t nteams;
 };
-extern "C" cudaError_t eri_coop_launch(int T, const EriLaunchArgs* a, const EriCoopArgs* p, int grid, int block,
-                                       size_t smem, cudaStream_t stream);
+extern "C" cudaError_t eri_coop_launch(int T, int ilp, const EriLaunchArgs* a, const EriCoopArgs* p, int grid,
+                                       int block, size_t smem, cudaStream_t stream);
 extern "C" cudaError_t eri_coop_set_smem(size_t bytes);
 extern "C" size_t eri_coop_rows_bytes(void);
 
@@ -95,6 +95,7 @@ struct ClassProg {
 struct CoopProg {
   int ls[4];
   int opts[3];
+  int ilp;
   int T, nh, nslot, L, nw1, nw2, n1, n2;
   int dims[4];
   double flops_prim, flops_p2;
@@ -187,6 +188,7 @@ bool load_blob(Library& L, const std::string& path, bool tables) {
       if (!ok) break;
       for (int k = 0; k < 4; ++k) p->ls[k] = hdr[k];
       for (int k = 0; k < 3; ++k) p->opts[k] = hdr[4 + k];
+      p->ilp = hdr[7] ? hdr[7] : 2;
       p->T = iv[0];
       p->nh = iv[1];
       p->nslot = iv[2];
@@ -773,7 +775,11 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
           const size_t per_team = rows + cp->nslot + (h_in ? (size_t)cp->nh : 0);
           if (per_team * tpb * sizeof(double) > L.smem_optin) continue;
           const size_t bsm = per_team * tpb * sizeof(double);
-          const int bps = (int)std::min<size_t>(16 * 32 / (tpb * cp->T), std::max<size_t>(1, smem_sm / (bsm + reserve)));
+          // registers: the 4-nodes-per-lane kernels hold ~230 registers, so at
+          // most 256 of their threads per SM; the others at most 512
+          const size_t max_threads = cp->ilp == 4 ? 256 : 512;
+          const int bps = (int)std::min<size_t>(max_threads / (tpb * cp->T), std::max<size_t>(1, smem_sm / (bsm + reserve)));
+          if (bps < 1) continue;
           const int warps = bps * tpb * cp->T / 32;
           // prefer H in shared memory at equal residency
           if (warps > best_warps) {
@@ -925,7 +931,7 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
       p.smem_slots = b.smem_slots;
       p.h_in_smem = b.h_in_smem;
       p.nteams = b.nteams;
-      CUDA_OR(eri_coop_launch(cp->T, &a, &p, b.grid, b.block, b.smem, stream), "cooperative launch");
+      CUDA_OR(eri_coop_launch(cp->T, cp->ilp, &a, &p, b.grid, b.block, b.smem, stream), "cooperative launch");
     } else {
       EriProgArgs p;
       p.ph1 = b.prog->d_ph1;

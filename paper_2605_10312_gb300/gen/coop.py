@@ -101,12 +101,13 @@ def allocate_over_waves(parents, waves, needs_slot, first_slot=0, pinned_until_e
     return slot, nxt - first_slot
 
 
-ILP = 2  # nodes per lane per step: two independent chains per lane
+ILP = 2  # default nodes per lane per step (independent chains per lane)
 
 
 @dataclass
 class CoopProgram:
     T: int
+    ilp: int
     ph1: np.ndarray        # uint32 [sum steps * T, 4]
     steps1: np.ndarray     # uint32 [nwave1] steps of each wave
     ph2: np.ndarray
@@ -122,9 +123,10 @@ class CoopProgram:
 PREFETCH_STEPS = 2  # no-op steps after the last wave: the executor loads ahead
 
 
-def _pack(waves, rows_of, T, nop):
-    """A step is ILP * T descriptors: lane l takes descriptors ILP*l .. ILP*l +
-    ILP - 1 of the step, so a wave of n nodes spreads over the lanes first."""
+def _pack(waves, rows_of, T, nop, ilp):
+    """A step is ilp * T descriptors: lane l takes descriptors ilp*l .. ilp*l +
+    ilp - 1 of the step, so a wave of n nodes spreads over the lanes first."""
+    ILP = ilp
     W = ILP * T
     steps = []
     out = []
@@ -142,15 +144,16 @@ def _pack(waves, rows_of, T, nop):
     return arr.astype(np.uint32), np.array(steps, dtype=np.uint32)
 
 
-def build(prog, T=128):
-    """CoopProgram of a class program for teams of T lanes."""
+def build(prog, T=128, ilp=ILP):
+    """CoopProgram of a class program for teams of T lanes taking ilp nodes
+    per step."""
     g = prog.g
     nh = prog.nh
     # ---------------- Phase 1
     order_pos = np.empty(len(g), dtype=np.int64)
     order_pos[np.array(prog.order, dtype=np.int64)] = np.arange(len(g))
     par1 = [[p for _, p in ts] for ts in g.terms]
-    waves1 = wave_schedule(par1, order_pos, ILP * T)
+    waves1 = wave_schedule(par1, order_pos, ilp * T)
     consumed = np.zeros(len(g), dtype=bool)
     for ps in par1:
         for p in ps:
@@ -184,7 +187,7 @@ def build(prog, T=128):
         return np.array([dst | ((h + 1) << 16 if h is not None else 0), src[0] | (src[1] << 16),
                          src[2] | (src[3] << 16), src[4] | (meta << 16)], dtype=np.uint32)
 
-    ph1, steps1 = _pack(waves1, row1, T, NOP1)
+    ph1, steps1 = _pack(waves1, row1, T, NOP1, ilp)
 
     # ---------------- Phase 2: graph of operations and output stores
     p2 = prog.p2
@@ -235,7 +238,7 @@ def build(prog, T=128):
     work = [v for v in range(n2) if nodes[v][0] != "h"]
     pos = {v: i for i, v in enumerate(work)}
     par_list = [[pos[p] for p in parents[v] if nodes[p][0] != "h"] for v in work]
-    waves2 = wave_schedule(par_list, np.array([prio[v] for v in work]), ILP * T)
+    waves2 = wave_schedule(par_list, np.array([prio[v] for v in work]), ilp * T)
     waves2 = [[work[i] for i in w] for w in waves2]
     needs = np.zeros(n2, dtype=bool)
     for v in range(n2):
@@ -278,35 +281,43 @@ def build(prog, T=128):
         return np.array([2 | (oid(val_node[val]) << 16), k,
                          int(i[0]) | (int(i[1]) << 8) | (int(i[2]) << 16) | (int(i[3]) << 24), 0], dtype=np.uint32)
 
-    ph2, steps2 = _pack(waves2, row2, T, NOP2)
+    ph2, steps2 = _pack(waves2, row2, T, NOP2, ilp)
     nslot = max(int(nslot1), int(nslot2))
     if nslot >= 0xFFFF or nh + nslot > MAX_ID:
         raise ValueError("class {} needs {} ids".format(prog.ls, nh + nslot))
-    eff1 = len(g) / max(1, int(steps1.sum()) * T * ILP)
-    eff2 = len(sched) / max(1, int(steps2.sum()) * T * ILP)
-    assert ph1.shape[0] == (int(steps1.sum()) + PREFETCH_STEPS) * T * ILP
-    return CoopProgram(T, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(p2.out_dims), eff1, eff2)
+    eff1 = len(g) / max(1, int(steps1.sum()) * T * ilp)
+    eff2 = len(sched) / max(1, int(steps2.sum()) * T * ilp)
+    assert ph1.shape[0] == (int(steps1.sum()) + PREFETCH_STEPS) * T * ilp
+    return CoopProgram(T, ilp, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(p2.out_dims), eff1, eff2)
 
 
 ROWS_BYTES = 32 * 56 * 8     # coefficient rows of one team (executor constant)
 SMEM_PER_SM = 228 * 1024
 
 
-def choose(prog, sizes=(32, 64, 128)):
-    """Team size with the most useful FP64 lanes per SM: resident warps
-    (shared memory for the team's rows, value slots and, when it fits, H;
-    at most 16 warps) times the lane efficiency of the waves."""
+def choose(prog, shapes=((32, 2), (64, 2), (128, 2), (128, 4))):
+    """(team size, nodes per lane) with the most useful FP64 work per SM:
+    resident warps (shared memory for the team's rows, value slots and, when
+    it fits, H; at most 16 warps), times the lane efficiency of the waves,
+    times a latency-hiding factor for the independent chains per SM
+    sub-partition (warps / 4 x nodes per lane, saturating at 4: measured,
+    two warps of two nodes each per sub-partition already cover the FP64
+    latency, and four nodes per lane then only cost lane efficiency)."""
     best, best_cp = -1.0, None
-    for T in sizes:
-        cp = build(prog, T)
+    for T, ilp in shapes:
+        cp = build(prog, T, ilp)
         vals = cp.nslot * 8 + ROWS_BYTES
         with_h = vals + cp.nh * 8
-        per_team = with_h if with_h * (128 // T) <= 227 * 1024 or with_h <= 227 * 1024 else vals
+        per_team = with_h if with_h <= 227 * 1024 else vals
         if per_team > 227 * 1024:
             continue
-        teams = max(1, min(SMEM_PER_SM // (per_team + 1024), 16 * 32 // T))
-        warps = teams * T // 32
-        score = min(warps, 16) * min(1.0, 0.5 * (cp.eff1 + cp.eff2) + 0.5 * cp.eff1)
+        # registers: 4 nodes per lane need ~230 registers (256 threads per SM)
+        max_threads = 256 if ilp == 4 else 512
+        teams = max(1, min(SMEM_PER_SM // (per_team + 1024), max_threads // T))
+        warps = min(teams * T // 32, max_threads // 32)
+        eff = 0.5 * (cp.eff1 + cp.eff2) * 0.2 + cp.eff1 * 0.8
+        chains = warps / 4.0 * ilp
+        score = warps * eff * min(1.0, chains / 4.0)
         if score > best:
             best, best_cp = score, cp
     return best_cp

@@ -199,7 +199,7 @@ def run_coop(cp, prog, basis, quartets):
     L = prog.L
     kmax = [int(basis.shell_nprim[q[:, k]].max()) for k in range(4)]
 
-    from paper_2605_10312_gb300.gen.coop import ILP
+    ILP = cp.ilp
 
     def waves(rows, steps):
         i = 0

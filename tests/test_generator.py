@@ -125,14 +125,14 @@ def test_all_classes_enumerated():
         assert key in cls
 
 
-@pytest.mark.parametrize("T", [32, 64, 128])
+@pytest.mark.parametrize("T,ilp", [(32, 2), (64, 2), (128, 2), (128, 4)])
 @pytest.mark.parametrize("ls", [(1, 1, 1, 1), (0, 2, 1, 2), (2, 2, 2, 1), (4, 0, 2, 1), (3, 3, 1, 0)])
-def test_coop_program_matches_oracle(ls, T):
+def test_coop_program_matches_oracle(ls, T, ilp):
     """Team-cooperative waves (bounded-width DSA list schedule, slots reused
     only across waves) reproduce the oracle, wave semantics included."""
     prog = program.make(*ls)
-    cp = coop.build(prog, T)
-    assert (int(cp.steps1.sum()) + coop.PREFETCH_STEPS) * T * coop.ILP == cp.ph1.shape[0]
+    cp = coop.build(prog, T, ilp)
+    assert (int(cp.steps1.sum()) + coop.PREFETCH_STEPS) * T * ilp == cp.ph1.shape[0]
     basis, q = synth.class_sweep(ls, 3, kset=(1, 2), seed=13, box_angstrom=3.0, exp_range=(0.1, 30))
     ref, _ = blocks(basis, q)
     got = run_coop(cp, prog, basis, q)
