@@ -197,7 +197,7 @@ def config_dict():
 # ---------------------------------------------------------------------------
 def run_ours(args):
     import torch
-    from paper_2605_10312_gb300 import eri
+    from paper_2605_10312_gb300 import eri, shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -250,13 +250,9 @@ def run_ours(args):
                 key = (ls, i)
                 launch_ms.setdefault(key, []).append((rec, rec["ms"]))
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    quartets = sum(n for _, n in sweep())
-    value = quartets * world * args.steps / (total_ms * 1e-3)
+    total_ms = shard.max_over_ranks(sum(step_ms), dev)
+    quartets = shard.sum_over_ranks(sum(p.nq for _, p in plans), dev)
+    value = quartets * args.steps / (total_ms * 1e-3)
 
     # dominant kernel: the launch with the largest time share
     dom_key = max(launch_ms, key=lambda k: sum(ms for _, ms in launch_ms[k]))
@@ -298,12 +294,8 @@ def run_ours(args):
         barrier()
         if it >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = sum(e2e_ms) if e2e_ms else float("nan")
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = quartets * world * args.steps / (e2e_total * 1e-3)
+    e2e_total = shard.max_over_ranks(sum(e2e_ms) if e2e_ms else float("nan"), dev)
+    e2e_value = quartets * args.steps / (e2e_total * 1e-3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -420,6 +412,71 @@ def run_ablation(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# batched mixed-class workload: Schwarz-screened water cluster
+# ---------------------------------------------------------------------------
+def run_water(args):
+    """All surviving classes of a Schwarz-screened water cluster (dz shell
+    layout) in one plan, replayed as one CUDA graph; optional autotuning."""
+    import torch
+    from paper_2605_10312_gb300 import eri, screen, tune
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    basis = synth.water_cluster(args.waters, seed=3, layout=args.layout)
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        pairs, qb = screen.pair_bounds(basis, stream=stream)
+        torch.cuda.synchronize()
+        t_bounds = time.perf_counter() - t0
+        quartets = synth.screened_quartets(qb, pairs, args.threshold)
+        t_screen = time.perf_counter() - t0
+        npairs = pairs.shape[0]
+        total = npairs * (npairs + 1) // 2
+        tuned = None
+        if args.autotune:
+            tuned = tune.autotune(basis, quartets, sample=1024)
+        plan = eri.Plan(basis, quartets)
+        out = torch.empty(max(1, plan.output_count), dtype=torch.float64, device="cuda")
+        plan.set_timing(True)
+        plan.compute(out, stream)
+        stream.synchronize()
+        per_class = {}
+        for rec in plan.launches()[1:]:
+            key = "".join("spdfg"[x] for x in rec["cls"])
+            e = per_class.setdefault(key, {"quartet_parts": 0, "ms": 0.0, "flops": 0.0, "tier": eri.TIERS_INV[rec["tier"]]})
+            e["quartet_parts"] += rec["quartets"]
+            e["ms"] += rec["ms"]
+            e["flops"] += rec["flops"]
+        plan.set_timing(False)
+        plan.capture(out, stream)
+        for _ in range(args.warmup):
+            plan.replay(stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.replay(stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+    st = plan.stats()
+    line = {"workload": "water cluster: {} waters ({} atoms), {} layout, Schwarz {:g}".format(
+                args.waters, 3 * args.waters, args.layout, args.threshold),
+            "nshell": int(basis.nshell), "pairs": int(npairs), "quartets_total": int(total),
+            "quartets_survived": int(quartets.shape[0]), "survived_frac": quartets.shape[0] / total,
+            "bounds_s": t_bounds, "screen_s": t_screen, "ms_per_step": ms,
+            "value": quartets.shape[0] / (ms * 1e-3), "unit": "quartets/s",
+            "fp64_tflops": st["flops"] / (ms * 1e-3) / 1e12,
+            "fp64_frac_of_peak": st["flops"] / (ms * 1e-3) / 1e12 / fp64_peak_tflops(),
+            "launches_per_step": st["launches"] + 1, "graph": True,
+            "autotuned": None if tuned is None else {"".join(map(str, c)): v["tier"] for c, v in tuned.items()},
+            "per_class": {k: {"parts": v["quartet_parts"], "ms": v["ms"], "tier": v["tier"],
+                              "fp64_frac": v["flops"] / max(1e-9, v["ms"] * 1e-3) / 1e12 / fp64_peak_tflops()}
+                          for k, v in sorted(per_class.items(), key=lambda kv: -kv[1]["ms"])}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -432,6 +489,11 @@ def main():
     ap.add_argument("--classes", default="", help="comma-separated subset, e.g. gggg (profiling runs)")
     ap.add_argument("--scale", type=float, default=1.0, help="multiply the quartet counts (profiling runs)")
     ap.add_argument("--ablation", action="store_true", help="axis / DSA / spherical / tier ablations instead")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "water"])
+    ap.add_argument("--waters", type=int, default=20)
+    ap.add_argument("--layout", default="dz", choices=["dz", "tz"])
+    ap.add_argument("--threshold", type=float, default=1e-10)
+    ap.add_argument("--autotune", action="store_true")
     args = ap.parse_args()
     global ONLY, SCALE
     ONLY = set(c for c in args.classes.split(",") if c) or None
@@ -440,6 +502,8 @@ def main():
         return run_reference(args)
     if args.ablation:
         return run_ablation(args)
+    if args.workload == "water":
+        return run_water(args)
     return run_ours(args)
 
 

@@ -309,7 +309,10 @@ def screened_quartets(pair_bound: np.ndarray, pairs: np.ndarray, threshold: floa
             break
         # partners j <= i in the sorted order with qb[i] qb[j] >= threshold:
         # a prefix, since qb is sorted descending
-        n = int(np.searchsorted(-qb[: i + 1], -threshold / qb[i], side="right")) if qb[i] > 0 else 0
+        if qb[i] > 0:
+            n = int(np.searchsorted(-qb[: i + 1], -threshold / qb[i], side="right"))
+        else:
+            n = i + 1 if threshold <= 0 else 0
         if n == 0:
             continue
         P = pairs[order[i]]

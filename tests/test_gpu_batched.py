@@ -1,0 +1,94 @@
+"""Batched mixed-class path: Schwarz bounds on the device, screening,
+CUDA-graph replay of a whole plan, and the autotuner's tier table."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_10312_gb300 import synth
+from ref import adjudicated, report, within
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eri():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2605_10312_gb300 import eri as m
+    m.library()
+    return m
+
+
+def test_schwarz_bounds_match_oracle(eri):
+    from paper_2605_10312_gb300 import screen
+    basis = synth.water_cluster(2, seed=5)
+    pairs, q = screen.pair_bounds(basis)
+    diag = np.concatenate([pairs, pairs], axis=1)
+    v, off = oracle.eri(basis, diag, nthreads=8)
+    ref = np.empty(pairs.shape[0])
+    ns = [1, 3, 5, 7, 9]
+    for i, (a, b) in enumerate(pairs):
+        n = ns[basis.shell_l[a]] * ns[basis.shell_l[b]]
+        blk = v[off[i]:off[i + 1]].reshape(n, n)
+        ref[i] = np.sqrt(np.max(np.abs(np.diag(blk))))
+    np.testing.assert_allclose(q, ref, rtol=1e-10, atol=1e-14)
+
+
+def test_screened_list_is_complete_and_bounded(eri):
+    from paper_2605_10312_gb300 import screen
+    basis = synth.water_cluster(3, seed=6)
+    pairs, q = screen.pair_bounds(basis)
+    thr = 1e-8
+    got = synth.screened_quartets(q, pairs, thr)
+    want = sum(1 for i in range(q.size) for j in range(i + 1) if q[i] * q[j] >= thr)
+    assert got.shape[0] == want
+    # every dropped quartet is below the threshold: spot check by the oracle
+    rng = np.random.default_rng(0)
+    keep = {tuple(x) for x in got.tolist()}
+    dropped = []
+    while len(dropped) < 40:
+        i, j = sorted(rng.integers(0, q.size, 2))[::-1]
+        quad = (int(pairs[i][0]), int(pairs[i][1]), int(pairs[j][0]), int(pairs[j][1]))
+        if q[i] * q[j] < thr and quad not in keep:
+            dropped.append(quad)
+    v, _ = oracle.eri(basis, np.array(dropped), nthreads=8)
+    assert np.abs(v).max() <= thr * (1 + 1e-9)
+
+
+def test_graph_replay_and_parity(eri):
+    import torch
+    from paper_2605_10312_gb300 import screen
+    basis = synth.water_cluster(3, seed=7)
+    quartets = screen.screened(basis, threshold=1e-10)
+    rng = np.random.default_rng(1)
+    sample = quartets[rng.choice(quartets.shape[0], min(3000, quartets.shape[0]), replace=False)]
+    p = eri.Plan(basis, sample)
+    stream = torch.cuda.Stream()
+    out = torch.empty(p.output_count, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        p.compute(out, stream)
+        stream.synchronize()
+        direct = out.cpu().numpy().copy()
+        out.fill_(np.nan)
+        p.capture(out, stream)
+        p.replay(stream)
+        stream.synchronize()
+    replay = out.cpu().numpy()
+    assert within(replay, direct, atol=1e-15, rtol=1e-13).all()
+    ref, _ = adjudicated(direct, basis, sample)
+    assert within(direct, ref).all(), report(direct, ref)
+    p.close()
+
+
+def test_autotune_keeps_results(eri):
+    import torch
+    from paper_2605_10312_gb300 import tune
+    basis, q = synth.mixed_class_set([(1, 1, 0, 0), (2, 1, 1, 0), (2, 2, 2, 1)], 300, kset=(1, 3), seed=9)
+    base = eri.eri(basis, q)[0].cpu().numpy()
+    result = tune.autotune(basis, q, sample=256)
+    assert result and all(v["tier"] in ("reg", "coop", "shared", "global") for v in result.values())
+    tuned = eri.eri(basis, q)[0].cpu().numpy()
+    assert within(tuned, base, atol=1e-14, rtol=1e-12).all()
+    for c in result:
+        eri.set_class_tier(c, 0)

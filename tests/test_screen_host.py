@@ -1,0 +1,46 @@
+"""Host-side Schwarz screening bookkeeping (no GPU): the surviving quartet
+list equals brute force over all unique pair pairs, each exactly once."""
+import numpy as np
+import pytest
+
+from paper_2605_10312_gb300 import synth
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("thr", [0.0, 1e-12, 1e-6, 1e-2, 10.0])
+def test_screened_quartets_brute_force(seed, thr):
+    rng = np.random.default_rng(seed)
+    nshell = 17
+    pairs = synth.shell_pairs(nshell)
+    q = 10.0 ** rng.uniform(-9, 0.5, pairs.shape[0])
+    q[rng.integers(0, q.size, 5)] = 0.0
+    q[3] = q[7]  # ties
+    got = synth.screened_quartets(q, pairs, thr)
+    want = set()
+    for i in range(q.size):
+        for j in range(i + 1):
+            if q[i] * q[j] >= thr:
+                want.add(frozenset([i, j]) if i != j else frozenset([i]))
+    index = {tuple(p): k for k, p in enumerate(pairs.tolist())}
+    seen = []
+    for row in got.tolist():
+        a, b = index[tuple(row[:2])], index[tuple(row[2:])]
+        assert q[a] * q[b] >= thr
+        seen.append(frozenset([a, b]) if a != b else frozenset([a]))
+    assert len(seen) == len(set(seen))
+    assert set(seen) == want
+
+
+def test_shell_pairs_unique():
+    p = synth.shell_pairs(9)
+    assert p.shape == (45, 2)
+    assert (p[:, 0] >= p[:, 1]).all()
+    assert len({tuple(x) for x in p.tolist()}) == 45
+
+
+def test_water_cluster_shapes():
+    b = synth.water_cluster(20, seed=3, layout="dz")
+    assert b.nshell == 240
+    assert synth.shell_pairs(b.nshell).shape[0] == 28920
+    t = synth.water_cluster(2, seed=3, layout="tz")
+    assert t.shell_l.max() == 3
