@@ -435,7 +435,9 @@ def run_water(args):
         tuned = None
         if args.autotune:
             tuned = tune.autotune(basis, quartets, sample=1024)
+        t1 = time.perf_counter()
         plan = eri.Plan(basis, quartets)
+        t_plan = time.perf_counter() - t1
         out = torch.empty(max(1, plan.output_count), dtype=torch.float64, device="cuda")
         plan.set_timing(True)
         plan.compute(out, stream)
@@ -464,7 +466,8 @@ def run_water(args):
                 args.waters, 3 * args.waters, args.layout, args.threshold),
             "nshell": int(basis.nshell), "pairs": int(npairs), "quartets_total": int(total),
             "quartets_survived": int(quartets.shape[0]), "survived_frac": quartets.shape[0] / total,
-            "bounds_s": t_bounds, "screen_s": t_screen, "ms_per_step": ms,
+            "bounds_s": t_bounds, "screen_s": t_screen, "plan_s": t_plan, "ms_per_step": ms,
+            "output_gb": plan.output_count * 8 / 1e9,
             "value": quartets.shape[0] / (ms * 1e-3), "unit": "quartets/s",
             "fp64_tflops": st["flops"] / (ms * 1e-3) / 1e12,
             "fp64_frac_of_peak": st["flops"] / (ms * 1e-3) / 1e12 / fp64_peak_tflops(),
