@@ -34,8 +34,11 @@ from paper_2605_10312_gb300 import synth  # noqa: E402
 
 METRIC = "contracted ERI shell-quartets/s (per-class FP64 sweep)"
 UNIT = "quartets/s"
-# (class, quartets per step): sized so that one step is about a second
-SWEEP = [((1, 1, 1, 1), 400_000), ((2, 2, 2, 2), 100_000), ((3, 3, 3, 3), 10_000), ((4, 4, 4, 4), 1_000)]
+# (class, quartets per step): 10^6 (pp|pp) and (dd|dd), 10^5 (ff|ff) and (gg|gg)
+SWEEP = [((1, 1, 1, 1), 1_000_000), ((2, 2, 2, 2), 1_000_000), ((3, 3, 3, 3), 100_000), ((4, 4, 4, 4), 100_000)]
+# batch latency: quartets per batch and repeats per class
+LATENCY = {(1, 1, 1, 1): 10_000, (2, 2, 2, 2): 10_000, (3, 3, 3, 3): 10_000, (4, 4, 4, 4): 1_000}
+LATENCY_REPEATS = 100
 KSET = (1, 3, 6)
 SEED = 2000
 ONLY = None     # --classes: subset of the sweep (profiling runs)
@@ -275,10 +278,11 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     e2e_ms, h2d, d2h = [], 0, 0
+    e2e_warmup = 1
     if args.no_e2e:
         args_e2e_steps = 0
     else:
-        args_e2e_steps = args.warmup + args.steps
+        args_e2e_steps = e2e_warmup + args.steps
     host_outs = [torch.empty(p.output_count, dtype=torch.float64).pin_memory() for _, p in plans]
     for it in range(args_e2e_steps):
         barrier()
@@ -292,10 +296,12 @@ def run_ours(args):
             stream.synchronize()
             p.close()
         barrier()
-        if it >= args.warmup:
+        if it >= e2e_warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_total = shard.max_over_ranks(sum(e2e_ms) if e2e_ms else float("nan"), dev)
     e2e_value = quartets * args.steps / (e2e_total * 1e-3)
+
+    latency = None if args.no_latency else batch_latency(plans, parts, flush, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -321,6 +327,7 @@ def run_ours(args):
                                    "2070 MHz".format(FP64_LANES_PER_SM_CLK)},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "latency": latency,
         "gpu_launches": nlaunch * args.steps,
         "clocks": clk,
     }
@@ -328,6 +335,34 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def batch_latency(plans, parts, flush, stream):
+    """p50/p99 device latency of one batch per class (the first LATENCY[class]
+    quartets of the sweep), LATENCY_REPEATS repeats after 3 warm-ups, L2
+    flushed before each, CUDA events on the launching stream."""
+    import torch
+    from paper_2605_10312_gb300 import eri
+    out = {}
+    for (ls, basis, q) in parts:
+        n = min(LATENCY.get(ls, 10_000), q.shape[0])
+        p = eri.Plan(basis, q[:n])
+        o = torch.empty(p.output_count, dtype=torch.float64, device=flush.device)
+        ms = []
+        for it in range(3 + LATENCY_REPEATS):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.compute(o, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= 3:
+                ms.append(e0.elapsed_time(e1))
+        p.close()
+        out["".join("spdfg"[x] for x in ls)] = {
+            "batch_quartets": n, "repeats": LATENCY_REPEATS, "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)), "mean_ms": float(np.mean(ms))}
+    return out
 
 
 def _traffic_for(rec):
@@ -480,15 +515,107 @@ def run_water(args):
     return 0
 
 
+def _class_labels(basis, quartets):
+    """Canonical class label of each quartet (pairs ordered high l first,
+    bra pair not below the ket pair) and the list of labels."""
+    l = basis.shell_l[np.asarray(quartets)]
+    bra = np.sort(l[:, :2], axis=1)[:, ::-1]
+    ket = np.sort(l[:, 2:], axis=1)[:, ::-1]
+    swap = bra[:, 0] * 5 + bra[:, 1] < ket[:, 0] * 5 + ket[:, 1]
+    hi = np.where(swap[:, None], ket, bra)
+    lo = np.where(swap[:, None], bra, ket)
+    code = ((hi[:, 0] * 5 + hi[:, 1]) * 5 + lo[:, 0]) * 5 + lo[:, 1]
+    uniq, inv = np.unique(code, return_inverse=True)
+    labels = ["".join("spdfg"[(c // 5 ** k) % 5] for k in (3, 2, 1, 0)) for c in uniq]
+    return inv, labels
+
+
+def run_water_mixed(args):
+    """Mixed precision on a screened water cluster: quartets with Schwarz
+    bound below --fp32-below run FP32 recurrences.  Times the mixed plan and
+    the all-FP64 plan on the same quartets (CUDA graphs) and reports the
+    per-class max and RMS difference between them."""
+    import torch
+    from paper_2605_10312_gb300 import eri, screen
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    basis = synth.water_cluster(args.waters, seed=3, layout=args.layout)
+    with torch.cuda.stream(stream):
+        pairs, qp = screen.pair_bounds(basis, stream=stream)
+        total = synth.count_screened(qp, args.threshold)
+        if args.sample and args.sample < total:
+            quartets = synth.sample_screened_quartets(qp, pairs, args.threshold, args.sample, seed=7)
+        else:
+            quartets = synth.screened_quartets(qp, pairs, args.threshold)
+        qb = screen.quartet_bounds(qp, quartets)
+        plans = {"fp64": eri.Plan(basis, quartets),
+                 "mixed": eri.Plan(basis, quartets, qbound=qb, fp32_below=args.fp32_below)}
+        outs, ms, launch_ms = {}, {}, {}
+        for name, p in plans.items():
+            o = torch.empty(max(1, p.output_count), dtype=torch.float64, device="cuda")
+            # one timed pass for the per-class, per-precision split
+            p.set_timing(True)
+            p.compute(o, stream)
+            stream.synchronize()
+            for rec in p.launches()[1:]:
+                key = "{}/{}".format("".join("spdfg"[x] for x in rec["cls"]), rec["precision"])
+                launch_ms[(name, key)] = launch_ms.get((name, key), 0.0) + rec["ms"]
+            p.set_timing(False)
+            p.capture(o, stream)
+            for _ in range(args.warmup):
+                p.replay(stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                p.replay(stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms[name] = e0.elapsed_time(e1) / args.steps
+            outs[name] = o
+        off = plans["fp64"].offsets()
+        cls, labels = _class_labels(basis, quartets)
+        fp32q = qb < args.fp32_below
+        sizes = torch.from_numpy(np.diff(off)).to("cuda")
+        cid = torch.repeat_interleave(torch.from_numpy(cls.astype(np.int64)).to("cuda"), sizes)
+        d = (outs["mixed"][: off[-1]] - outs["fp64"][: off[-1]]).abs()
+        nc = len(labels)
+        mx = torch.zeros(nc, dtype=torch.float64, device="cuda").scatter_reduce_(0, cid, d, reduce="amax")
+        ss = torch.zeros(nc, dtype=torch.float64, device="cuda").index_add_(0, cid, d * d)
+        cnt = torch.zeros(nc, dtype=torch.float64, device="cuda").index_add_(0, cid, torch.ones_like(d))
+        mx, rms = mx.cpu().numpy(), torch.sqrt(ss / cnt.clamp(min=1)).cpu().numpy()
+        stream.synchronize()
+    st = plans["mixed"].stats()
+    per_class = {}
+    for k, lab in enumerate(labels):
+        sel = cls == k
+        per_class[lab] = {"quartets": int(sel.sum()), "fp32_quartets": int((sel & fp32q).sum()),
+                          "max_abs_diff_vs_fp64": float(mx[k]), "rms_diff_vs_fp64": float(rms[k])}
+    line = {"workload": "water cluster: {} waters ({} atoms), {} layout, Schwarz {:g}, FP32 below {:g}".format(
+                args.waters, 3 * args.waters, args.layout, args.threshold, args.fp32_below),
+            "nshell": int(basis.nshell), "pairs": int(pairs.shape[0]), "quartets_screened": int(total),
+            "quartets": int(quartets.shape[0]),
+            "sample": None if quartets.shape[0] == total else "uniform seeded sample of the screened list",
+            "fp32_quartets": int(fp32q.sum()), "fp32_parts": st["fp32_parts"],
+            "ms_fp64": ms["fp64"], "ms_mixed": ms["mixed"], "speedup": ms["fp64"] / ms["mixed"],
+            "value_mixed": quartets.shape[0] / (ms["mixed"] * 1e-3),
+            "value_fp64": quartets.shape[0] / (ms["fp64"] * 1e-3), "unit": "quartets/s",
+            "max_abs_diff_vs_fp64": float(mx.max()), "per_class": per_class,
+            "launch_ms": {n: {k: v for (nn, k), v in sorted(launch_ms.items(), key=lambda kv: -kv[1]) if nn == n}
+                          for n in plans}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--classes", default="", help="comma-separated subset, e.g. gggg (profiling runs)")
     ap.add_argument("--scale", type=float, default=1.0, help="multiply the quartet counts (profiling runs)")
     ap.add_argument("--ablation", action="store_true", help="axis / DSA / spherical / tier ablations instead")
@@ -497,6 +624,9 @@ def main():
     ap.add_argument("--layout", default="dz", choices=["dz", "tz"])
     ap.add_argument("--threshold", type=float, default=1e-10)
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--fp32-below", type=float, default=None,
+                    help="water workload in mixed precision: FP32 recurrences below this Schwarz bound")
+    ap.add_argument("--sample", type=int, default=0, help="water workload: sample this many screened quartets")
     args = ap.parse_args()
     global ONLY, SCALE
     ONLY = set(c for c in args.classes.split(",") if c) or None
@@ -506,7 +636,7 @@ def main():
     if args.ablation:
         return run_ablation(args)
     if args.workload == "water":
-        return run_water(args)
+        return run_water_mixed(args) if args.fp32_below is not None else run_water(args)
     return run_ours(args)
 
 

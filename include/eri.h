@@ -76,7 +76,10 @@ typedef struct {
   int32_t orientation;  /* 0 per primitive pair: each recurs on its tighter primitive's centre (a pair may split
                            into two oriented parts whose blocks are summed), 1 whole pair on the higher l,
                            2 whole pair on the shell holding the largest exponent */
-  int32_t reserved[3];
+  int32_t streams;      /* launches of one part round that may run concurrently, on up to this many streams
+                           (the caller's plus streams the plan owns, joined back before eri_compute returns):
+                           0 auto (4 for plans holding several classes, else 1), 1 serial, at most 8 */
+  int32_t reserved[2];
 } eri_opts;
 
 typedef struct eri_plan_s eri_plan_t;
@@ -88,6 +91,23 @@ typedef struct eri_plan_s eri_plan_t;
  * the plan owns its device memory.  nq may be 0.  Synchronous. */
 int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
              int64_t nq, const eri_opts* opts, eri_plan_t** plan_out);
+
+/* Mixed-precision plan (the precision axis of the method's extensions; the
+ * paper evaluates everything in FP64 and has no counterpart).  Like eri_plan,
+ * plus qbound (host, nq doubles >= 0): an upper bound on |(ab|cd)| for each
+ * quartet, normally the Schwarz product Q_ab Q_cd.  Quartets with
+ * qbound[q] < fp32_below run the recurrences (VRR, contraction sums, HRR and
+ * the spherical transform) in FP32; the pair and primitive-quartet set-up,
+ * the Boys function, every other quartet and the output (stores and the
+ * accumulation of split parts) stay FP64.  The absolute error of an FP32
+ * quartet is then about qbound[q] times a small multiple of 2^-24 per
+ * recurrence level.  FP32 is used only with the default generator options
+ * and tier 0, 1 or 4; otherwise the plan is all FP64.  Errors: ERI_EINVAL
+ * for a NULL bound array (nq > 0), a negative or NaN bound, or a negative or
+ * non-finite threshold; otherwise as eri_plan. */
+int eri_plan_mixed(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
+                   int64_t nq, const double* qbound, double fp32_below, const eri_opts* opts,
+                   eri_plan_t** plan_out);
 
 /* Total number of doubles eri_compute writes (sum of block sizes). */
 int64_t eri_output_count(const eri_plan_t* plan);
@@ -110,8 +130,9 @@ int eri_compute_host(eri_plan_t* plan, double* host_out, void* stream);
 /* Per-plan statistics, host memory: stats[0] = number of class launches,
  * stats[1] = algorithmic FP64 flops of one eri_compute (FMA = 2),
  * stats[2] = scratch bytes, stats[3] = quartets, stats[4] = primitive
- * quartets, stats[5] = bytes eri_plan copied host-to-device.
- * n = entries wanted (<= 6). */
+ * quartets, stats[5] = bytes eri_plan copied host-to-device, stats[6] =
+ * algorithmic FP32 flops (eri_plan_mixed), stats[7] = quartet parts with
+ * FP32 recurrences.  n = entries wanted (<= 8). */
 int eri_plan_stats(const eri_plan_t* plan, double* stats, int n);
 
 /* Launch timing: when enabled, eri_compute records a CUDA event pair on its
@@ -127,6 +148,11 @@ int eri_plan_launch_count(const eri_plan_t* plan);
  * flops, *ms = its duration from the event pair (-1 when timing is off);
  * the stream must have completed.  Any output pointer may be NULL. */
 int eri_plan_launch_info(const eri_plan_t* plan, int i, int32_t* info, double* flops, float* ms);
+
+/* Precision of launch i's recurrences: 64, or 32 for an FP32 bucket of an
+ * eri_plan_mixed plan (its flops from eri_plan_launch_info are FP32 flops);
+ * ERI_EINVAL for a bad index. */
+int eri_plan_launch_precision(const eri_plan_t* plan, int i);
 
 /* Evaluate like eri_compute without allocating: for callers that may not
  * allocate device memory while they evaluate (stream capture without

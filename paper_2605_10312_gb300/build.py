@@ -85,15 +85,24 @@ def _class_job(args):
     if want_reg and rec["size"] <= REG_TIER_MAX:
         rec["cuda"] = emit_cuda.emit_class(prog, "reg")
         rec["kname"] = emit_cuda.kernel_name(ls, "reg")
+        # the reduced-precision form (FP32 recurrences) of the same schedule
+        rec["cuda_f32"] = emit_cuda.emit_class(prog, "reg", real="float")
+        rec["kname_f32"] = emit_cuda.kernel_name(ls, "reg", real="float")
     if (want_reg and rec["size"] > REG_TIER_MAX) or force_coop:
         # team-cooperative form: one warp per primitive quartet while four
         # teams' live sets fit in shared memory, else four warps
         from paper_2605_10312_gb300.gen import coop
-        cp = coop.choose(prog)
-        rec["coop"] = dict(T=cp.T, ilp=cp.ilp, nh=cp.nh, nslot=cp.nslot, L=cp.L, dims=cp.out_dims, steps1=cp.steps1.tobytes(),
-                           steps2=cp.steps2.tobytes(), nw1=int(cp.steps1.shape[0]), nw2=int(cp.steps2.shape[0]),
-                           ph1=cp.ph1.tobytes(), ph2=cp.ph2.tobytes(), n1=int(cp.ph1.shape[0]),
-                           n2=int(cp.ph2.shape[0]), eff1=cp.eff1, eff2=cp.eff2)
+
+        def pack(cp):
+            return dict(T=cp.T, ilp=cp.ilp, nh=cp.nh, nslot=cp.nslot, L=cp.L, dims=cp.out_dims,
+                        steps1=cp.steps1.tobytes(), steps2=cp.steps2.tobytes(), nw1=int(cp.steps1.shape[0]),
+                        nw2=int(cp.steps2.shape[0]), ph1=cp.ph1.tobytes(), ph2=cp.ph2.tobytes(),
+                        n1=int(cp.ph1.shape[0]), n2=int(cp.ph2.shape[0]), eff1=cp.eff1, eff2=cp.eff2)
+        deep, shallow = coop.choose_both(prog)
+        rec["coop"] = pack(deep)
+        # a second shape for shallow contractions, when it differs
+        if shallow is not None and (shallow.T, shallow.ilp) != (deep.T, deep.ilp):
+            rec["coop_shallow"] = pack(shallow)
     return rec
 
 
@@ -125,31 +134,38 @@ def write_blob(path, recs, boys, c2s):
             f.write(struct.pack("<2d", r["flops_prim"], r["flops_p2"]))
             f.write(r["ph1"])
             f.write(r["ph2"])
-        coops = [r for r in recs if "coop" in r]
-        f.write(struct.pack("<I", len(coops)))
-        for r in coops:
-            o, c = r["opts"], r["coop"]
-            f.write(struct.pack("<8b", *r["ls"], AXIS[o[0]], SCHED[o[1]], SPH[o[2]], c["ilp"]))
-            f.write(struct.pack("<12i", c["T"], c["nh"], c["nslot"], c["L"], c["nw1"], c["nw2"], c["n1"], c["n2"],
-                                *c["dims"]))
-            f.write(struct.pack("<2d", r["flops_prim"], r["flops_p2"]))
-            f.write(c["steps1"])
-            f.write(c["steps2"])
-            f.write(c["ph1"])
-            f.write(c["ph2"])
+        # team-cooperative programs: the deep-contraction shape of every class,
+        # then the shallow-contraction shapes that differ from it
+        for key in ("coop", "coop_shallow"):
+            _write_coops(f, [r for r in recs if key in r], key)
     os.replace(path + ".tmp", path)
+
+
+def _write_coops(f, coops, key):
+    f.write(struct.pack("<I", len(coops)))
+    for r in coops:
+        o, c = r["opts"], r[key]
+        f.write(struct.pack("<8b", *r["ls"], AXIS[o[0]], SCHED[o[1]], SPH[o[2]], c["ilp"]))
+        f.write(struct.pack("<12i", c["T"], c["nh"], c["nslot"], c["L"], c["nw1"], c["nw2"], c["n1"], c["n2"],
+                            *c["dims"]))
+        f.write(struct.pack("<2d", r["flops_prim"], r["flops_p2"]))
+        f.write(c["steps1"])
+        f.write(c["steps2"])
+        f.write(c["ph1"])
+        f.write(c["ph2"])
 
 
 def _registry(recs):
     lines = ['#include "eri_common.cuh"', "struct EriRegEntry { int8_t ls[4]; const void* fn; };"]
-    regs = [r for r in recs if "cuda" in r]
-    for r in regs:
-        lines.append('extern "C" __global__ void {}(const EriLaunchArgs a);'.format(r["kname"]))
-    lines.append('extern "C" const EriRegEntry eri_reg_table[] = {')
-    for r in regs:
-        lines.append("  {{{{{}, {}, {}, {}}}, (const void*){}}},".format(*r["ls"], r["kname"]))
-    lines.append("  {{0, 0, 0, 0}, nullptr}};")
-    lines.append('extern "C" const int eri_reg_count = {};'.format(len(regs)))
+    for table, key in (("eri_reg", "kname"), ("eri_reg_f32", "kname_f32")):
+        regs = [r for r in recs if key in r]
+        for r in regs:
+            lines.append('extern "C" __global__ void {}(const EriLaunchArgs a);'.format(r[key]))
+        lines.append('extern "C" const EriRegEntry {}_table[] = {{'.format(table))
+        for r in regs:
+            lines.append("  {{{{{}, {}, {}, {}}}, (const void*){}}},".format(*r["ls"], r[key]))
+        lines.append("  {{0, 0, 0, 0}, nullptr}};")
+        lines.append('extern "C" const int {}_count = {};'.format(table, len(regs)))
     return "\n".join(lines) + "\n"
 
 
@@ -204,11 +220,13 @@ def build(force=False, jobs=None, log=print):
         for r in recs:
             if "cuda" in r:
                 _write_if_changed(os.path.join(GEN_DIR, r["kname"] + ".cu"), r["cuda"])
+            if "cuda_f32" in r:
+                _write_if_changed(os.path.join(GEN_DIR, r["kname_f32"] + ".cu"), r["cuda_f32"])
         _write_if_changed(os.path.join(GEN_DIR, "eri_registry.cu"), _registry(recs))
         # class table for the docs and the benchmark: per-class counts
         with open(os.path.join(BUILD, "classes.tsv"), "w") as f:
             f.write("la\tlb\tlc\tld\ttier\tvrr_nodes\tpeak_live\tnslot\tnh\tnout\tper_prim_flops\tp2_flops"
-                    "\tcoop_T\tcoop_ilp\tcoop_nslot\tcoop_eff1\tcoop_eff2\n")
+                    "\tcoop_T\tcoop_ilp\tcoop_nslot\tcoop_eff1\tcoop_eff2\tshallow_T\tshallow_ilp\n")
             for r in sorted(recs, key=lambda r: r["ls"]):
                 c = r["counts"]
                 cp = r.get("coop")
@@ -218,18 +236,21 @@ def build(force=False, jobs=None, log=print):
                                                    cp["T"] if cp else "", cp["ilp"] if cp else "",
                                                    cp["nslot"] if cp else "",
                                                    round(cp["eff1"], 3) if cp else "",
-                                                   round(cp["eff2"], 3) if cp else "")) + "\n")
+                                                   round(cp["eff2"], 3) if cp else "",
+                                                   r["coop_shallow"]["T"] if "coop_shallow" in r else "",
+                                                   r["coop_shallow"]["ilp"] if "coop_shallow" in r else "")) + "\n")
         open(stamp, "w").write(gen_key)
     units = [os.path.join(CSRC, "eri_runtime.cu"), os.path.join(CSRC, "eri_exec.cu"),
              os.path.join(CSRC, "eri_coop.cu"), os.path.join(GEN_DIR, "eri_registry.cu")]
     units += sorted(os.path.join(GEN_DIR, f) for f in os.listdir(GEN_DIR)
-                    if f.endswith("_reg.cu"))
+                    if f.endswith("_reg.cu") or f.endswith("_reg_f32.cu"))
+    units.sort(key=lambda u: -os.path.getsize(u))  # largest first: the pool ends evenly
     objs = [os.path.join(BUILD, os.path.basename(u)[:-3] + ".o") for u in units]
     # drop objects of classes no longer generated
     keep = set(objs)
     for f in os.listdir(BUILD):
         p = os.path.join(BUILD, f)
-        if f.endswith("_reg.o") and p not in keep:
+        if (f.endswith("_reg.o") or f.endswith("_reg_f32.o")) and p not in keep:
             os.remove(p)
     t1 = time.time()
     with ThreadPoolExecutor(jobs) as ex:

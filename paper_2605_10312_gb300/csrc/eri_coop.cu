@@ -30,6 +30,7 @@ struct EriCoopArgs {
   int32_t smem_slots;                 // value slots held in shared memory
   int32_t h_in_smem;
   int32_t nteams;                     // teams in the grid
+  int32_t batch;                      // coefficient rows per team (1..ERI_COOP_BATCH)
 };
 
 __device__ __forceinline__ double eri_coop_pick8(int k, const double (&t)[8]) {
@@ -66,8 +67,8 @@ template <int T>
 __device__ __forceinline__ void eri_team_sync() {
   if (T == 32) {
     __syncwarp();
-  } else if (T == 128) {
-    __syncthreads();
+  } else if (T >= 128) {
+    __syncthreads();  // one team per block
   } else {
     // two teams of 64 lanes per 128-thread block: named barriers 1 and 2
     asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / T)), "r"(T) : "memory");
@@ -82,39 +83,47 @@ __device__ __forceinline__ void eri_team_sync() {
 //   45 + k - 1                 k / (2 (zeta + eta))
 //   53 + side                  -rho/zeta, -rho/eta
 #define ERI_COOP_NC 56
-#define ERI_COOP_BATCH 32
+#define ERI_COOP_BATCH 32  // largest row batch (one row per lane of a warp)
 
+// The row is formed in FP64 (Boys function included) and rounded once to the
+// value type R of the recurrences.
+template <typename R>
 __device__ __forceinline__ void eri_coop_row(const EriPairPrim& bp, const EriPairPrim& kp, int L,
-                                             const double* __restrict__ tab, double* row) {
+                                             const double* __restrict__ tab, R* row) {
   EriPrimQuartet pq;
   eri_prim_quartet(bp, kp, pq);
   double F[ERI_BOYS_LMAX + 1];
   eri_coop_boys(L, pq.T, F, tab);
-  for (int m = 0; m <= L; ++m) row[m] = pq.pref * F[m];
+  for (int m = 0; m <= L; ++m) row[m] = (R)(pq.pref * F[m]);
   for (int i = 0; i < 3; ++i) {
-    row[17 + i] = bp.PA[i];
-    row[20 + i] = pq.WP[i];
-    row[23 + i] = kp.PA[i];
-    row[26 + i] = pq.WQ[i];
+    row[17 + i] = (R)bp.PA[i];
+    row[20 + i] = (R)pq.WP[i];
+    row[23 + i] = (R)kp.PA[i];
+    row[26 + i] = (R)pq.WQ[i];
   }
   for (int k = 0; k < 8; ++k) {
-    row[29 + k] = (double)(k + 1) * bp.inv2z;
-    row[37 + k] = (double)(k + 1) * kp.inv2z;
-    row[45 + k] = (double)(k + 1) * (0.5 * pq.s);
+    row[29 + k] = (R)((double)(k + 1) * bp.inv2z);
+    row[37 + k] = (R)((double)(k + 1) * kp.inv2z);
+    row[45 + k] = (R)((double)(k + 1) * (0.5 * pq.s));
   }
-  row[53] = -pq.te;
-  row[54] = -pq.tz;
+  row[53] = (R)(-pq.te);
+  row[54] = (R)(-pq.tz);
 }
+
+__device__ __forceinline__ double eri_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float eri_fma(float a, float b, float c) { return fmaf(a, b, c); }
 
 // Phase-1 nodes (descriptor: see the generator's coop module).  Operands
 // are value slots in the team's shared memory; a lane's two nodes of a step
 // belong to one wave and never alias, so both nodes' operands are loaded
 // before either result is stored and the two FMA chains interleave.
+template <typename R>
 struct EriCoopOps {
-  double a, b, c, d, e;
+  R a, b, c, d, e;
 };
 
-__device__ __forceinline__ void eri_coop_load1(const uint4& d, const double* V, EriCoopOps& v) {
+template <typename R>
+__device__ __forceinline__ void eri_coop_load1(const uint4& d, const R* V, EriCoopOps<R>& v) {
   const unsigned meta = d.w >> 16;
   if (meta & 0xC000u) return;  // no-op or base node
   v.a = V[d.y & 0xFFFF];
@@ -126,20 +135,21 @@ __device__ __forceinline__ void eri_coop_load1(const uint4& d, const double* V, 
   if (meta & (15u << 9)) v.e = V[d.w & 0xFFFF];
 }
 
-__device__ __forceinline__ double eri_coop_eval1(const uint4& d, const double* row, const EriCoopOps& v) {
+template <typename R>
+__device__ __forceinline__ R eri_coop_eval1(const uint4& d, const R* row, const EriCoopOps<R>& v) {
   const unsigned meta = d.w >> 16;
   const unsigned k = (meta >> 4) & 31;
   if (meta & 0x4000u) return row[k];  // base node: pref * F_m
   const unsigned cgo = meta & 15, k3 = (meta >> 9) & 15, side = (meta >> 13) & 1;
-  double x = row[17 + cgo] * v.a;
-  x = fma(row[20 + cgo], v.b, x);
-  if (k) x = fma(row[28 + 8 * side + k], fma(row[53 + side], v.d, v.c), x);
-  if (k3) x = fma(row[44 + k3], v.e, x);
+  R x = row[17 + cgo] * v.a;
+  x = eri_fma(row[20 + cgo], v.b, x);
+  if (k) x = eri_fma(row[28 + 8 * side + k], eri_fma(row[53 + side], v.d, v.c), x);
+  if (k3) x = eri_fma(row[44 + k3], v.e, x);
   return x;
 }
 
-template <bool HSM>
-__device__ __forceinline__ void eri_coop_store1(const uint4& d, double x, double* V, double* H) {
+template <bool HSM, typename R>
+__device__ __forceinline__ void eri_coop_store1(const uint4& d, R x, R* V, R* H) {
   if ((d.w >> 16) & 0x8000u) return;
   const unsigned dst = d.x & 0xFFFF, h = d.x >> 16;
   if (dst != 0xFFFF) V[dst] = x;
@@ -155,8 +165,8 @@ __device__ __forceinline__ void eri_coop_store1(const uint4& d, double x, double
 
 // Phase-2 operations and stores, two per lane per step (never aliasing
 // within a wave): operands first, then results.
-template <typename Ptr>
-__device__ __forceinline__ void eri_coop_load2(const uint4& d, const Ptr& ptr, double (&v)[4]) {
+template <typename R, typename Ptr>
+__device__ __forceinline__ void eri_coop_load2(const uint4& d, const Ptr& ptr, R (&v)[4]) {
   const int kind = d.x & 3;
   if (kind == 0) {
     v[0] = *ptr(d.y & 0xFFFF);
@@ -172,59 +182,65 @@ __device__ __forceinline__ void eri_coop_load2(const uint4& d, const Ptr& ptr, d
   }
 }
 
-template <typename Ptr>
-__device__ __forceinline__ void eri_coop_exec2(const uint4& d, const double (&v)[4], const EriPairRec& bra,
+template <typename R, typename Ptr>
+__device__ __forceinline__ void eri_coop_exec2(const uint4& d, const R (&v)[4], const EriPairRec& bra,
                                                const EriPairRec& ket, const EriQuartetRec& qr, double* o, bool acc,
                                                bool red, const double* __restrict__ c2s, const Ptr& ptr) {
   const int kind = d.x & 3;
   const unsigned dst = d.x >> 16;
   if (kind == 0) {
     const int ax = d.z;
-    const double X = ax < 3 ? eri_coop_pick3(ax, bra.AB[0], bra.AB[1], bra.AB[2])
-                            : eri_coop_pick3(ax - 3, ket.AB[0], ket.AB[1], ket.AB[2]);
-    *ptr(dst) = fma(X, v[1], v[0]);
+    const R X = (R)(ax < 3 ? eri_coop_pick3(ax, bra.AB[0], bra.AB[1], bra.AB[2])
+                           : eri_coop_pick3(ax - 3, ket.AB[0], ket.AB[1], ket.AB[2]));
+    *ptr(dst) = eri_fma(X, v[1], v[0]);
   } else if (kind == 1) {
     const int nt = (d.x >> 2) & 7;
-    double x = __ldg(c2s + (d.w & 255)) * v[0];
-    if (nt > 1) x = fma(__ldg(c2s + ((d.w >> 8) & 255)), v[1], x);
-    if (nt > 2) x = fma(__ldg(c2s + ((d.w >> 16) & 255)), v[2], x);
-    if (nt > 3) x = fma(__ldg(c2s + (d.w >> 24)), v[3], x);
+    R x = (R)__ldg(c2s + (d.w & 255)) * v[0];
+    if (nt > 1) x = eri_fma((R)__ldg(c2s + ((d.w >> 8) & 255)), v[1], x);
+    if (nt > 2) x = eri_fma((R)__ldg(c2s + ((d.w >> 16) & 255)), v[2], x);
+    if (nt > 3) x = eri_fma((R)__ldg(c2s + (d.w >> 24)), v[3], x);
     *ptr(dst) = x;
   } else if (kind == 2) {
+    // the block store (and any accumulation into the output) is FP64
     const int64_t off = (int64_t)(d.z & 255) * qr.st[0] + (int64_t)((d.z >> 8) & 255) * qr.st[1] +
                         (int64_t)((d.z >> 16) & 255) * qr.st[2] + (int64_t)(d.z >> 24) * qr.st[3];
-    eri_st(o + off, v[0], acc, red);
+    eri_st(o + off, (double)v[0], acc, red);
   }
 }
 
 // HSM: the accumulators H share the team's shared-memory region with the
 // value slots ([H | slots], operand id = offset); otherwise H is a
 // team-private global region and slots follow at id - nh.
-template <int T, bool HSM, int ILP>
-__global__ void __launch_bounds__(128, ILP == 4 ? 2 : 4) eri_coop_kernel(const EriLaunchArgs a, const EriCoopArgs p) {
+// R: value type of the recurrences, the contraction sums H, HRR and the
+// transform -- double, or float for the reduced-precision form (coefficient
+// rows and the Boys function are still formed in FP64; stores are FP64).
+// Blocks are 128 threads (teams of up to 128 lanes) or one 256-lane team.
+template <typename R, int T, bool HSM, int ILP>
+__global__ void __launch_bounds__(T > 128 ? T : 128, T > 128 ? (ILP == 4 ? 1 : 2) : (ILP == 4 ? 2 : 4))
+    eri_coop_kernel(const EriLaunchArgs a, const EriCoopArgs p) {
   extern __shared__ double eri_coop_smem[];
   const int tb = threadIdx.x / T;           // team within the block
   const int l = threadIdx.x - tb * T;       // lane within the team
   const int team = blockIdx.x * (blockDim.x / T) + tb;
-  const int per_team = ERI_COOP_BATCH * ERI_COOP_NC + (HSM ? p.nh : 0) + p.nslot;
-  double* const rows = eri_coop_smem + (size_t)tb * per_team;
-  double* const Hsm = rows + ERI_COOP_BATCH * ERI_COOP_NC;           // H when HSM
-  double* const V = Hsm + (HSM ? p.nh : 0);                         // value slots (shared)
-  double* const Hs = HSM ? Hsm : p.gH + (size_t)team * p.nh;
+  const int per_team = p.batch * ERI_COOP_NC + (HSM ? p.nh : 0) + p.nslot;
+  R* const rows = reinterpret_cast<R*>(eri_coop_smem) + (size_t)tb * per_team;
+  R* const Hsm = rows + p.batch * ERI_COOP_NC;                        // H when HSM
+  R* const V = Hsm + (HSM ? p.nh : 0);                              // value slots (shared)
+  R* const Hs = HSM ? Hsm : reinterpret_cast<R*>(p.gH) + (size_t)team * p.nh;
   const unsigned nh = (unsigned)p.nh;
   // Phase-2 operand id -> address: H below nh, value slots above
-  auto ptr = [&](unsigned id) -> double* { return id < nh ? Hs + id : V + (id - nh); };
+  auto ptr = [&](unsigned id) -> R* { return id < nh ? Hs + id : V + (id - nh); };
   for (int q = team; q < a.nq; q += p.nteams) {
     const EriQuartetRec qr = a.quartets[q];
     const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];
     const bool acc = ERI_ACCUMULATE(qr.bra);
     const bool red = ERI_REDUCE(qr.bra);
     const EriPairRec ket = a.pairs[qr.ket];
-    for (int h = l; h < p.nh; h += T) Hs[h] = 0.0;
+    for (int h = l; h < p.nh; h += T) Hs[h] = (R)0;
     const int kk = ket.nprim;
     const int k4 = bra.nprim * kk;
-    for (int b0 = 0; b0 < k4; b0 += ERI_COOP_BATCH) {
-      const int nb = min(ERI_COOP_BATCH, k4 - b0);
+    for (int b0 = 0; b0 < k4; b0 += p.batch) {
+      const int nb = min(p.batch, k4 - b0);
       if (l < nb) {
         const int pidx = b0 + l;
         const int i = pidx / kk, j = pidx - (pidx / kk) * kk;
@@ -233,7 +249,7 @@ __global__ void __launch_bounds__(128, ILP == 4 ? 2 : 4) eri_coop_kernel(const E
       }
       eri_team_sync<T>();
       for (int pi = 0; pi < nb; ++pi) {
-        const double* const row = rows + pi * ERI_COOP_NC;
+        const R* const row = rows + pi * ERI_COOP_NC;
         // a step gives each lane ILP descriptors (independent nodes of the
         // same wave); they are loaded two steps ahead -- the stream ends in
         // two no-op steps -- so the L2 latency overlaps the previous step
@@ -251,10 +267,10 @@ __global__ void __launch_bounds__(128, ILP == 4 ? 2 : 4) eri_coop_kernel(const E
 #pragma unroll
             for (int u = 0; u < ILP; ++u) dnn[u] = __ldg(dp + 2 * ILP * T + u);
             dp += ILP * T;
-            EriCoopOps v[ILP];
+            EriCoopOps<R> v[ILP];
 #pragma unroll
             for (int u = 0; u < ILP; ++u) eri_coop_load1(d[u], V, v[u]);
-            double x[ILP];
+            R x[ILP];
 #pragma unroll
             for (int u = 0; u < ILP; ++u) x[u] = eri_coop_eval1(d[u], row, v[u]);
 #pragma unroll
@@ -290,7 +306,7 @@ __global__ void __launch_bounds__(128, ILP == 4 ? 2 : 4) eri_coop_kernel(const E
 #pragma unroll
         for (int u = 0; u < ILP; ++u) dnn[u] = __ldg(dp + 2 * ILP * T + u);
         dp += ILP * T;
-        double v[ILP][4];
+        R v[ILP][4];
 #pragma unroll
         for (int u = 0; u < ILP; ++u) eri_coop_load2(d[u], ptr, v[u]);
 #pragma unroll
@@ -306,45 +322,34 @@ __global__ void __launch_bounds__(128, ILP == 4 ? 2 : 4) eri_coop_kernel(const E
   }
 }
 
-extern "C" cudaError_t eri_coop_launch(int T, int ilp, const EriLaunchArgs* a, const EriCoopArgs* p, int grid,
-                                       int block, size_t smem, cudaStream_t stream) {
-  const bool hsm = p->h_in_smem != 0;
-#define ERI_COOP_GO(TT, II)                                                    \
-  do {                                                                         \
-    if (hsm)                                                                   \
-      eri_coop_kernel<TT, true, II><<<grid, block, smem, stream>>>(*a, *p);    \
-    else                                                                       \
-      eri_coop_kernel<TT, false, II><<<grid, block, smem, stream>>>(*a, *p);   \
-  } while (0)
-  if (ilp == 2) {
-    if (T == 32) ERI_COOP_GO(32, 2);
-    else if (T == 64) ERI_COOP_GO(64, 2);
-    else if (T == 128) ERI_COOP_GO(128, 2);
-    else return cudaErrorInvalidValue;
-  } else if (ilp == 4) {
-    if (T == 32) ERI_COOP_GO(32, 4);
-    else if (T == 64) ERI_COOP_GO(64, 4);
-    else if (T == 128) ERI_COOP_GO(128, 4);
-    else return cudaErrorInvalidValue;
-  } else {
-    return cudaErrorInvalidValue;
-  }
-#undef ERI_COOP_GO
-  return cudaGetLastError();
+#define ERI_COOP_FNS_T(R, I)                                                                      \
+  (const void*)eri_coop_kernel<R, 32, true, I>, (const void*)eri_coop_kernel<R, 32, false, I>,     \
+      (const void*)eri_coop_kernel<R, 64, true, I>, (const void*)eri_coop_kernel<R, 64, false, I>, \
+      (const void*)eri_coop_kernel<R, 128, true, I>, (const void*)eri_coop_kernel<R, 128, false, I>, \
+      (const void*)eri_coop_kernel<R, 256, true, I>, (const void*)eri_coop_kernel<R, 256, false, I>
+#define ERI_COOP_FNS(R) ERI_COOP_FNS_T(R, 2), ERI_COOP_FNS_T(R, 4)
+
+// every instantiation, indexed [fp32][ilp 4][T 32/64/128/256][H not in shared memory]
+static const void* const eri_coop_fns[] = {ERI_COOP_FNS(double), ERI_COOP_FNS(float)};
+
+extern "C" cudaError_t eri_coop_launch(int T, int ilp, int fp32, const EriLaunchArgs* a, const EriCoopArgs* p,
+                                       int grid, int block, size_t smem, cudaStream_t stream) {
+  const int ti = T == 32 ? 0 : T == 64 ? 1 : T == 128 ? 2 : T == 256 ? 3 : -1;
+  if (ti < 0 || (ilp != 2 && ilp != 4)) return cudaErrorInvalidValue;
+  if (block != (T > 128 ? T : 128) && !(T <= 128 && block % T == 0 && block <= 128)) return cudaErrorInvalidValue;
+  const int idx = (fp32 ? 16 : 0) + (ilp == 4 ? 8 : 0) + 2 * ti + (p->h_in_smem ? 0 : 1);
+  EriLaunchArgs aa = *a;
+  EriCoopArgs pp = *p;
+  void* args[] = {&aa, &pp};
+  return cudaLaunchKernel(eri_coop_fns[idx], dim3(grid), dim3(block), args, smem, stream);
 }
 
-// shared memory a team needs besides its H and value slots
-extern "C" size_t eri_coop_rows_bytes(void) { return (size_t)ERI_COOP_BATCH * ERI_COOP_NC * sizeof(double); }
+// shared memory of one coefficient row, in elements, and the largest batch
+extern "C" size_t eri_coop_row_elems(void) { return (size_t)ERI_COOP_NC; }
+extern "C" int eri_coop_max_batch(void) { return ERI_COOP_BATCH; }
 
 extern "C" cudaError_t eri_coop_set_smem(size_t bytes) {
-  const void* fns[] = {
-      (const void*)eri_coop_kernel<32, true, 2>,  (const void*)eri_coop_kernel<32, false, 2>,
-      (const void*)eri_coop_kernel<64, true, 2>,  (const void*)eri_coop_kernel<64, false, 2>,
-      (const void*)eri_coop_kernel<128, true, 2>, (const void*)eri_coop_kernel<128, false, 2>,
-      (const void*)eri_coop_kernel<32, true, 4>,  (const void*)eri_coop_kernel<32, false, 4>,
-      (const void*)eri_coop_kernel<64, true, 4>,  (const void*)eri_coop_kernel<64, false, 4>,
-      (const void*)eri_coop_kernel<128, true, 4>, (const void*)eri_coop_kernel<128, false, 4>};
-  for (const void* f : fns) {
+  for (const void* f : eri_coop_fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
   }

@@ -16,6 +16,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 #include <unordered_map>
@@ -44,11 +45,16 @@ struct EriCoopArgs {
   int32_t smem_slots;
   int32_t h_in_smem;
   int32_t nteams;
+  int32_t batch;
 };
-extern "C" cudaError_t eri_coop_launch(int T, int ilp, const EriLaunchArgs* a, const EriCoopArgs* p, int grid,
-                                       int block, size_t smem, cudaStream_t stream);
+extern "C" cudaError_t eri_coop_launch(int T, int ilp, int fp32, const EriLaunchArgs* a, const EriCoopArgs* p,
+                                       int grid, int block, size_t smem, cudaStream_t stream);
 extern "C" cudaError_t eri_coop_set_smem(size_t bytes);
-extern "C" size_t eri_coop_rows_bytes(void);
+extern "C" size_t eri_coop_row_elems(void);
+extern "C" int eri_coop_max_batch(void);
+// contractions of at most this many primitive quartets per part use the
+// cooperative tier's shallow-contraction shape (the generator's SHALLOW_ROWS)
+static const int kShallowK4 = 12;
 
 struct EriRegEntry {
   int8_t ls[4];
@@ -56,6 +62,8 @@ struct EriRegEntry {
 };
 extern "C" const EriRegEntry eri_reg_table[];
 extern "C" const int eri_reg_count;
+extern "C" const EriRegEntry eri_reg_f32_table[];  // FP32-recurrence forms
+extern "C" const int eri_reg_f32_count;
 
 // ---------------------------------------------------------------------------
 // errors
@@ -112,7 +120,9 @@ struct Library {
   std::vector<double> boys, c2s;
   std::map<std::vector<int>, std::unique_ptr<ClassProg>> progs;  // key: ls[4] + opts[3]
   std::map<std::vector<int>, std::unique_ptr<CoopProg>> coops;   // key: ls[4] + opts[3]
+  std::map<std::vector<int>, std::unique_ptr<CoopProg>> coops_shallow;  // shapes for K4 <= kShallowK4
   std::map<std::vector<int>, const void*> reg;                      // key: ls[4]
+  std::map<std::vector<int>, const void*> reg_f32;                  // key: ls[4]
   double* d_boys = nullptr;
   double* d_c2s = nullptr;
   int device = -1;
@@ -177,8 +187,12 @@ bool load_blob(Library& L, const std::string& path, bool tables) {
     std::vector<int> key = {p->ls[0], p->ls[1], p->ls[2], p->ls[3], p->opts[0], p->opts[1], p->opts[2]};
     L.progs[key] = std::move(p);
   }
-  uint32_t ncoop = 0;
-  if (ok && rd(f, &ncoop)) {
+  // team-cooperative programs: the deep-contraction section, then the
+  // shallow-contraction section (shapes that differ from the deep one)
+  for (int section = 0; section < 2 && ok; ++section) {
+    uint32_t ncoop = 0;
+    if (!rd(f, &ncoop)) break;
+    auto& dst = section == 0 ? L.coops : L.coops_shallow;
     for (uint32_t c = 0; ok && c < ncoop; ++c) {
       auto p = std::make_unique<CoopProg>();
       int8_t hdr[8];
@@ -208,7 +222,7 @@ bool load_blob(Library& L, const std::string& path, bool tables) {
            rd(f, p->ph1.data(), p->ph1.size()) && rd(f, p->ph2.data(), p->ph2.size());
       if (!ok) break;
       std::vector<int> key = {p->ls[0], p->ls[1], p->ls[2], p->ls[3], p->opts[0], p->opts[1], p->opts[2]};
-      L.coops[key] = std::move(p);
+      dst[key] = std::move(p);
     }
   }
   fclose(f);
@@ -232,6 +246,10 @@ int ensure_library() {
     for (int i = 0; i < eri_reg_count; ++i) {
       const EriRegEntry& e = eri_reg_table[i];
       L.reg[{e.ls[0], e.ls[1], e.ls[2], e.ls[3]}] = e.fn;
+    }
+    for (int i = 0; i < eri_reg_f32_count; ++i) {
+      const EriRegEntry& e = eri_reg_f32_table[i];
+      L.reg_f32[{e.ls[0], e.ls[1], e.ls[2], e.ls[3]}] = e.fn;
     }
     L.loaded = true;
   }
@@ -379,6 +397,11 @@ struct Bucket {
   double flops = 0;              // algorithmic FP64 flops of this launch
   CoopProg* coop = nullptr;      // team-cooperative tier
   int smem_slots = 0, h_in_smem = 0, nteams = 0;
+  int batch = 0;                 // cooperative tier: coefficient rows per team
+  int fp32 = 0;                  // recurrences in FP32 (quartets with a small Schwarz bound)
+  int round = 0;                 // part round: buckets of a round are independent
+  int lane = 0;                  // stream of its round (0 = the caller's stream)
+  bool shared_scratch = false;   // uses the plan's global scratch (runs on lane 0)
 };
 
 template <typename T>
@@ -416,6 +439,8 @@ struct eri_plan_s {
   int npair = 0;
   int64_t npprim = 0;
   double flops = 0, nprimq = 0;
+  double flops32 = 0;            // FP32 flops of the reduced-precision buckets
+  int64_t nparts32 = 0;          // quartet parts evaluated with FP32 recurrences
   DevBuf<DevShell> shells;
   DevBuf<double> exps, coefs;
   DevBuf<DevPairIn> pin;
@@ -433,10 +458,17 @@ struct eri_plan_s {
   DevBuf<int64_t> d_offsets;
   DevBuf<int32_t> d_nab;
   cudaGraphExec_t graph_exec = nullptr;
+  int nlanes = 1;                      // streams one round's launches may use
+  std::vector<cudaStream_t> lanes;     // lanes[k - 1] = stream of lane k >= 1 (plan-owned)
+  cudaEvent_t fork_ev = nullptr;       // caller stream -> lanes
+  std::vector<cudaEvent_t> join_ev;    // lane -> caller stream
   bool timing = false;
   std::vector<cudaEvent_t> events;  // two per launch: pair set-up, then buckets
   ~eri_plan_s() {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaEvent_t e : join_ev) cudaEventDestroy(e);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    for (cudaStream_t s : lanes) cudaStreamDestroy(s);
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
   }
 };
@@ -444,15 +476,17 @@ struct eri_plan_s {
 static int nfun(int l, bool cart) { return cart ? (l + 1) * (l + 2) / 2 : 2 * l + 1; }
 int preferred_tier(const int ls[4]);
 
-extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
-                        int64_t nq, const eri_opts* opts_in, eri_plan_t** plan_out) {
+static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
+                     int64_t nq, const double* qbound, double fp32_below, const eri_opts* opts_in,
+                     eri_plan_t** plan_out) {
   if (!plan_out) return fail(ERI_EINVAL, "plan_out is NULL");
   *plan_out = nullptr;
   eri_opts opts;
   memset(&opts, 0, sizeof opts);
   if (opts_in) opts = *opts_in;
   if (opts.axis_rule < 0 || opts.axis_rule > 2 || opts.schedule < 0 || opts.schedule > 1 || opts.sph_mode < 0 ||
-      opts.sph_mode > 2 || opts.tier < 0 || opts.tier > 4 || opts.orientation < 0 || opts.orientation > 2)
+      opts.sph_mode > 2 || opts.tier < 0 || opts.tier > 4 || opts.orientation < 0 || opts.orientation > 2 ||
+      opts.streams < 0 || opts.streams > 8)
     return fail(ERI_EINVAL, "option out of range");
   if (nq < 0 || nshell < 0 || (nq > 0 && (!shells || !basis || !quartets)))
     return fail(ERI_EINVAL, "NULL or negative argument");
@@ -542,16 +576,21 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
   // pair's primitive pairs) that different teams run concurrently.
   const int kCoopChunk = 32;
   const bool default_opts0 = opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0;
+  // class code ((la * 5 + lb) * 5 + lc) * 5 + ld; per-code answers cached
+  std::vector<int8_t> coop_of(625, -1);
   auto is_coop = [&](int la, int lb, int lc, int ld) {
-    std::vector<int> key = {la, lb, lc, ld, opts.axis_rule, opts.schedule, opts.sph_mode};
-    if (L.coops.find(key) == L.coops.end()) return false;
-    if (opts.tier == TIER_COOP) return true;
-    if (opts.tier != 0) return false;
-    return !(default_opts0 && L.reg.count({la, lb, lc, ld}));
+    int8_t& c = coop_of[((la * 5 + lb) * 5 + lc) * 5 + ld];
+    if (c < 0) {
+      std::vector<int> key = {la, lb, lc, ld, opts.axis_rule, opts.schedule, opts.sph_mode};
+      bool v = L.coops.find(key) != L.coops.end();
+      if (v && opts.tier != TIER_COOP) v = opts.tier == 0 && !(default_opts0 && L.reg.count({la, lb, lc, ld}));
+      c = v ? 1 : 0;
+    }
+    return c == 1;
   };
-  std::map<std::tuple<int, int, int>, int> alias_id;
+  std::unordered_map<uint64_t, int> alias_id;
   auto get_alias = [&](int parent, int start, int count) {
-    auto key = std::make_tuple(parent, start, count);
+    const uint64_t key = ((uint64_t)(uint32_t)parent << 32) | ((uint64_t)(uint32_t)start << 16) | (uint32_t)count;
     auto it = alias_id.find(key);
     if (it != alias_id.end()) return it->second;
     DevPairIn d = pin[parent];
@@ -564,7 +603,7 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
     return id;
   };
   bool any_reduce = false;
-  auto split = [&](int s0, int s1, PairPart* out) {
+  auto split_uncached = [&](int s0, int s1, PairPart* out) {
     const int l0 = shells[s0].l, l1 = shells[s1].l;
     if (opts.orientation == 1 || opts.orientation == 2) {
       bool first = opts.orientation == 1 ? l0 >= l1
@@ -589,18 +628,41 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
     }
     return k;
   };
+  struct SplitRes {
+    int n;
+    PairPart part[2];
+  };
+  std::unordered_map<uint64_t, SplitRes> split_cache;
+  auto split = [&](int s0, int s1, PairPart* out) {
+    const uint64_t key = ((uint64_t)(uint32_t)s0 << 32) | (uint32_t)s1;
+    auto it = split_cache.find(key);
+    if (it == split_cache.end()) {
+      SplitRes r;
+      r.n = split_uncached(s0, s1, r.part);
+      it = split_cache.emplace(key, r).first;
+    }
+    out[0] = it->second.part[0];
+    out[1] = it->second.part[1];
+    return it->second.n;
+  };
   struct QInfo {
     int cls;    // class key index
     int round;  // part number within its quartet: 0 writes the block, later parts add
     int kb, kk;
+    int prec;   // 1: FP32 recurrences
     EriQuartetRec rec;
   };
+  // reduced precision is offered for the default generator options, where
+  // every class has an FP32 form (register or team-cooperative tier)
+  const bool mixed = qbound != nullptr && opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0 &&
+                     (opts.tier == 0 || opts.tier == TIER_REG || opts.tier == TIER_COOP);
   std::vector<QInfo> qi;
-  qi.reserve(nq);
-  std::map<std::vector<int>, int> cls_index;
+  qi.reserve(nq + nq / 2);
+  std::vector<int> cls_index(625, -1);  // class code -> class key index
   std::vector<std::vector<int>> cls_keys;
   for (int64_t q = 0; q < nq; ++q) {
     const int32_t* s = quartets + 4 * q;
+    const int prec = mixed && qbound[q] < fp32_below ? 1 : 0;
     int n[4];
     for (int k = 0; k < 4; ++k) n[k] = nfun(shells[s[k]].l, cart);
     const int ustride[4] = {n[1] * n[2] * n[3], n[2] * n[3], n[3], 1};
@@ -624,11 +686,10 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
           std::swap(lb0, lk0);
           std::swap(lb1, lk1);
         }
-        std::vector<int> key = {lb0, lb1, lk0, lk1};
-        auto it = cls_index.find(key);
-        if (it == cls_index.end()) {
-          it = cls_index.emplace(key, (int)cls_keys.size()).first;
-          cls_keys.push_back(key);
+        int& cidx = cls_index[((lb0 * 5 + lb1) * 5 + lk0) * 5 + lk1];
+        if (cidx < 0) {
+          cidx = (int)cls_keys.size();
+          cls_keys.push_back({lb0, lb1, lk0, lk1});
         }
         int cb = B.nprim, nchunk = 1;
         if ((int64_t)B.nprim * K.nprim > kCoopChunk && is_coop(lb0, lb1, lk0, lk1)) {
@@ -643,10 +704,11 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
           x.rec.ket = K.pair;
           x.rec.out_off = plan->offsets[q];
           for (int k = 0; k < 4; ++k) x.rec.st[k] = ustride[pos[k]];
-          x.cls = it->second;
+          x.cls = cidx;
           x.round = round;
           x.kb = cnt;
           x.kk = K.nprim;
+          x.prec = prec;
           qi.push_back(x);
         }
         if (nchunk > 1) any_reduce = true;
@@ -656,9 +718,9 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
   plan->zero_out = any_reduce;
   if (pprim > ((int64_t)1 << 31) - 1) return fail(ERI_EINVAL, "too many primitive pairs");
   // ---- buckets: by part round (a block is written before it is added to),
-  // then class (heaviest first), then contraction signature
-  std::vector<int64_t> order(nparts);
-  for (int64_t q = 0; q < nparts; ++q) order[q] = q;
+  // then class (heaviest first), precision, then contraction signature
+  // (K4 descending, then bra depth descending).  One counting sort over a
+  // dense key; equal keys keep their input order.
   std::vector<int> cls_rank(cls_keys.size());
   {
     std::vector<int> idx(cls_keys.size());
@@ -673,28 +735,78 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
     });
     for (size_t r = 0; r < idx.size(); ++r) cls_rank[idx[r]] = (int)r;
   }
-  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-    if (qi[a].round != qi[b].round) return qi[a].round < qi[b].round;
-    if (qi[a].cls != qi[b].cls) return cls_rank[qi[a].cls] < cls_rank[qi[b].cls];
-    const int64_t ka = (int64_t)qi[a].kb * qi[a].kk, kb = (int64_t)qi[b].kb * qi[b].kk;
-    if (ka != kb) return ka > kb;
-    return qi[a].kb > qi[b].kb;
-  });
+  const int64_t ncls = (int64_t)cls_keys.size();
+  auto gid = [&](const QInfo& x) { return ((int64_t)x.round * ncls + cls_rank[x.cls]) * 2 + x.prec; };
+  struct PartKey {
+    int32_t cls, round, prec, kb, kk;
+  };
+  std::vector<PartKey> pk(nparts);
   std::vector<EriQuartetRec> recs(nparts);
-  for (int64_t i = 0; i < nparts; ++i) recs[i] = qi[order[i]].rec;
+  {
+    // dense ids: used (round, class, precision) groups and (K4, kb) signatures
+    std::vector<int32_t> gdense(4 * ncls * 2, -1);
+    std::unordered_map<uint64_t, int32_t> sig_id;
+    std::vector<std::pair<int64_t, int32_t>> sigs;  // (K4, kb)
+    std::vector<uint32_t> key(nparts);
+    for (int64_t q = 0; q < nparts; ++q) {
+      const QInfo& x = qi[q];
+      gdense[gid(x)] = 0;
+      const uint64_t sk = ((uint64_t)(uint32_t)x.kb << 32) | (uint32_t)x.kk;
+      auto it = sig_id.find(sk);
+      if (it == sig_id.end()) {
+        it = sig_id.emplace(sk, (int32_t)sigs.size()).first;
+        sigs.push_back({(int64_t)x.kb * x.kk, x.kb});
+      }
+      key[q] = (uint32_t)it->second;
+    }
+    int32_t ng = 0;
+    for (int32_t& g : gdense)
+      if (g == 0) g = ng++;
+    std::vector<int32_t> sig_rank(sigs.size());
+    {
+      std::vector<int32_t> idx(sigs.size());
+      for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int32_t)i;
+      std::sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return sigs[a] > sigs[b]; });
+      for (size_t r = 0; r < idx.size(); ++r) sig_rank[idx[r]] = (int32_t)r;
+    }
+    const int64_t ns = (int64_t)sigs.size(), nkey = (int64_t)ng * ns;
+    if (nkey > ((int64_t)1 << 27)) return fail(ERI_EUNSUPPORTED, "too many distinct contraction signatures");
+    std::vector<int64_t> start(nkey + 1, 0);
+    for (int64_t q = 0; q < nparts; ++q) {
+      key[q] = (uint32_t)(gdense[gid(qi[q])] * ns + sig_rank[key[q]]);
+      ++start[key[q] + 1];
+    }
+    for (int64_t k = 0; k < nkey; ++k) start[k + 1] += start[k];
+    for (int64_t q = 0; q < nparts; ++q) {
+      const QInfo& x = qi[q];
+      const int64_t p = start[key[q]]++;
+      recs[p] = x.rec;
+      pk[p] = {x.cls, x.round, x.prec, x.kb, x.kk};
+    }
+  }
+  std::vector<QInfo>().swap(qi);  // release the unsorted parts
   // ---- launches: one per (class, group size); G lanes share a quartet and
-  // split its K4 primitive quartets, about three per lane
-  // G = lanes per quartet: about three primitive quartets per lane, but no
-  // more lanes than needed to give the launch ~16 warps per SM (every extra
-  // lane costs a share of the accumulator reduction)
-  std::map<std::tuple<int, int, int64_t>, int64_t> k4_count;
-  for (const QInfo& x : qi) ++k4_count[std::make_tuple(x.round, x.cls, (int64_t)x.kb * x.kk)];
+  // split its K4 primitive quartets: about three primitive quartets per lane,
+  // but no more lanes than needed to give the launch ~16 warps per SM (every
+  // extra lane costs a share of the accumulator reduction).  run_len[i] =
+  // the number of parts with part i's (round, class, precision, K4): a run of
+  // the sorted order.
+  auto same_group = [](const PartKey& a, const PartKey& b) {
+    return a.cls == b.cls && a.round == b.round && a.prec == b.prec;
+  };
+  std::vector<int64_t> run_len(nparts);
+  for (int64_t i = 0; i < nparts;) {
+    const int64_t k4 = (int64_t)pk[i].kb * pk[i].kk;
+    int64_t j = i + 1;
+    while (j < nparts && same_group(pk[j], pk[i]) && (int64_t)pk[j].kb * pk[j].kk == k4) ++j;
+    for (int64_t t = i; t < j; ++t) run_len[t] = j - i;
+    i = j;
+  }
   const int64_t lanes_target = (int64_t)L.nsm * 512;
-  auto group_of = [&](const QInfo& x) {
-    const int64_t k4 = (int64_t)x.kb * x.kk;
-    const int64_t cnt = k4_count[std::make_tuple(x.round, x.cls, k4)];
+  auto group_at = [&](int64_t i) {
+    const int64_t k4 = (int64_t)pk[i].kb * pk[i].kk;
     int64_t want = std::min<int64_t>(32, std::max<int64_t>(1, (k4 + 2) / 3));
-    want = std::min<int64_t>(want, std::max<int64_t>(1, lanes_target / std::max<int64_t>(1, cnt)));
+    want = std::min<int64_t>(want, std::max<int64_t>(1, lanes_target / std::max<int64_t>(1, run_len[i])));
     int g = 1;
     while (g * 2 <= want) g *= 2;
     return g;
@@ -704,20 +816,26 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
   size_t max_coop_vals = 0, max_coop_h = 0;
   const bool default_opts = opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0;
   for (int64_t i = 0; i < nparts;) {
-    const int c = qi[order[i]].cls;
-    const int round = qi[order[i]].round;
+    const int c = pk[i].cls;
+    const int round = pk[i].round;
+    const int prec = pk[i].prec;
     Bucket b;
+    b.fp32 = prec;
     for (int k = 0; k < 4; ++k) b.ls[k] = cls_keys[c][k];
     std::vector<int> pkey = {b.ls[0], b.ls[1], b.ls[2], b.ls[3], opts.axis_rule, opts.schedule, opts.sph_mode};
     auto pit = L.progs.find(pkey);
     ClassProg* prog = pit == L.progs.end() ? nullptr : pit->second.get();
     auto cit = L.coops.find(pkey);
     CoopProg* cp = cit == L.coops.end() ? nullptr : cit->second.get();
-    auto rit = L.reg.find({b.ls[0], b.ls[1], b.ls[2], b.ls[3]});
-    const void* regfn = (rit != L.reg.end() && default_opts) ? rit->second : nullptr;
+    const auto& regmap = prec ? L.reg_f32 : L.reg;
+    auto rit = regmap.find({b.ls[0], b.ls[1], b.ls[2], b.ls[3]});
+    const void* regfn = (rit != regmap.end() && default_opts) ? rit->second : nullptr;
     const size_t smem_need = prog ? (size_t)prog->nslot * 128 * sizeof(double) : 0;
     int tier = opts.tier;
-    if (tier == 0) {
+    if (prec && tier == 0) {
+      // FP32 forms: the compiled register kernel, else the cooperative program
+      tier = regfn ? TIER_REG : TIER_COOP;
+    } else if (tier == 0) {
       // the autotuner's choice when it is feasible, else the static rule
       const int pt = preferred_tier(b.ls);
       const bool ok = (pt == TIER_REG && regfn) || (pt == TIER_COOP && cp) ||
@@ -735,12 +853,17 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
       return fail(ERI_EUNSUPPORTED, "class does not fit the shared-memory tier");
     // one launch per class for the cooperative tier (a team walks all the
     // primitive quartets of its shell quartet); otherwise one per group size
-    const int g = tier == TIER_COOP ? 1 : group_of(qi[order[i]]);
+    const int g = tier == TIER_COOP ? 1 : group_at(i);
+    // K4 of the bucket's first (deepest) part; cooperative buckets split at
+    // the shallow-contraction boundary
+    const int64_t k4_first = (int64_t)pk[i].kb * pk[i].kk;
+    const bool shallow = tier == TIER_COOP && k4_first <= kShallowK4;
     int64_t j = i;
     double kprim = 0;
-    while (j < nparts && qi[order[j]].cls == c && qi[order[j]].round == round &&
-           (tier == TIER_COOP || group_of(qi[order[j]]) == g)) {
-      kprim += (double)qi[order[j]].kb * qi[order[j]].kk;
+    while (j < nparts && pk[j].cls == c && pk[j].round == round && pk[j].prec == prec &&
+           (tier == TIER_COOP ? ((int64_t)pk[j].kb * pk[j].kk <= kShallowK4) == shallow
+                              : group_at(j) == g)) {
+      kprim += (double)pk[j].kb * pk[j].kk;
       ++j;
     }
     b.first = i;
@@ -765,16 +888,22 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
       // team-cooperative: value slots (and H when it fits) in shared memory.
       // Pick the block shape (teams per block) and the H placement that keep
       // the most warps resident per SM, up to 16.
+      if (shallow) {
+        auto sit = L.coops_shallow.find(pkey);
+        if (sit != L.coops_shallow.end()) cp = sit->second.get();
+      }
       b.coop = cp;
+      b.batch = (int)std::min<int64_t>(eri_coop_max_batch(), std::max<int64_t>(1, k4_first));
       const size_t smem_sm = L.smem_per_sm, reserve = 1024;
       int best_warps = -1;
-      const size_t rows = eri_coop_rows_bytes() / sizeof(double);
+      const size_t rows = eri_coop_row_elems() * (size_t)b.batch;
+      const size_t elem = prec ? sizeof(float) : sizeof(double);
       for (int h_in = 1; h_in >= 0; --h_in) {
-        for (int tpb = 128 / cp->T; tpb >= 1; tpb /= 2) {
+        for (int tpb = std::max(1, 128 / cp->T); tpb >= 1; tpb /= 2) {
           // every value slot lives in shared memory; H too when it fits
           const size_t per_team = rows + cp->nslot + (h_in ? (size_t)cp->nh : 0);
-          if (per_team * tpb * sizeof(double) > L.smem_optin) continue;
-          const size_t bsm = per_team * tpb * sizeof(double);
+          if (per_team * tpb * elem > L.smem_optin) continue;
+          const size_t bsm = (per_team * tpb * elem + 15) / 16 * 16;
           // registers: the 4-nodes-per-lane kernels hold ~230 registers, so at
           // most 256 of their threads per SM; the others at most 512
           const size_t max_threads = cp->ilp == 4 ? 256 : 512;
@@ -804,11 +933,57 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
     if (prog) {
       if ((tier == TIER_SHARED || tier == TIER_GLOBAL) && (rc = upload_prog(prog))) return rc;
       b.flops = kprim * prog->flops_prim + (double)b.count * prog->flops_p2;
-      plan->flops += b.flops;
+      if (prec) {
+        plan->flops32 += b.flops;
+        plan->nparts32 += b.count;
+      } else {
+        plan->flops += b.flops;
+      }
     }
     plan->nprimq += kprim;
+    b.round = round;
+    b.shared_scratch = tier == TIER_GLOBAL || (tier == TIER_COOP && (!b.h_in_smem || b.smem_slots < cp->nslot));
     plan->buckets.push_back(b);
     i = j;
+  }
+  // ---- concurrency: the launches of one part round write distinct blocks,
+  // so they may overlap on several streams (fork/join per round); launches
+  // on the plan's global scratch stay on the caller's stream.  Greedy
+  // assignment, heaviest class first, by estimated cost (flops plus a fixed
+  // per-launch share).
+  {
+    std::set<std::vector<int>> classes;
+    for (const Bucket& b : plan->buckets) classes.insert({b.ls[0], b.ls[1], b.ls[2], b.ls[3]});
+    const int want = opts.streams > 0 ? opts.streams : (classes.size() > 1 ? 4 : 1);
+    int used = 1;
+    for (size_t i = 0; i < plan->buckets.size();) {
+      size_t j = i;
+      while (j < plan->buckets.size() && plan->buckets[j].round == plan->buckets[i].round) ++j;
+      std::vector<double> load(want, 0.0);
+      for (size_t k = i; k < j; ++k) {
+        Bucket& b = plan->buckets[k];
+        int lane = 0;
+        if (!b.shared_scratch)
+          for (int l = 1; l < want; ++l)
+            if (load[l] < load[lane]) lane = l;
+        b.lane = lane;
+        load[lane] += b.flops + 2e7;
+        used = std::max(used, lane + 1);
+      }
+      i = j;
+    }
+    plan->nlanes = used;
+    if (used > 1) {
+      CUDA_OR(cudaEventCreateWithFlags(&plan->fork_ev, cudaEventDisableTiming), "cudaEventCreate");
+      for (int l = 1; l < used; ++l) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        CUDA_OR(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "cudaStreamCreate");
+        plan->lanes.push_back(st);
+        CUDA_OR(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate");
+        plan->join_ev.push_back(ev);
+      }
+    }
   }
   if ((rc = plan->coop_vals.alloc(max_coop_vals, "cooperative spill")) ||
       (rc = plan->coop_h.alloc(max_coop_h, "cooperative accumulators")))
@@ -858,6 +1033,21 @@ extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis
   return ERI_OK;
 }
 
+extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
+                        int64_t nq, const eri_opts* opts, eri_plan_t** plan_out) {
+  return plan_impl(shells, nshell, basis, quartets, nq, nullptr, 0.0, opts, plan_out);
+}
+
+extern "C" int eri_plan_mixed(const eri_shell* shells, int32_t nshell, const eri_basis* basis,
+                              const int32_t* quartets, int64_t nq, const double* qbound, double fp32_below,
+                              const eri_opts* opts, eri_plan_t** plan_out) {
+  if (nq > 0 && !qbound) return fail(ERI_EINVAL, "NULL bound array");
+  if (!(fp32_below >= 0) || !std::isfinite(fp32_below)) return fail(ERI_EINVAL, "bad FP32 threshold");
+  for (int64_t q = 0; q < nq; ++q)
+    if (!(qbound[q] >= 0)) return fail(ERI_EINVAL, "negative or NaN Schwarz bound");
+  return plan_impl(shells, nshell, basis, quartets, nq, qbound, fp32_below, opts, plan_out);
+}
+
 extern "C" int64_t eri_output_count(const eri_plan_t* plan) { return plan ? plan->offsets.back() : 0; }
 
 extern "C" int eri_output_offsets(const eri_plan_t* plan, int64_t* offsets) {
@@ -882,9 +1072,22 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
     }
   }
   size_t li = 0;
+  cudaStream_t cur = stream;  // stream of the current launch
   auto mark = [&](int end) -> cudaError_t {
-    return plan->timing ? cudaEventRecord(plan->events[2 * li + end], stream) : cudaSuccess;
+    return plan->timing ? cudaEventRecord(plan->events[2 * li + end], cur) : cudaSuccess;
   };
+  // lanes of the current round that received work, to join back
+  std::vector<char> lane_used(plan->nlanes, 0);
+  auto join_round = [&]() -> int {
+    for (int l = 1; l < plan->nlanes; ++l) {
+      if (!lane_used[l]) continue;
+      CUDA_OR(cudaEventRecord(plan->join_ev[l - 1], plan->lanes[l - 1]), "cudaEventRecord (join)");
+      CUDA_OR(cudaStreamWaitEvent(stream, plan->join_ev[l - 1], 0), "cudaStreamWaitEvent (join)");
+      lane_used[l] = 0;
+    }
+    return ERI_OK;
+  };
+  int cur_round = -1;
   if (plan->zero_out)
     CUDA_OR(cudaMemsetAsync(out, 0, (size_t)plan->offsets.back() * sizeof(double), stream), "zero output");
   {
@@ -899,6 +1102,20 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
     ++li;
   }
   for (const Bucket& b : plan->buckets) {
+    if (b.round != cur_round) {
+      // a round's blocks are complete before the next round adds to them
+      if (int rc = join_round()) return rc;
+      cur_round = b.round;
+      if (plan->nlanes > 1) CUDA_OR(cudaEventRecord(plan->fork_ev, stream), "cudaEventRecord (fork)");
+    }
+    cur = stream;
+    if (b.lane > 0) {
+      cur = plan->lanes[b.lane - 1];
+      if (!lane_used[b.lane]) {
+        CUDA_OR(cudaStreamWaitEvent(cur, plan->fork_ev, 0), "cudaStreamWaitEvent (fork)");
+        lane_used[b.lane] = 1;
+      }
+    }
     CUDA_OR(mark(0), "cudaEventRecord");
     EriLaunchArgs a;
     a.quartets = plan->quartets.p + b.first;
@@ -912,7 +1129,7 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
     a.group = b.group;
     if (b.tier == TIER_REG) {
       void* args[] = {&a};
-      CUDA_OR(cudaLaunchKernel(b.reg_fn, dim3(b.grid), dim3(b.block), args, 0, stream), "class kernel launch");
+      CUDA_OR(cudaLaunchKernel(b.reg_fn, dim3(b.grid), dim3(b.block), args, 0, cur), "class kernel launch");
     } else if (b.tier == TIER_COOP) {
       const CoopProg* cp = b.coop;
       EriCoopArgs p;
@@ -931,7 +1148,9 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
       p.smem_slots = b.smem_slots;
       p.h_in_smem = b.h_in_smem;
       p.nteams = b.nteams;
-      CUDA_OR(eri_coop_launch(cp->T, cp->ilp, &a, &p, b.grid, b.block, b.smem, stream), "cooperative launch");
+      p.batch = b.batch;
+      CUDA_OR(eri_coop_launch(cp->T, cp->ilp, b.fp32, &a, &p, b.grid, b.block, b.smem, cur),
+              "cooperative launch");
     } else {
       EriProgArgs p;
       p.ph1 = b.prog->d_ph1;
@@ -941,12 +1160,12 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
       p.n2 = b.prog->n2;
       p.nh = b.prog->nh;
       p.L = b.prog->L;
-      CUDA_OR(eri_exec_launch(b.tier == TIER_SHARED, &a, &p, b.grid, b.block, b.smem, stream), "executor launch");
+      CUDA_OR(eri_exec_launch(b.tier == TIER_SHARED, &a, &p, b.grid, b.block, b.smem, cur), "executor launch");
     }
     CUDA_OR(mark(1), "cudaEventRecord");
     ++li;
   }
-  return ERI_OK;
+  return join_round();
 }
 
 extern "C" int eri_plan_set_timing(eri_plan_t* plan, int enable) {
@@ -1011,10 +1230,15 @@ extern "C" int eri_compute_host(eri_plan_t* plan, double* host_out, void* stream
 
 extern "C" int eri_plan_stats(const eri_plan_t* plan, double* stats, int n) {
   if (!plan || !stats || n < 0) return fail(ERI_EINVAL, "bad argument");
-  const double v[6] = {(double)plan->buckets.size(), plan->flops, (double)(plan->scratch.n * sizeof(double)),
-                       (double)plan->nq, plan->nprimq, plan->h2d_bytes};
-  for (int i = 0; i < n && i < 6; ++i) stats[i] = v[i];
+  const double v[8] = {(double)plan->buckets.size(), plan->flops, (double)(plan->scratch.n * sizeof(double)),
+                       (double)plan->nq, plan->nprimq, plan->h2d_bytes, plan->flops32, (double)plan->nparts32};
+  for (int i = 0; i < n && i < 8; ++i) stats[i] = v[i];
   return ERI_OK;
+}
+
+extern "C" int eri_plan_launch_precision(const eri_plan_t* plan, int i) {
+  if (!plan || i < 0 || i >= eri_plan_launch_count(plan)) return fail(ERI_EINVAL, "bad launch index");
+  return i > 0 && plan->buckets[i - 1].fp32 ? 32 : 64;
 }
 
 extern "C" int eri_plan_destroy(eri_plan_t* plan) {

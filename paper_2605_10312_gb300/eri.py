@@ -41,7 +41,8 @@ class _Basis(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("axis_rule", ctypes.c_int32), ("schedule", ctypes.c_int32), ("sph_mode", ctypes.c_int32),
-                ("tier", ctypes.c_int32), ("orientation", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("tier", ctypes.c_int32), ("orientation", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 _lib = None
@@ -57,6 +58,12 @@ def library(path: str = LIB):
         lib.eri_plan.restype = ctypes.c_int
         lib.eri_plan.argtypes = [ctypes.POINTER(_Shell), ctypes.c_int32, ctypes.POINTER(_Basis), ctypes.c_void_p,
                                  ctypes.c_int64, ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_void_p)]
+        lib.eri_plan_mixed.restype = ctypes.c_int
+        lib.eri_plan_mixed.argtypes = [ctypes.POINTER(_Shell), ctypes.c_int32, ctypes.POINTER(_Basis),
+                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
+                                       ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_void_p)]
+        lib.eri_plan_launch_precision.restype = ctypes.c_int
+        lib.eri_plan_launch_precision.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.eri_output_count.restype = ctypes.c_int64
         lib.eri_output_count.argtypes = [ctypes.c_void_p]
         lib.eri_output_offsets.restype = ctypes.c_int
@@ -108,25 +115,38 @@ class Plan:
     """A device-resident plan for one quartet list (see eri_plan)."""
 
     def __init__(self, basis, quartets, axis_rule="prose", schedule="dsa", sph_mode="stepwise", tier="auto",
-                 orientation="split"):
+                 orientation="split", qbound=None, fp32_below=None, streams=0):
+        """qbound/fp32_below: mixed precision (eri_plan_mixed) -- quartets whose
+        bound is below fp32_below run their recurrences in FP32."""
         lib = library()
         q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
         ns = int(basis.shell_l.shape[0])
-        sh = (_Shell * max(ns, 1))()
-        for i in range(ns):
-            sh[i].l = int(basis.shell_l[i])
-            sh[i].nprim = int(basis.shell_nprim[i])
-            sh[i].center = int(basis.shell_center[i])
-            sh[i].prim_offset = int(basis.shell_prim[i])
+        # eri_shell records {l, nprim, center, prim_offset}, int32 each
+        shv = np.empty((max(ns, 1), 4), dtype=np.int32)
+        if ns:
+            shv[:, 0] = basis.shell_l
+            shv[:, 1] = basis.shell_nprim
+            shv[:, 2] = basis.shell_center
+            shv[:, 3] = basis.shell_prim
+        sh = shv.ctypes.data_as(ctypes.POINTER(_Shell))
         self._keep = [np.ascontiguousarray(basis.centers, dtype=np.float64),
                       np.ascontiguousarray(basis.exps, dtype=np.float64),
-                      np.ascontiguousarray(basis.coefs, dtype=np.float64), q]
+                      np.ascontiguousarray(basis.coefs, dtype=np.float64), q, shv]
         b = _Basis(self._keep[0].ctypes.data, int(self._keep[0].shape[0]), self._keep[1].ctypes.data,
                    self._keep[2].ctypes.data, int(self._keep[1].shape[0]))
         o = _Opts(AXIS_RULES[axis_rule], SCHEDULES[schedule], SPH_MODES[sph_mode], TIERS[tier],
-                  ORIENTATIONS[orientation])
+                  ORIENTATIONS[orientation], int(streams))
         h = ctypes.c_void_p()
-        _check(lib.eri_plan(sh, ns, ctypes.byref(b), q.ctypes.data, q.shape[0], ctypes.byref(o), ctypes.byref(h)))
+        if qbound is None:
+            _check(lib.eri_plan(sh, ns, ctypes.byref(b), q.ctypes.data, q.shape[0], ctypes.byref(o),
+                                ctypes.byref(h)))
+        else:
+            qb = np.ascontiguousarray(np.asarray(qbound, dtype=np.float64).reshape(-1))
+            if qb.shape[0] != q.shape[0]:
+                raise ValueError("qbound needs one entry per quartet")
+            _check(lib.eri_plan_mixed(sh, ns, ctypes.byref(b), q.ctypes.data, q.shape[0], qb.ctypes.data,
+                                      float(fp32_below if fp32_below is not None else 0.0), ctypes.byref(o),
+                                      ctypes.byref(h)))
         self._h = h
         self.nq = q.shape[0]
         self._keep = None
@@ -149,10 +169,11 @@ class Plan:
         return off
 
     def stats(self) -> dict:
-        s = np.zeros(6)
-        _check(library().eri_plan_stats(self._h, s.ctypes.data, 6))
+        s = np.zeros(8)
+        _check(library().eri_plan_stats(self._h, s.ctypes.data, 8))
         return dict(launches=int(s[0]), flops=float(s[1]), scratch_bytes=float(s[2]), quartets=int(s[3]),
-                    primitive_quartets=float(s[4]), h2d_bytes=float(s[5]))
+                    primitive_quartets=float(s[4]), h2d_bytes=float(s[5]), flops_fp32=float(s[6]),
+                    fp32_parts=int(s[7]))
 
     def set_timing(self, enable=True):
         _check(library().eri_plan_set_timing(self._h, 1 if enable else 0))
@@ -168,7 +189,8 @@ class Plan:
             ms = ctypes.c_float()
             _check(lib.eri_plan_launch_info(self._h, i, info.ctypes.data, ctypes.byref(fl), ctypes.byref(ms)))
             out.append(dict(cls=tuple(int(x) for x in info[:4]), tier=int(info[4]), grid=int(info[5]),
-                            block=int(info[6]), quartets=int(info[7]), flops=fl.value, ms=ms.value))
+                            block=int(info[6]), quartets=int(info[7]), flops=fl.value, ms=ms.value,
+                            precision=int(lib.eri_plan_launch_precision(self._h, i))))
         return out
 
     def compute(self, out, stream=None):

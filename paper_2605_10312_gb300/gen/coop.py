@@ -291,33 +291,62 @@ def build(prog, T=128, ilp=ILP):
     return CoopProgram(T, ilp, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(p2.out_dims), eff1, eff2)
 
 
-ROWS_BYTES = 32 * 56 * 8     # coefficient rows of one team (executor constant)
+ROW_BYTES = 56 * 8           # one primitive quartet's coefficient row (executor constant)
+DEEP_ROWS = 32               # rows per team for deep contractions (one per lane of a warp)
+SHALLOW_ROWS = 12            # rows per team for contractions of at most 12 primitive quartets
 SMEM_PER_SM = 228 * 1024
+SHAPES = ((32, 2), (64, 2), (128, 2), (128, 4))
 
 
-def choose(prog, shapes=((32, 2), (64, 2), (128, 2), (128, 4))):
-    """(team size, nodes per lane) with the most useful FP64 work per SM:
-    resident warps (shared memory for the team's rows, value slots and, when
-    it fits, H; at most 16 warps), times the lane efficiency of the waves,
-    times a latency-hiding factor for the independent chains per SM
-    sub-partition (warps / 4 x nodes per lane, saturating at 4: measured,
-    two warps of two nodes each per sub-partition already cover the FP64
-    latency, and four nodes per lane then only cost lane efficiency)."""
-    best, best_cp = -1.0, None
-    for T, ilp in shapes:
-        cp = build(prog, T, ilp)
-        vals = cp.nslot * 8 + ROWS_BYTES
-        with_h = vals + cp.nh * 8
-        per_team = with_h if with_h <= 227 * 1024 else vals
-        if per_team > 227 * 1024:
-            continue
-        # registers: 4 nodes per lane need ~230 registers (256 threads per SM)
-        max_threads = 256 if ilp == 4 else 512
-        teams = max(1, min(SMEM_PER_SM // (per_team + 1024), max_threads // T))
-        warps = min(teams * T // 32, max_threads // 32)
-        eff = 0.5 * (cp.eff1 + cp.eff2) * 0.2 + cp.eff1 * 0.8
-        chains = warps / 4.0 * ilp
-        score = warps * eff * min(1.0, chains / 4.0)
-        if score > best:
-            best, best_cp = score, cp
-    return best_cp
+def _score(cp, rows):
+    """Useful FP64 work per SM of a built shape: resident warps (shared
+    memory for the team's rows, value slots and, when it fits, H; at most
+    16 warps), times the lane efficiency of the waves, times a
+    latency-hiding factor for the independent chains per SM sub-partition
+    (warps / 4 x nodes per lane, saturating at 4: measured, two warps of two
+    nodes each per sub-partition already cover the FP64 latency, and four
+    nodes per lane then only cost lane efficiency).  None if it does not
+    fit."""
+    vals = cp.nslot * 8 + rows * ROW_BYTES
+    with_h = vals + cp.nh * 8
+    per_team = with_h if with_h <= 227 * 1024 else vals
+    if per_team > 227 * 1024:
+        return None
+    # registers: 4 nodes per lane need ~230 registers (256 threads per SM)
+    max_threads = 256 if cp.ilp == 4 else 512
+    teams = max(1, min(SMEM_PER_SM // (per_team + 1024), max_threads // cp.T))
+    warps = min(teams * cp.T // 32, max_threads // 32)
+    eff = 0.5 * (cp.eff1 + cp.eff2) * 0.2 + cp.eff1 * 0.8
+    chains = warps / 4.0 * cp.ilp
+    return warps * eff * min(1.0, chains / 4.0)
+
+
+WIDE_SHAPES = ((256, 2), (256, 4))
+
+
+def _teams_per_sm(cp, rows):
+    vals = cp.nslot * 8 + rows * ROW_BYTES
+    with_h = vals + cp.nh * 8
+    per_team = with_h if with_h <= 227 * 1024 else vals
+    return SMEM_PER_SM // (per_team + 1024)
+
+
+def choose_both(prog, shapes=SHAPES):
+    """(deep, shallow): the best (team size, nodes per lane) shape when a
+    team holds DEEP_ROWS coefficient rows, and when it holds SHALLOW_ROWS
+    (shallow contractions: fewer rows leave shared memory for more teams).
+    Classes whose 128-lane team is alone on an SM also try one 256-lane team
+    (eight warps on the same shared-memory live set)."""
+    built = [build(prog, T, ilp) for T, ilp in shapes]
+    if any(cp.T == 128 and _teams_per_sm(cp, DEEP_ROWS) <= 1 for cp in built):
+        built += [build(prog, T, ilp) for T, ilp in WIDE_SHAPES]
+    out = []
+    for rows in (DEEP_ROWS, SHALLOW_ROWS):
+        scored = [(sc, k) for k, cp in enumerate(built) for sc in [_score(cp, rows)] if sc is not None]
+        out.append(built[max(scored)[1]] if scored else None)
+    return tuple(out)
+
+
+def choose(prog, shapes=SHAPES):
+    """The best shape for deep contractions (see choose_both)."""
+    return choose_both(prog, shapes)[0]

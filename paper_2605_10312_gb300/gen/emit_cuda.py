@@ -26,15 +26,19 @@ TIERS = ("reg", "smem", "global")
 AX = "xyz"
 
 
-def kernel_name(ls, tier, opts=None):
+def kernel_name(ls, tier, opts=None, real="double"):
     base = "eri_{}{}{}{}_{}".format(*ls, tier)
     if opts is not None and opts.key() != ("prose", "dsa", "stepwise"):
         base += "_" + "_".join(opts.key())
+    if real == "float":
+        base += "_f32"
     return base
 
 
-def _coef_expr(sym):
+def _coef_expr(sym, real="double"):
     kind, k = sym
+    if real == "float":
+        return "f{}_{}".format(kind, k) if kind in ("PA", "QC", "WP", "WQ") else "{}_{}".format(kind, k)
     if kind == "PA":
         return "bp.PA[{}]".format(k)
     if kind == "QC":
@@ -46,11 +50,21 @@ def _coef_expr(sym):
     return "{}_{}".format(kind, k)
 
 
-def _coef_defs(syms):
+def _coef_defs(syms, real="double"):
     """Definitions of the integer-multiple coefficients a class uses:
     c1z_k = k/(2 zeta), c2z_k = -k rho/(2 zeta^2), likewise for eta, and
-    c3_k = k/(2(zeta+eta))."""
+    c3_k = k/(2(zeta+eta)).  In single precision every coefficient is
+    formed in FP64 and rounded once."""
     lines = []
+    if real == "float":
+        src = {"PA": "bp.PA[{}]", "QC": "kp.PA[{}]", "WP": "pq.WP[{}]", "WQ": "pq.WQ[{}]"}
+        for kind, k in sorted(s for s in syms if s[0] in src):
+            lines.append("    const float f{}_{} = (float){};".format(kind, k, src[kind].format(k)))
+        base = {"c1z": "bp.inv2z", "c1e": "kp.inv2z", "c2z": "(-bp.inv2z * pq.te)",
+                "c2e": "(-kp.inv2z * pq.tz)", "c3": "(0.5 * pq.s)"}
+        for kind, k in sorted(s for s in syms if s[0] in base):
+            lines.append("    const float {}_{} = (float)({}.0 * {});".format(kind, k, k, base[kind]))
+        return lines
     need = sorted(s for s in syms if s[0] in ("c1z", "c2z", "c1e", "c2e", "c3"))
     have = set()
 
@@ -75,23 +89,31 @@ def _coef_defs(syms):
     return lines
 
 
-def _fmt(c):
+def _fmt(c, real="double"):
     r = repr(float(c))
-    return r if ("e" in r or "." in r) else r + ".0"
+    r = r if ("e" in r or "." in r) else r + ".0"
+    return r + "f" if real == "float" else r
 
 
-def emit_class(prog, tier="reg", threads=128):
-    """CUDA source of one class kernel."""
+def emit_class(prog, tier="reg", threads=128, real="double"):
+    """CUDA source of one class kernel.  real="float" (register tier only)
+    gives the reduced-precision form: pair and quartet set-up, the Boys
+    function and the output store in FP64, the recurrences, the
+    contraction sums, HRR and the transform in FP32."""
+    assert real == "double" or tier == "reg"
+    R = real
+    FMA = "fmaf" if real == "float" else "fma"
+    ZERO = "0.0f" if real == "float" else "0.0"
     g = prog.g
     la, lb, lc, ld = prog.ls
     L = prog.L
-    name = kernel_name(prog.ls, tier, prog.opts)
+    name = kernel_name(prog.ls, tier, prog.opts, real)
     nh = prog.nh
     out = []
     w = out.append
     c = prog.counts()
-    w("// class ({} {} | {} {}), tier {}, axis rule {}, schedule {}, sph {}".format(
-        la, lb, lc, ld, tier, *prog.opts.key()))
+    w("// class ({} {} | {} {}), tier {}, axis rule {}, schedule {}, sph {}, recurrences in {}".format(
+        la, lb, lc, ld, tier, *prog.opts.key(), R))
     w("// VRR nodes {}  PeakLive {}  slots {}  accumulators {}  outputs {}".format(
         c["vrr_nodes"], c["peak_live"], c["nslot"], c["nh"], c["nout"]))
     w("// flops per primitive quartet {}  Phase-2 flops {}".format(c["per_prim_flops"], c["p2_flops"]))
@@ -123,7 +145,7 @@ def emit_class(prog, tier="reg", threads=128):
         hname = lambda i: "HV({})".format(i)
     else:
         for i0 in range(0, nh, 16):
-            w("  double " + ", ".join("h{} = 0.0".format(i) for i in range(i0, min(nh, i0 + 16))) + ";")
+            w("  {} ".format(R) + ", ".join("h{} = {}".format(i, ZERO) for i in range(i0, min(nh, i0 + 16))) + ";")
         hname = lambda i: "h{}".format(i)
     w("  const int kk = ket.nprim;")
     w("  const int nk = valid ? bra.nprim : 0;")
@@ -137,7 +159,11 @@ def emit_class(prog, tier="reg", threads=128):
     w("    eri_prim_quartet(bp, kp, pq);")
     w("    double F[{}];".format(L + 1))
     w("    eri_boys<{}>(pq.T, F, a.boys_tab);".format(L))
-    for ln in _coef_defs(prog.coef_syms):
+    if real == "float":
+        used_m = sorted(set(g.keys[v][2] for v in prog.order if not g.terms[v]))
+        for m in used_m:
+            w("    const float fF{0} = (float)(pq.pref * F[{0}]);".format(m))
+    for ln in _coef_defs(prog.coef_syms, real):
         w(ln)
     slot = prog.slot
     consumed = set(p for ts in g.terms for _, p in ts)
@@ -149,15 +175,21 @@ def emit_class(prog, tier="reg", threads=128):
         ts = g.terms[v]
         tgt = g.target.get(v)
         if tier == "reg":
-            ops = [(_coef_expr(cs), loc(p)) for cs, p in ts]
+            ops = [(_coef_expr(cs, real), loc(p)) for cs, p in ts]
         else:
             ops = [(_coef_expr(cs), "r{}".format(k)) for k, (cs, p) in enumerate(ts)]
         if not ts:
-            ops = [("pq.pref", "F[{}]".format(g.keys[v][2]))]
+            if real == "float":
+                ops = [(None, "fF{}".format(g.keys[v][2]))]
+            else:
+                ops = [("pq.pref", "F[{}]".format(g.keys[v][2]))]
         fold = tgt is not None and v not in consumed and tier != "global"
         expr = hname(tgt) if fold else None
         for cexp, pv_ in ops:
-            expr = "{} * {}".format(cexp, pv_) if expr is None else "fma({}, {}, {})".format(cexp, pv_, expr)
+            if cexp is None:
+                expr = pv_ if expr is None else "{} + {}".format(expr, pv_)
+            else:
+                expr = "{} * {}".format(cexp, pv_) if expr is None else "{}({}, {}, {})".format(FMA, cexp, pv_, expr)
         loads = ""
         if tier != "reg" and ts:
             loads = " ".join("const double r{} = {};".format(k, loc(p)) for k, (cs, p) in enumerate(ts)) + " "
@@ -168,9 +200,9 @@ def emit_class(prog, tier="reg", threads=128):
             if v in consumed:
                 line += " {} = x{};".format(loc(v), v) if tier != "reg" else ""
                 if tier == "reg":
-                    line = "{}const double v{} = {}; {} += v{};".format(loads, v, expr, hname(tgt), v)
+                    line = "{}const {} v{} = {}; {} += v{};".format(loads, R, v, expr, hname(tgt), v)
         else:
-            line = "{}{}{} = {};".format(loads, "const double " if tier == "reg" else "", loc(v), expr)
+            line = "{}{}{} = {};".format(loads, "const {} ".format(R) if tier == "reg" else "", loc(v), expr)
         w("    " + ("{ " + line + " }" if tier != "reg" else line))
     w("  }")
     if tier != "global":
@@ -193,8 +225,8 @@ def emit_class(prog, tier="reg", threads=128):
             w("      const bool up = (lane & off) != 0;")
             for i in range(half):
                 lo, hi = vec[i], vec[half + i]
-                w("      {{ const double snd = up ? {0} : {1}; const double kp = up ? {1} : {0}; "
-                  "{0} = kp + __shfl_xor_sync(m, snd, off); }}".format(lo, hi))
+                w("      {{ const {2} snd = up ? {0} : {1}; const {2} kp = up ? {1} : {0}; "
+                  "{0} = kp + __shfl_xor_sync(m, snd, off); }}".format(lo, hi, R))
             if n % 2:
                 x = vec[n - 1]
                 w("      {0} += __shfl_xor_sync(m, {0}, off);".format(x))
@@ -212,8 +244,8 @@ def emit_class(prog, tier="reg", threads=128):
             w("      const bool up = (lane & o2) != 0;")
             for i in range(half):
                 lo, hi = v[i], v[half + i]
-                w("      {{ const double mine = {0}; const double oth = __shfl_xor_sync(m, mine, o2); "
-                  "{0} = up ? oth : mine; {1} = up ? mine : oth; }}".format(lo, hi))
+                w("      {{ const {2} mine = {0}; const {2} oth = __shfl_xor_sync(m, mine, o2); "
+                  "{0} = up ? oth : mine; {1} = up ? mine : oth; }}".format(lo, hi, R))
             w("    }")
         w("  }")
     w("  if (!valid || r != 0) return;")
@@ -223,17 +255,23 @@ def emit_class(prog, tier="reg", threads=128):
     def pv(i):
         return hname(i) if i < nh else "p{}".format(i)
 
+    if real == "float":
+        for i in range(3):
+            w("  const float fAB{0} = (float)bra.AB[{0}], fCD{0} = (float)ket.AB[{0}];".format(i))
     for op in p2.ops:
         if op[0] == "hrr":
             _, d, hi, (sym, i), lo = op
-            src = "bra.AB[{}]".format(i) if sym == "AB" else "ket.AB[{}]".format(i)
-            w("  const double p{} = fma({}, {}, {});".format(d, src, pv(lo), pv(hi)))
+            if real == "float":
+                src = "fAB{}".format(i) if sym == "AB" else "fCD{}".format(i)
+            else:
+                src = "bra.AB[{}]".format(i) if sym == "AB" else "ket.AB[{}]".format(i)
+            w("  const {} p{} = {}({}, {}, {});".format(R, d, FMA, src, pv(lo), pv(hi)))
         else:
             _, d, terms = op
-            expr = "{} * {}".format(_fmt(terms[0][0]), pv(terms[0][1]))
+            expr = "{} * {}".format(_fmt(terms[0][0], real), pv(terms[0][1]))
             for cc, s in terms[1:]:
-                expr = "fma({}, {}, {})".format(_fmt(cc), pv(s), expr)
-            w("  const double p{} = {};".format(d, expr))
+                expr = "{}({}, {}, {})".format(FMA, _fmt(cc, real), pv(s), expr)
+            w("  const {} p{} = {};".format(R, d, expr))
     w("  double* const o = a.out + qr.out_off;")
     dims = p2.out_dims
     for k, vid in enumerate(p2.outputs):
@@ -243,7 +281,7 @@ def emit_class(prog, tier="reg", threads=128):
             if ii:
                 terms.append("{}*qr.st[{}]".format(int(ii), axis))
         off = " + ".join(terms) if terms else "0"
-        w("  eri_st(o + {}, {}, acc);".format(off, pv(vid)))
+        w("  eri_st(o + {}, {}{}, acc);".format(off, "(double)" if real == "float" else "", pv(vid)))
     if tier in ("smem", "global"):
         w("#undef SV")
     if tier == "global":

@@ -32,3 +32,14 @@ def screened(basis, threshold=1e-10, stream=None):
     """Unique quartets of the basis surviving Schwarz screening, [n, 4]."""
     pairs, q = pair_bounds(basis, stream=stream)
     return synth.screened_quartets(q, pairs, threshold)
+
+
+def quartet_bounds(pair_q, quartets):
+    """Schwarz bound Q_ab Q_cd of each quartet, given the per-pair factors of
+    synth.shell_pairs order (pair (a, b), a >= b, at a (a + 1) / 2 + b)."""
+    q = np.asarray(quartets, dtype=np.int64).reshape(-1, 4)
+
+    def idx(a, b):
+        hi, lo = np.maximum(a, b), np.minimum(a, b)
+        return hi * (hi + 1) // 2 + lo
+    return pair_q[idx(q[:, 0], q[:, 1])] * pair_q[idx(q[:, 2], q[:, 3])]

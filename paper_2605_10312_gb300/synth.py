@@ -321,3 +321,57 @@ def screened_quartets(pair_bound: np.ndarray, pairs: np.ndarray, threshold: floa
     if not out:
         return np.zeros((0, 4), dtype=np.int32)
     return np.ascontiguousarray(np.concatenate(out).astype(np.int32))
+
+
+def count_screened(pair_bound: np.ndarray, threshold: float) -> int:
+    """Number of unique quartets (pair P >= pair Q) with Q_P Q_Q >= threshold."""
+    qs = np.sort(np.asarray(pair_bound, dtype=np.float64))[::-1]
+    idx = np.arange(qs.size)
+    with np.errstate(divide="ignore"):
+        lim = np.where(qs > 0, threshold / np.where(qs > 0, qs, 1.0), np.inf if threshold > 0 else -np.inf)
+    # partners k <= i with qs[k] >= lim[i]: a prefix of the descending order
+    nk = np.searchsorted(-qs, -lim, side="right")
+    return int(np.minimum(nk, idx + 1).sum())
+
+
+def sample_screened_quartets(pair_bound: np.ndarray, pairs: np.ndarray, threshold: float, n: int,
+                             seed: int = 0, max_draws: int = 1 << 34) -> np.ndarray:
+    """A uniform random sample (without replacement, seeded) of n unique
+    quartets (pair P >= pair Q) whose Schwarz bound Q_P Q_Q >= threshold, for
+    screened lists too large to enumerate; fewer than n if fewer survive
+    within max_draws draws.  [m, 4] int32 in draw order."""
+    rng = np.random.default_rng(seed)
+    npair = pair_bound.shape[0]
+    ntri = npair * (npair + 1) // 2
+    if n >= count_screened(pair_bound, threshold):
+        full = screened_quartets(pair_bound, pairs, threshold)
+        return np.ascontiguousarray(full[rng.permutation(full.shape[0])])
+    seen = set()
+    out = []
+    draws = 0
+    have = 0
+    while have < n and draws < max_draws and len(seen) < ntri:
+        m = int(min(max(4 * (n - have), 1 << 16), 1 << 24))
+        t = rng.integers(0, ntri, size=m, dtype=np.int64)
+        draws += m
+        # triangle index -> (i, j), i >= j
+        i = ((np.sqrt(8.0 * t + 1.0) - 1.0) // 2).astype(np.int64)
+        i -= (i * (i + 1) // 2 > t)
+        i += ((i + 1) * (i + 2) // 2 <= t)
+        j = t - i * (i + 1) // 2
+        keep = pair_bound[i] * pair_bound[j] >= threshold
+        t, i, j = t[keep], i[keep], j[keep]
+        _, first = np.unique(t, return_index=True)
+        for k in np.sort(first):
+            tk = int(t[k])
+            if tk in seen:
+                continue
+            seen.add(tk)
+            out.append((i[k], j[k]))
+            have += 1
+            if have >= n:
+                break
+    if not out:
+        return np.zeros((0, 4), dtype=np.int32)
+    ij = np.array(out, dtype=np.int64)
+    return np.ascontiguousarray(np.concatenate([pairs[ij[:, 0]], pairs[ij[:, 1]]], axis=1).astype(np.int32))

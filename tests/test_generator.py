@@ -163,3 +163,15 @@ def test_wave_schedule_respects_dependencies_and_width():
         if s in owners:
             assert last[owners[s]] < wave_of[v]
         owners[s] = v
+
+
+def test_coop_shallow_shape_prefers_narrow_teams():
+    """With 12 coefficient rows instead of 32 a team needs less shared
+    memory, so a mid-size class fits 16 one-warp teams per SM and takes the
+    narrower (better-filled) waves; both choices are valid programs."""
+    prog = program.make(1, 2, 1, 2)
+    deep, shallow = coop.choose_both(prog)
+    assert deep is not None and shallow is not None
+    assert shallow.T < deep.T
+    assert coop._score(shallow, coop.SHALLOW_ROWS) >= coop._score(deep, coop.SHALLOW_ROWS)
+    assert coop._score(deep, coop.DEEP_ROWS) >= coop._score(shallow, coop.DEEP_ROWS)

@@ -44,3 +44,35 @@ def test_water_cluster_shapes():
     assert synth.shell_pairs(b.nshell).shape[0] == 28920
     t = synth.water_cluster(2, seed=3, layout="tz")
     assert t.shell_l.max() == 3
+
+
+def test_sample_screened_quartets():
+    rng = np.random.default_rng(3)
+    pairs = synth.shell_pairs(30)
+    q = 10.0 ** rng.uniform(-8, 0, pairs.shape[0])
+    thr = 1e-6
+    full = synth.screened_quartets(q, pairs, thr)
+    index = {tuple(p): k for k, p in enumerate(pairs.tolist())}
+
+    def key(row):
+        a, b = index[tuple(row[:2])], index[tuple(row[2:])]
+        return (max(a, b), min(a, b))
+    want = {key(r) for r in full.tolist()}
+    s = synth.sample_screened_quartets(q, pairs, thr, 500, seed=1)
+    got = [key(r) for r in s.tolist()]
+    assert len(got) == 500 and len(set(got)) == 500
+    assert set(got) <= want
+    # asking for more than survive returns every survivor once
+    s_all = synth.sample_screened_quartets(q, pairs, thr, len(want) + 10, seed=2)
+    assert {key(r) for r in s_all.tolist()} == want and s_all.shape[0] == len(want)
+    # same seed, same sample
+    assert np.array_equal(s, synth.sample_screened_quartets(q, pairs, thr, 500, seed=1))
+
+
+@pytest.mark.parametrize("thr", [0.0, 1e-9, 1e-4, 1.0])
+def test_count_screened(thr):
+    rng = np.random.default_rng(5)
+    pairs = synth.shell_pairs(20)
+    q = 10.0 ** rng.uniform(-8, 0.3, pairs.shape[0])
+    q[:4] = 0.0
+    assert synth.count_screened(q, thr) == synth.screened_quartets(q, pairs, thr).shape[0]
