@@ -374,12 +374,15 @@ def _traffic_for(rec):
     except (OSError, ValueError):
         return None
     import hashlib
-    h = hashlib.sha256()
-    for f in ("eri_exec.cu", "eri_common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2605_10312_gb300", "csrc", f), "rb").read())
+    from paper_2605_10312_gb300 import eri
     key = "".join("spdfg"[x] for x in rec["cls"]) if rec["cls"][0] >= 0 else "setup"
     ent = d.get(key)
-    if not ent or ent.get("source_sha256") != h.hexdigest():
+    if not ent or ent.get("tier") != eri.TIERS_INV.get(rec["tier"]):
+        return None
+    h = hashlib.sha256()
+    for f in ent.get("source_files", []):
+        h.update(open(os.path.join(ROOT, "paper_2605_10312_gb300", "csrc", f), "rb").read())
+    if ent.get("source_sha256") != h.hexdigest():
         return None
     return ent["bytes_per_quartet"] * rec["quartets"]
 
