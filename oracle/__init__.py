@@ -18,6 +18,12 @@ Parity status of each function (what pins it; the pins live in ``tests/``):
                 for l <= 1 (and spot d cases), 8-fold permutation symmetry,
                 rotational and translational invariance, Schwarz inequality,
                 long-double adjudication.
+  full_tensor, jk
+             -- pinned: on s-only bases every (ij|kl) and hence J and K are
+                given by the electrostatics of Gaussian charge clouds (closed
+                form, independent of this package); J, K symmetric for a
+                symmetric density; Coulomb and exchange energies
+                tr(D J) >= 0 and tr(D K) >= 0 for a positive semidefinite D.
 """
 from __future__ import annotations
 
@@ -132,3 +138,37 @@ def eri(basis, quartets, cart: bool = False, nthreads: int = 1, long_double: boo
     if rc != 0:
         raise ValueError("oracle: invalid basis or quartet list")
     return out, off
+
+
+def basis_function_offsets(basis, cart: bool = False) -> np.ndarray:
+    """First basis function of each shell (shells in order), and the total:
+    [nshell + 1]."""
+    n = np.array([ncart(l) if cart else nsph(l) for l in basis.shell_l], dtype=np.int64)
+    return np.concatenate([[0], np.cumsum(n)])
+
+
+def full_tensor(basis, cart: bool = False, nthreads: int = 1) -> np.ndarray:
+    """The full ERI tensor (ij|kl) over the basis functions, [nbf]*4, from
+    every ordered shell quartet (no symmetry used).  Small bases only."""
+    ns = int(basis.shell_l.shape[0])
+    idx = np.indices((ns, ns, ns, ns)).reshape(4, -1).T.astype(np.int32)
+    v, off = eri(basis, idx, cart=cart, nthreads=nthreads)
+    bf = basis_function_offsets(basis, cart)
+    nbf = int(bf[-1])
+    out = np.zeros((nbf, nbf, nbf, nbf))
+    for q, (a, b, c, d) in enumerate(idx.tolist()):
+        blk = v[off[q]:off[q + 1]].reshape(bf[a + 1] - bf[a], bf[b + 1] - bf[b], bf[c + 1] - bf[c], bf[d + 1] - bf[d])
+        out[bf[a]:bf[a + 1], bf[b]:bf[b + 1], bf[c]:bf[c + 1], bf[d]:bf[d + 1]] = blk
+    return out
+
+
+def jk(basis, density: np.ndarray, cart: bool = False, nthreads: int = 1):
+    """Coulomb and exchange matrices of a density D (FusionRCG Alg. 2, the
+    digestion of the integrals into the Fock build):
+        J_ij = sum_kl (ij|kl) D_kl,     K_ij = sum_kl (ik|jl) D_kl,
+    written out over the full tensor."""
+    g = full_tensor(basis, cart=cart, nthreads=nthreads)
+    D = np.asarray(density, dtype=np.float64)
+    J = np.einsum("ijkl,kl->ij", g, D)
+    K = np.einsum("ikjl,kl->ij", g, D)
+    return J, K
