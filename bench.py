@@ -474,7 +474,7 @@ def run_water(args):
         if args.autotune:
             tuned = tune.autotune(basis, quartets, sample=1024)
         t1 = time.perf_counter()
-        plan = eri.Plan(basis, quartets)
+        plan = eri.Plan(basis, quartets, digest=args.jk)
         t_plan = time.perf_counter() - t1
         out = torch.empty(max(1, plan.output_count), dtype=torch.float64, device="cuda")
         plan.set_timing(True)
@@ -499,6 +499,7 @@ def run_water(args):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
+    jk = run_water_jk(args, basis, plan, out, stream) if args.jk else None
     st = plan.stats()
     line = {"workload": "water cluster: {} waters ({} atoms), {} layout, Schwarz {:g}".format(
                 args.waters, 3 * args.waters, args.layout, args.threshold),
@@ -509,13 +510,61 @@ def run_water(args):
             "value": quartets.shape[0] / (ms * 1e-3), "unit": "quartets/s",
             "fp64_tflops": st["flops"] / (ms * 1e-3) / 1e12,
             "fp64_frac_of_peak": st["flops"] / (ms * 1e-3) / 1e12 / fp64_peak_tflops(),
-            "launches_per_step": st["launches"] + 1, "graph": True,
+            "launches_per_step": st["launches"] + 1, "graph": True, "jk": jk,
             "autotuned": None if tuned is None else {"".join(map(str, c)): v["tier"] for c, v in tuned.items()},
             "per_class": {k: {"parts": v["quartet_parts"], "ms": v["ms"], "tier": v["tier"],
                               "fp64_frac": v["flops"] / max(1e-9, v["ms"] * 1e-3) / 1e12 / fp64_peak_tflops()}
                           for k, v in sorted(per_class.items(), key=lambda kv: -kv[1]["ms"])}}
     print(json.dumps(line))
     return 0
+
+
+def run_water_jk(args, basis, plan, out, stream):
+    """Coulomb and exchange matrices of a random positive semidefinite
+    density from the screened list: per step the ERI graph replay, J and K
+    zeroed, and the digestion kernel; the digestion kernel's HBM roofline
+    counts one read of every block plus 24 B of quartet data per quartet."""
+    import torch
+    nbf = int(sum(2 * l + 1 for l in basis.shell_l))
+    rng = np.random.default_rng(11)
+    C = rng.standard_normal((nbf, nbf // 4))
+    D = torch.from_numpy(C @ C.T / nbf).cuda()
+    J = torch.zeros_like(D)
+    K = torch.zeros_like(D)
+    step_ms, dig_ms = [], []
+    with torch.cuda.stream(stream):
+        for it in range(args.warmup + args.steps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            plan.replay(stream)
+            J.zero_()
+            K.zero_()
+            e1.record(stream)
+            plan.digest_jk(out, D, J, K, stream)
+            e2.record(stream)
+            e2.synchronize()
+            if it >= args.warmup:
+                step_ms.append(e0.elapsed_time(e2))
+                dig_ms.append(e1.elapsed_time(e2))
+    nq = plan.nq
+    nbytes = 8.0 * plan.output_count + 24.0 * nq
+    dig = statistics.mean(dig_ms)
+    peak = hbm_peak_gbs()
+    return {"nbf": nbf, "ms_per_step": statistics.mean(step_ms), "digest_ms": dig,
+            "value": nq / (statistics.mean(step_ms) * 1e-3), "unit": "quartets/s (ERI + J/K digestion)",
+            "digest_roofline": {"bound": "hbm", "achieved": nbytes / (dig * 1e-3) / 1e9, "peak": peak,
+                                "unit": "GB/s", "frac": nbytes / (dig * 1e-3) / 1e9 / peak,
+                                "algorithmic_bytes": nbytes},
+            "energies": {"coulomb": float(torch.sum(D * J).item()), "exchange": float(torch.sum(D * K).item())}}
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s (MEASURED_PEAKS.json),
+    else the recipe's fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
 
 
 def _class_labels(basis, quartets):
@@ -609,6 +658,49 @@ def run_water_mixed(args):
     return 0
 
 
+def run_serve(args):
+    """Serving loop with continuous batching: a pool of seeded water clusters
+    (dz layout, 4-66 waters) registered on the device, requests of a seeded
+    slice of a molecule's Schwarz-screened quartet list (log-uniform in
+    [1e3, 1e6] quartets), mixed FP32/FP64 policy.  Phases: a burst (all
+    requests at t = 0: the capacity), Poisson arrivals at --rate, at 70% of
+    the capacity and at 150% of it."""
+    import torch
+    from paper_2605_10312_gb300 import eri, serve
+    torch.cuda.set_device(0)
+    eri.library()
+    rng = np.random.default_rng(5)
+    planners = max(1, min(8, (os.cpu_count() or 2) - 1))
+    srv = serve.Server(budget_bytes=args.serve_budget_gb << 30, slots=args.slots, planners=planners,
+                       fp32_below=args.fp32_below if args.fp32_below is not None else 1e-6, timeout_s=30.0)
+    t0 = time.perf_counter()
+    pools = {}
+    sizes = sorted(int(x) for x in rng.integers(4, 67, size=args.molecules))
+    for k, nw in enumerate(sizes):
+        mol = srv.register(k, synth.water_cluster(nw, seed=500 + k, layout="dz"))
+        pools[k] = serve.screened_pool(mol, args.threshold, 2_000_000, seed=k)
+    setup_s = time.perf_counter() - t0
+    # warm-up: compile-free, but first plans of each class upload programs
+    srv.serve(serve.poisson_requests(pools, 1.0, 8, seed=99, burst=True))
+    phases = {}
+    burst = serve.poisson_requests(pools, 1.0, args.requests, seed=1, burst=True)
+    phases["burst"] = serve.summary(srv.serve(burst), offered_span=0.0)
+    cap = phases["burst"]["served_requests_per_s"]
+    for name, rate, seed in (("rate_{:g}".format(args.rate), args.rate, 2), ("capacity_70pct", 0.7 * cap, 3),
+                             ("capacity_150pct", 1.5 * cap, 4)):
+        reqs = serve.poisson_requests(pools, rate, args.requests, seed=seed)
+        phases[name] = dict(serve.summary(srv.serve(reqs)), rate=rate)
+    srv.close()
+    line = {"workload": "serving: Poisson ERI requests over {} water clusters ({} waters), dz layout, "
+                        "Schwarz {:g}, requests of 1e3-1e6 quartets, FP32 below {:g}".format(
+                            len(sizes), sizes, args.threshold, srv.fp32_below),
+            "slots": args.slots, "planners": planners, "budget_gb": args.serve_budget_gb,
+            "requests_per_phase": args.requests, "setup_s": setup_s, "capacity_requests_per_s": cap,
+            "phases": phases}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -622,11 +714,17 @@ def main():
     ap.add_argument("--classes", default="", help="comma-separated subset, e.g. gggg (profiling runs)")
     ap.add_argument("--scale", type=float, default=1.0, help="multiply the quartet counts (profiling runs)")
     ap.add_argument("--ablation", action="store_true", help="axis / DSA / spherical / tier ablations instead")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "water"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "water", "serve"])
+    ap.add_argument("--rate", type=float, default=50.0, help="serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests per phase")
+    ap.add_argument("--molecules", type=int, default=8, help="serve: molecules in the pool")
+    ap.add_argument("--slots", type=int, default=8, help="serve: concurrent requests (streams)")
+    ap.add_argument("--serve-budget-gb", type=int, default=16, help="serve: device-memory budget")
     ap.add_argument("--waters", type=int, default=20)
     ap.add_argument("--layout", default="dz", choices=["dz", "tz"])
     ap.add_argument("--threshold", type=float, default=1e-10)
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--jk", action="store_true", help="water workload: also digest into J and K")
     ap.add_argument("--fp32-below", type=float, default=None,
                     help="water workload in mixed precision: FP32 recurrences below this Schwarz bound")
     ap.add_argument("--sample", type=int, default=0, help="water workload: sample this many screened quartets")
@@ -640,6 +738,8 @@ def main():
         return run_ablation(args)
     if args.workload == "water":
         return run_water_mixed(args) if args.fp32_below is not None else run_water(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

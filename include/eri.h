@@ -79,7 +79,9 @@ typedef struct {
   int32_t streams;      /* launches of one part round that may run concurrently, on up to this many streams
                            (the caller's plus streams the plan owns, joined back before eri_compute returns):
                            0 auto (4 for plans holding several classes, else 1), 1 serial, at most 8 */
-  int32_t reserved[2];
+  int32_t digest;       /* 1: also keep on the device what eri_digest_jk / eri_compute_jk need (the quartet list,
+                           16 B per quartet); 0: no */
+  int32_t reserved[1];
 } eri_opts;
 
 typedef struct eri_plan_s eri_plan_t;
@@ -108,6 +110,20 @@ int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis* basis, co
 int eri_plan_mixed(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
                    int64_t nq, const double* qbound, double fp32_below, const eri_opts* opts,
                    eri_plan_t** plan_out);
+
+/* Stream-ordered plan, for serving loops whose requests overlap on the
+ * device: like eri_plan_mixed (qbound may be NULL: all FP64), but every
+ * device buffer of the plan is allocated with cudaMallocAsync and filled
+ * with cudaMemcpyAsync on stream (a non-default cudaStream_t), and
+ * eri_plan_destroy frees them with cudaFreeAsync on the same stream instead
+ * of synchronising the device.  Run eri_compute for this plan on the same
+ * stream (or on one ordered after it) and destroy the plan only after the
+ * last eri_compute was enqueued.  Host inputs are copied before the call
+ * returns.  Errors: ERI_EINVAL for a NULL stream or bad bounds; otherwise as
+ * eri_plan. */
+int eri_plan_on_stream(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
+                       int64_t nq, const double* qbound, double fp32_below, const eri_opts* opts, void* stream,
+                       eri_plan_t** plan_out);
 
 /* Total number of doubles eri_compute writes (sum of block sizes). */
 int64_t eri_output_count(const eri_plan_t* plan);
@@ -154,6 +170,28 @@ int eri_plan_launch_info(const eri_plan_t* plan, int i, int32_t* info, double* f
  * ERI_EINVAL for a bad index. */
 int eri_plan_launch_precision(const eri_plan_t* plan, int i);
 
+/* Coulomb and exchange digestion (FusionRCG Alg. 2, the scatter of each
+ * quartet's integrals into the Fock build):
+ *     J_ij += sum_kl (ij|kl) D_kl,     K_ij += sum_kl (ik|jl) D_kl
+ * from the blocks eri_compute wrote for this plan (device memory, the plan's
+ * layout), for a symmetric density D (device, [nbf][nbf] row-major FP64).
+ * Each quartet of the plan stands for its orbit under the 8 index
+ * permutations: pass every such orbit once (e.g. a >= b, c >= d, pair (ab) >=
+ * pair (cd)); quartets that map onto themselves under some permutations are
+ * weighted accordingly.  J and K (device, [nbf][nbf], either may be NULL) are
+ * accumulated into, not overwritten, with FP64 atomic additions (so the last
+ * bits depend on the order of the additions).  nbf must equal the number of
+ * basis functions of the plan's shells (spherical, or Cartesian with
+ * sph_mode 2), shells numbered consecutively.  The plan must have been built
+ * with opts.digest = 1.  Asynchronous on stream.  Errors: ERI_EINVAL (NULL
+ * blocks or density, wrong nbf), ERI_ESTATE (plan without digest data). */
+int eri_digest_jk(eri_plan_t* plan, const double* blocks, const double* density, int32_t nbf, double* J,
+                  double* K, void* stream);
+
+/* eri_compute into a plan-owned device buffer followed by eri_digest_jk on
+ * the same stream: J and K of a density without handing the blocks out. */
+int eri_compute_jk(eri_plan_t* plan, const double* density, int32_t nbf, double* J, double* K, void* stream);
+
 /* Evaluate like eri_compute without allocating: for callers that may not
  * allocate device memory while they evaluate (stream capture without
  * graph-safe allocation, or a device-memory budget owned by another
@@ -198,7 +236,9 @@ int eri_set_class_tier(int la, int lb, int lc, int ld, int tier);
 int eri_plan_graph_capture(eri_plan_t* plan, double* out, void* stream);
 int eri_plan_graph_launch(eri_plan_t* plan, void* stream);
 
-/* Release the plan and its device memory (synchronises the device first). */
+/* Release the plan and its device memory.  A plan from eri_plan_on_stream
+ * frees its memory stream-ordered on its stream and returns at once; any
+ * other plan synchronises the device first. */
 int eri_plan_destroy(eri_plan_t* plan);
 
 /* Message for the calling thread's last error ("" if none). */

@@ -32,6 +32,19 @@ extern "C" cudaError_t eri_exec_launch(int shared, const EriLaunchArgs* a, const
                                        int block, size_t smem, cudaStream_t stream);
 extern "C" cudaError_t eri_exec_set_smem(size_t bytes);
 
+struct EriDigestArgs {
+  const int32_t* quartets;
+  const int64_t* offsets;
+  const int32_t* shell_bf;
+  const double* blocks;
+  const double* D;
+  double* J;
+  double* K;
+  int64_t nq;
+  int32_t nbf;
+};
+extern "C" cudaError_t eri_digest_launch(const EriDigestArgs* g, cudaStream_t stream);
+
 struct EriCoopArgs {
   const uint4* ph1;
   const uint32_t* steps1;
@@ -404,29 +417,62 @@ struct Bucket {
   bool shared_scratch = false;   // uses the plan's global scratch (runs on lane 0)
 };
 
+// Plans built by eri_plan_on_stream allocate stream-ordered on that stream
+// (set for the duration of the build on the building thread).
+thread_local cudaStream_t g_alloc_stream = nullptr;
+thread_local bool g_alloc_async = false;
+struct AllocStreamScope {
+  AllocStreamScope(cudaStream_t s, bool on) {
+    g_alloc_stream = s;
+    g_alloc_async = on;
+  }
+  ~AllocStreamScope() {
+    g_alloc_stream = nullptr;
+    g_alloc_async = false;
+  }
+};
+
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  cudaStream_t st = nullptr;  // stream-ordered buffer (plans built on a stream), else nullptr
+  bool async = false;
   ~DevBuf() { reset(); }
   void reset() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (async)
+        cudaFreeAsync(p, st);
+      else
+        cudaFree(p);
+    }
     p = nullptr;
     n = 0;
   }
   int alloc(size_t count, const char* what) {
     n = count;
+    async = g_alloc_async;
+    st = g_alloc_stream;
     if (count == 0) return ERI_OK;
-    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    const cudaError_t e = async ? cudaMallocAsync((void**)&p, count * sizeof(T), st)
+                                : cudaMalloc((void**)&p, count * sizeof(T));
+    if (e != cudaSuccess) {
       cudaGetLastError();
-      return fail(ERI_ENOMEM, std::string("cudaMalloc failed: ") + what);
+      p = nullptr;
+      return fail(ERI_ENOMEM, std::string("device allocation failed: ") + what);
     }
     return ERI_OK;
   }
   int upload(const std::vector<T>& v, const char* what) {
     int rc = alloc(v.size(), what);
     if (rc) return rc;
-    if (!v.empty()) CUDA_OR(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+    if (!v.empty()) {
+      // pageable source: the copy is staged before the call returns
+      if (async)
+        CUDA_OR(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st), what);
+      else
+        CUDA_OR(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+    }
     return ERI_OK;
   }
 };
@@ -455,9 +501,15 @@ struct eri_plan_s {
   double h2d_bytes = 0;
   bool zero_out = false;  // chunks reduce into their block: eri_compute zeroes the output first
   std::vector<int32_t> nab;          // (ab|ab) plans: components of ab per quartet (else empty)
-  DevBuf<int64_t> d_offsets;
+  DevBuf<int64_t> d_offsets;         // block offsets, for (ab|ab) and digest plans
+  DevBuf<int32_t> d_uq;              // digest plans: the caller's quartet list
+  DevBuf<int32_t> d_shell_bf;        // digest plans: first basis function of each shell, and the total
+  int32_t nbf = 0;
+  bool digest = false;
   DevBuf<int32_t> d_nab;
   cudaGraphExec_t graph_exec = nullptr;
+  bool stream_ordered = false;         // built by eri_plan_on_stream: memory is freed on alloc_stream
+  cudaStream_t alloc_stream = nullptr;
   int nlanes = 1;                      // streams one round's launches may use
   std::vector<cudaStream_t> lanes;     // lanes[k - 1] = stream of lane k >= 1 (plan-owned)
   cudaEvent_t fork_ev = nullptr;       // caller stream -> lanes
@@ -486,7 +538,7 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   if (opts_in) opts = *opts_in;
   if (opts.axis_rule < 0 || opts.axis_rule > 2 || opts.schedule < 0 || opts.schedule > 1 || opts.sph_mode < 0 ||
       opts.sph_mode > 2 || opts.tier < 0 || opts.tier > 4 || opts.orientation < 0 || opts.orientation > 2 ||
-      opts.streams < 0 || opts.streams > 8)
+      opts.streams < 0 || opts.streams > 8 || opts.digest < 0 || opts.digest > 1)
     return fail(ERI_EINVAL, "option out of range");
   if (nq < 0 || nshell < 0 || (nq > 0 && (!shells || !basis || !quartets)))
     return fail(ERI_EINVAL, "NULL or negative argument");
@@ -1016,11 +1068,23 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       diag = s4[0] == s4[2] && s4[1] == s4[3];
       nab[q] = nfun(shells[s4[0]].l, cart) * nfun(shells[s4[1]].l, cart);
     }
+    if (diag || opts.digest) {
+      std::vector<int64_t> offs(plan->offsets.begin(), plan->offsets.end() - 1);
+      if ((rc = plan->d_offsets.upload(offs, "offsets"))) return rc;
+    }
     if (diag) {
       plan->nab = nab;
-      std::vector<int64_t> offs(plan->offsets.begin(), plan->offsets.end() - 1);
-      if ((rc = plan->d_offsets.upload(offs, "offsets")) || (rc = plan->d_nab.upload(nab, "pair sizes"))) return rc;
+      if ((rc = plan->d_nab.upload(nab, "pair sizes"))) return rc;
     }
+  }
+  if (opts.digest) {
+    std::vector<int32_t> uq(quartets, quartets + 4 * nq);
+    std::vector<int32_t> bf(nshell + 1, 0);
+    for (int s = 0; s < nshell; ++s) bf[s + 1] = bf[s] + nfun(shells[s].l, cart);
+    if ((rc = plan->d_uq.upload(uq, "quartet list")) || (rc = plan->d_shell_bf.upload(bf, "shell offsets")))
+      return rc;
+    plan->nbf = bf[nshell];
+    plan->digest = true;
   }
   plan->h2d_bytes = (double)(dsh.size() * sizeof(DevShell) + 2 * ex.size() * sizeof(double) +
                              pin.size() * sizeof(DevPairIn) + plist.size() * sizeof(uint32_t) +
@@ -1036,6 +1100,26 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
 extern "C" int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
                         int64_t nq, const eri_opts* opts, eri_plan_t** plan_out) {
   return plan_impl(shells, nshell, basis, quartets, nq, nullptr, 0.0, opts, plan_out);
+}
+
+extern "C" int eri_plan_on_stream(const eri_shell* shells, int32_t nshell, const eri_basis* basis,
+                                  const int32_t* quartets, int64_t nq, const double* qbound, double fp32_below,
+                                  const eri_opts* opts, void* stream, eri_plan_t** plan_out) {
+  if (!stream) return fail(ERI_EINVAL, "stream-ordered plans need a non-default stream");
+  if (qbound)
+    for (int64_t q = 0; q < nq; ++q)
+      if (!(qbound[q] >= 0)) return fail(ERI_EINVAL, "negative or NaN Schwarz bound");
+  if (qbound && (!(fp32_below >= 0) || !std::isfinite(fp32_below))) return fail(ERI_EINVAL, "bad FP32 threshold");
+  int rc;
+  {
+    AllocStreamScope scope((cudaStream_t)stream, true);
+    rc = plan_impl(shells, nshell, basis, quartets, nq, qbound, fp32_below, opts, plan_out);
+  }
+  if (rc == ERI_OK && *plan_out) {
+    (*plan_out)->stream_ordered = true;
+    (*plan_out)->alloc_stream = (cudaStream_t)stream;
+  }
+  return rc;
 }
 
 extern "C" int eri_plan_mixed(const eri_shell* shells, int32_t nshell, const eri_basis* basis,
@@ -1168,6 +1252,42 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
   return join_round();
 }
 
+extern "C" int eri_digest_jk(eri_plan_t* plan, const double* blocks, const double* density, int32_t nbf, double* J,
+                             double* K, void* stream) {
+  if (!plan) return fail(ERI_EINVAL, "NULL plan");
+  if (plan->nq == 0) return ERI_OK;
+  if (!plan->digest) return fail(ERI_ESTATE, "plan built without opts.digest = 1");
+  if (!blocks || !density) return fail(ERI_EINVAL, "NULL blocks or density");
+  if (nbf != plan->nbf) return fail(ERI_EINVAL, "nbf does not match the plan's basis functions");
+  if (!J && !K) return ERI_OK;
+  EriDigestArgs g;
+  g.quartets = plan->d_uq.p;
+  g.offsets = plan->d_offsets.p;
+  g.shell_bf = plan->d_shell_bf.p;
+  g.blocks = blocks;
+  g.D = density;
+  g.J = J;
+  g.K = K;
+  g.nq = plan->nq;
+  g.nbf = nbf;
+  CUDA_OR(eri_digest_launch(&g, (cudaStream_t)stream), "digest launch");
+  return ERI_OK;
+}
+
+extern "C" int eri_compute_jk(eri_plan_t* plan, const double* density, int32_t nbf, double* J, double* K,
+                              void* stream) {
+  if (!plan) return fail(ERI_EINVAL, "NULL plan");
+  if (plan->nq == 0) return ERI_OK;
+  if (!plan->digest) return fail(ERI_ESTATE, "plan built without opts.digest = 1");
+  const size_t n = (size_t)plan->offsets.back();
+  if (plan->outbuf.n < n) {
+    plan->outbuf.reset();
+    if (int rc = plan->outbuf.alloc(n, "output buffer")) return rc;
+  }
+  if (int rc = eri_compute(plan, plan->outbuf.p, stream)) return rc;
+  return eri_digest_jk(plan, plan->outbuf.p, density, nbf, J, K, stream);
+}
+
 extern "C" int eri_plan_set_timing(eri_plan_t* plan, int enable) {
   if (!plan) return fail(ERI_EINVAL, "NULL plan");
   plan->timing = enable != 0;
@@ -1243,7 +1363,9 @@ extern "C" int eri_plan_launch_precision(const eri_plan_t* plan, int i) {
 
 extern "C" int eri_plan_destroy(eri_plan_t* plan) {
   if (!plan) return ERI_OK;
-  cudaDeviceSynchronize();
+  // a stream-ordered plan frees its memory on its stream, after the work
+  // already queued there; any other plan waits for the device first
+  if (!plan->stream_ordered) cudaDeviceSynchronize();
   delete plan;
   return ERI_OK;
 }

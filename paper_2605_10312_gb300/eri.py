@@ -42,7 +42,7 @@ class _Basis(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("axis_rule", ctypes.c_int32), ("schedule", ctypes.c_int32), ("sph_mode", ctypes.c_int32),
                 ("tier", ctypes.c_int32), ("orientation", ctypes.c_int32), ("streams", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("digest", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 _lib = None
@@ -62,6 +62,16 @@ def library(path: str = LIB):
         lib.eri_plan_mixed.argtypes = [ctypes.POINTER(_Shell), ctypes.c_int32, ctypes.POINTER(_Basis),
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                        ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_void_p)]
+        lib.eri_plan_on_stream.restype = ctypes.c_int
+        lib.eri_plan_on_stream.argtypes = [ctypes.POINTER(_Shell), ctypes.c_int32, ctypes.POINTER(_Basis),
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
+                                           ctypes.POINTER(_Opts), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+        lib.eri_digest_jk.restype = ctypes.c_int
+        lib.eri_digest_jk.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_compute_jk.restype = ctypes.c_int
+        lib.eri_compute_jk.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]
         lib.eri_plan_launch_precision.restype = ctypes.c_int
         lib.eri_plan_launch_precision.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.eri_output_count.restype = ctypes.c_int64
@@ -115,9 +125,11 @@ class Plan:
     """A device-resident plan for one quartet list (see eri_plan)."""
 
     def __init__(self, basis, quartets, axis_rule="prose", schedule="dsa", sph_mode="stepwise", tier="auto",
-                 orientation="split", qbound=None, fp32_below=None, streams=0):
+                 orientation="split", qbound=None, fp32_below=None, streams=0, stream=None, digest=False):
         """qbound/fp32_below: mixed precision (eri_plan_mixed) -- quartets whose
-        bound is below fp32_below run their recurrences in FP32."""
+        bound is below fp32_below run their recurrences in FP32.  stream: a
+        stream-ordered plan (eri_plan_on_stream) whose device memory lives and
+        dies on that stream; compute it on the same stream."""
         lib = library()
         q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
         ns = int(basis.shell_l.shape[0])
@@ -135,15 +147,22 @@ class Plan:
         b = _Basis(self._keep[0].ctypes.data, int(self._keep[0].shape[0]), self._keep[1].ctypes.data,
                    self._keep[2].ctypes.data, int(self._keep[1].shape[0]))
         o = _Opts(AXIS_RULES[axis_rule], SCHEDULES[schedule], SPH_MODES[sph_mode], TIERS[tier],
-                  ORIENTATIONS[orientation], int(streams))
+                  ORIENTATIONS[orientation], int(streams), 1 if digest else 0)
         h = ctypes.c_void_p()
-        if qbound is None:
-            _check(lib.eri_plan(sh, ns, ctypes.byref(b), q.ctypes.data, q.shape[0], ctypes.byref(o),
-                                ctypes.byref(h)))
-        else:
+        qb = None
+        if qbound is not None:
             qb = np.ascontiguousarray(np.asarray(qbound, dtype=np.float64).reshape(-1))
             if qb.shape[0] != q.shape[0]:
                 raise ValueError("qbound needs one entry per quartet")
+        if stream is not None:
+            _check(lib.eri_plan_on_stream(sh, ns, ctypes.byref(b), q.ctypes.data, q.shape[0],
+                                          None if qb is None else qb.ctypes.data,
+                                          float(fp32_below if fp32_below is not None else 0.0), ctypes.byref(o),
+                                          _stream_handle(stream), ctypes.byref(h)))
+        elif qbound is None:
+            _check(lib.eri_plan(sh, ns, ctypes.byref(b), q.ctypes.data, q.shape[0], ctypes.byref(o),
+                                ctypes.byref(h)))
+        else:
             _check(lib.eri_plan_mixed(sh, ns, ctypes.byref(b), q.ctypes.data, q.shape[0], qb.ctypes.data,
                                       float(fp32_below if fp32_below is not None else 0.0), ctypes.byref(o),
                                       ctypes.byref(h)))
@@ -229,6 +248,30 @@ class Plan:
 
     def replay(self, stream=None):
         _check(library().eri_plan_graph_launch(self._h, _stream_handle(stream)))
+
+    @staticmethod
+    def _square(t, n, name):
+        import torch
+        if t is None:
+            return None
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and tuple(t.shape) == (n, n)):
+            raise TypeError("{} must be a contiguous CUDA float64 tensor of shape ({n}, {n})".format(name, n=n))
+        return t.data_ptr()
+
+    def digest_jk(self, blocks, density, J=None, K=None, stream=None):
+        """Add the Coulomb and exchange matrices of ``density`` from this
+        plan's blocks into J and K (eri_digest_jk; plan built with
+        digest=True)."""
+        n = int(density.shape[0])
+        _check(library().eri_digest_jk(self._h, blocks.data_ptr(), self._square(density, n, "density"), n,
+                                       self._square(J, n, "J"), self._square(K, n, "K"), _stream_handle(stream)))
+
+    def compute_jk(self, density, J=None, K=None, stream=None):
+        """Evaluate and digest in one call (eri_compute_jk)."""
+        n = int(density.shape[0])
+        _check(library().eri_compute_jk(self._h, self._square(density, n, "density"), n, self._square(J, n, "J"),
+                                        self._square(K, n, "K"), _stream_handle(stream)))
 
     def compute_host(self, out, stream=None):
         """Compute and copy every block into ``out`` (a contiguous CPU float64

@@ -1,0 +1,266 @@
+"""Serving loop with continuous batching for ERI requests.
+
+A request is a batch of shell quartets of one registered molecule.  The
+server keeps each molecule's basis and Schwarz data resident (pair factors
+Q_ab computed once on the device at registration), and runs requests as they
+arrive:
+
+  * admission: a request enters when a slot (a CUDA stream) is free and its
+    device-memory footprint (output blocks, quartet records, pair data) fits
+    in the remaining budget; requests are admitted in arrival order;
+  * planning: a pool of host threads builds each admitted request's plan
+    (eri_plan_on_stream: stream-ordered device memory, so that retiring one
+    request never synchronises the device under the others); the native
+    planner releases the interpreter lock;
+  * execution: each plan runs on its slot's stream, so requests that arrive
+    while others are on the device overlap with them;
+  * completion: polled with CUDA events; a request that has not finished
+    within its timeout is reported with status "timeout" (the host stops
+    waiting for it; its memory is reclaimed when the device finishes);
+  * precision: quartets whose bound Q_ab Q_cd is below fp32_below run their
+    recurrences in FP32 (eri_plan_on_stream with the per-quartet bounds).
+
+Latency is measured from arrival to the completion of the request's work on
+the device (host polling granularity included).
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import dataclasses
+import time
+
+import numpy as np
+
+from . import eri, screen
+
+NSPH = np.array([1, 3, 5, 7, 9], dtype=np.int64)
+
+
+@dataclasses.dataclass
+class Molecule:
+    key: object
+    basis: object
+    pairs: np.ndarray     # [npair, 2] shell pairs (a >= b)
+    pair_q: np.ndarray    # Schwarz factor per pair (host copy)
+    pair_q_dev: object    # the same on the device
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    mol: object           # registered molecule key
+    quartets: np.ndarray  # [n, 4] shell indices
+    arrival: float        # seconds after the start of the run
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    status: str           # "ok", "timeout", "rejected"
+    quartets: int
+    arrival: float
+    admitted: float = float("nan")
+    launched: float = float("nan")
+    finished: float = float("nan")
+    fp32_parts: int = 0
+    output: object = None  # device tensor (keep_outputs=True)
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+
+class Server:
+    def __init__(self, budget_bytes=8 << 30, slots=8, planners=4, fp32_below=1e-6, timeout_s=10.0,
+                 keep_outputs=False, poll_s=50e-6):
+        import torch
+        self.torch = torch
+        self.budget = int(budget_bytes)
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.pool = cf.ThreadPoolExecutor(max_workers=planners)
+        self.fp32_below = fp32_below
+        self.timeout_s = timeout_s
+        self.keep_outputs = keep_outputs
+        self.poll_s = poll_s
+        self.molecules = {}
+
+    def close(self):
+        self.pool.shutdown(wait=True)
+
+    # -- molecules ----------------------------------------------------------
+    def register(self, key, basis):
+        """Keep a molecule resident: Schwarz factors of every shell pair,
+        computed on the device."""
+        pairs, q = screen.pair_bounds(basis)
+        mol = Molecule(key, basis, pairs, q, self.torch.from_numpy(q).to("cuda"))
+        self.molecules[key] = mol
+        return mol
+
+    # -- accounting ---------------------------------------------------------
+    @staticmethod
+    def footprint(mol, quartets):
+        """Device bytes a request holds while it runs: its output blocks, up
+        to four quartet-part records per quartet and its pair data."""
+        q = np.asarray(quartets)
+        l = mol.basis.shell_l[q]
+        out = int(np.prod(NSPH[l], axis=1).sum())
+        kp = mol.basis.shell_nprim[q]
+        pair_prims = int((kp[:, 0] * kp[:, 1] + kp[:, 2] * kp[:, 3]).sum())
+        return 8 * out + 4 * 32 * q.shape[0] + 80 * pair_prims + (1 << 16)
+
+    def bounds(self, mol, quartets):
+        return screen.quartet_bounds(mol.pair_q, quartets)
+
+    # -- one request --------------------------------------------------------
+    def _build(self, req, stream):
+        mol = self.molecules[req.mol]
+        if self.fp32_below is None:
+            return eri.Plan(mol.basis, req.quartets, stream=stream)
+        qb = self.bounds(mol, req.quartets)
+        return eri.Plan(mol.basis, req.quartets, qbound=qb, fp32_below=self.fp32_below, stream=stream)
+
+    def run_alone(self, req):
+        """The request evaluated by itself (plain plan, default stream
+        order): the reference for results in the mix."""
+        mol = self.molecules[req.mol]
+        if self.fp32_below is None:
+            p = eri.Plan(mol.basis, req.quartets)
+        else:
+            p = eri.Plan(mol.basis, req.quartets, qbound=self.bounds(mol, req.quartets),
+                         fp32_below=self.fp32_below)
+        out = self.torch.empty(max(1, p.output_count), dtype=self.torch.float64, device="cuda")
+        p.compute(out)
+        self.torch.cuda.synchronize()
+        p.close()
+        return out
+
+    # -- the loop -----------------------------------------------------------
+    def serve(self, requests):
+        """Run a request stream (arrival times relative to the start) to
+        completion; returns one Result per request, in request order."""
+        torch = self.torch
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        results = {r.rid: Result(r.rid, "ok", int(r.quartets.shape[0]), r.arrival) for r in requests}
+        queue = collections.deque()
+        free_slots = list(range(len(self.streams)))[::-1]
+        free_bytes = self.budget
+        planning = {}   # future -> (req, slot, nbytes)
+        running = []    # [req, slot, nbytes, plan, out, event, timed_out]
+        t0 = time.perf_counter()
+        while pending or queue or planning or running:
+            now = time.perf_counter() - t0
+            progressed = False
+            while pending and pending[0].arrival <= now:
+                queue.append(pending.popleft())
+                progressed = True
+            # admission in arrival order while the head fits
+            while queue and free_slots:
+                req = queue[0]
+                nbytes = self.footprint(self.molecules[req.mol], req.quartets)
+                if nbytes > self.budget:
+                    queue.popleft()
+                    res = results[req.rid]
+                    res.status, res.finished = "rejected", now
+                    progressed = True
+                    continue
+                if nbytes > free_bytes:
+                    break
+                queue.popleft()
+                slot = free_slots.pop()
+                free_bytes -= nbytes
+                results[req.rid].admitted = now
+                fut = self.pool.submit(self._build, req, self.streams[slot])
+                planning[fut] = (req, slot, nbytes)
+                progressed = True
+            # launch the plans that are built
+            for fut in [f for f in planning if f.done()]:
+                req, slot, nbytes = planning.pop(fut)
+                plan = fut.result()
+                st = self.streams[slot]
+                with torch.cuda.stream(st):
+                    out = torch.empty(max(1, plan.output_count), dtype=torch.float64, device="cuda")
+                    plan.compute(out, st)
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                res = results[req.rid]
+                res.launched = time.perf_counter() - t0
+                res.fp32_parts = plan.stats()["fp32_parts"]
+                running.append([req, slot, nbytes, plan, out, ev, False])
+                progressed = True
+            # completions (bounded waits)
+            still = []
+            for item in running:
+                req, slot, nbytes, plan, out, ev, timed_out = item
+                res = results[req.rid]
+                if ev.query():
+                    t = time.perf_counter() - t0
+                    if not timed_out:
+                        res.finished = t
+                    plan.close()   # stream-ordered: frees after the work on the slot's stream
+                    if self.keep_outputs and not timed_out:
+                        res.output = out
+                    del out
+                    free_slots.append(slot)
+                    free_bytes += nbytes
+                    progressed = True
+                    continue
+                if not timed_out and time.perf_counter() - t0 - res.arrival > self.timeout_s:
+                    res.status, res.finished = "timeout", time.perf_counter() - t0
+                    item[6] = True
+                still.append(item)
+            running = still
+            if not progressed:
+                time.sleep(self.poll_s)
+        return [results[r.rid] for r in requests]
+
+
+def summary(results, offered_span=None):
+    """p50/p99 latency (ms) and throughput of a finished run."""
+    ok = [r for r in results if r.status == "ok"]
+    lat = np.array([r.latency for r in ok]) * 1e3
+    first = min(r.arrival for r in results)
+    last = max(r.finished for r in results)
+    nq = sum(r.quartets for r in ok)
+    arrivals = np.array(sorted(r.arrival for r in results))
+    span = offered_span if offered_span is not None else (arrivals[-1] - arrivals[0] if len(arrivals) > 1 else 0.0)
+    return {
+        "requests": len(results), "ok": len(ok),
+        "timeout": sum(r.status == "timeout" for r in results),
+        "rejected": sum(r.status == "rejected" for r in results),
+        "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+        "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+        "mean_ms": float(lat.mean()) if len(lat) else None,
+        "served_quartets_per_s": nq / max(1e-9, last - first),
+        "served_requests_per_s": len(ok) / max(1e-9, last - first),
+        "offered_requests_per_s": (len(results) - 1) / span if span > 0 else None,
+        "offered_quartets_per_s": sum(r.quartets for r in results) / span if span > 0 else None,
+        "fp32_parts": int(sum(r.fp32_parts for r in ok)),
+    }
+
+
+def screened_pool(mol, threshold, n, seed):
+    """A seeded random sample of n quartets from the molecule's screened
+    list (all of them, shuffled, if fewer survive)."""
+    from . import synth
+    return synth.sample_screened_quartets(mol.pair_q, mol.pairs, threshold, n, seed=seed)
+
+
+def poisson_requests(pools, rate, nreq, nq_range=(1_000, 1_000_000), seed=0, burst=False):
+    """A request stream: exponential inter-arrival times of mean 1/rate (all
+    at t = 0 when burst), each request a random molecule of `pools` (key ->
+    screened quartet pool) and a seeded slice of its pool whose length is
+    log-uniform in nq_range."""
+    rng = np.random.default_rng(seed)
+    keys = sorted(pools)
+    t = 0.0
+    out = []
+    for rid in range(nreq):
+        if not burst and rid:
+            t += rng.exponential(1.0 / rate)
+        key = keys[int(rng.integers(len(keys)))]
+        pool = pools[key]
+        n = int(min(pool.shape[0], round(10 ** rng.uniform(np.log10(nq_range[0]), np.log10(nq_range[1])))))
+        start = int(rng.integers(0, pool.shape[0] - n + 1))
+        out.append(Request(rid, key, np.ascontiguousarray(pool[start:start + n]), 0.0 if burst else t))
+    return out

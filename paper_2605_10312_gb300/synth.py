@@ -335,43 +335,32 @@ def count_screened(pair_bound: np.ndarray, threshold: float) -> int:
 
 
 def sample_screened_quartets(pair_bound: np.ndarray, pairs: np.ndarray, threshold: float, n: int,
-                             seed: int = 0, max_draws: int = 1 << 34) -> np.ndarray:
+                             seed: int = 0) -> np.ndarray:
     """A uniform random sample (without replacement, seeded) of n unique
     quartets (pair P >= pair Q) whose Schwarz bound Q_P Q_Q >= threshold, for
-    screened lists too large to enumerate; fewer than n if fewer survive
-    within max_draws draws.  [m, 4] int32 in draw order."""
+    screened lists too large to enumerate (all survivors, shuffled, when
+    there are at most n).  [m, 4] int32 in random order."""
     rng = np.random.default_rng(seed)
     npair = pair_bound.shape[0]
     ntri = npair * (npair + 1) // 2
-    if n >= count_screened(pair_bound, threshold):
+    total = count_screened(pair_bound, threshold)
+    if n >= total:
         full = screened_quartets(pair_bound, pairs, threshold)
         return np.ascontiguousarray(full[rng.permutation(full.shape[0])])
-    seen = set()
-    out = []
-    draws = 0
-    have = 0
-    while have < n and draws < max_draws and len(seen) < ntri:
-        m = int(min(max(4 * (n - have), 1 << 16), 1 << 24))
+    frac = total / max(1, ntri)
+    got = np.zeros(0, dtype=np.int64)
+    while got.size < n:
+        m = int(min(max(1.3 * (n - got.size) / max(frac, 1e-12), 1 << 16), 1 << 26))
         t = rng.integers(0, ntri, size=m, dtype=np.int64)
-        draws += m
-        # triangle index -> (i, j), i >= j
-        i = ((np.sqrt(8.0 * t + 1.0) - 1.0) // 2).astype(np.int64)
+        i = ((np.sqrt(8.0 * t + 1.0) - 1.0) // 2).astype(np.int64)  # triangle index -> (i, j), i >= j
         i -= (i * (i + 1) // 2 > t)
         i += ((i + 1) * (i + 2) // 2 <= t)
         j = t - i * (i + 1) // 2
-        keep = pair_bound[i] * pair_bound[j] >= threshold
-        t, i, j = t[keep], i[keep], j[keep]
-        _, first = np.unique(t, return_index=True)
-        for k in np.sort(first):
-            tk = int(t[k])
-            if tk in seen:
-                continue
-            seen.add(tk)
-            out.append((i[k], j[k]))
-            have += 1
-            if have >= n:
-                break
-    if not out:
-        return np.zeros((0, 4), dtype=np.int32)
-    ij = np.array(out, dtype=np.int64)
-    return np.ascontiguousarray(np.concatenate([pairs[ij[:, 0]], pairs[ij[:, 1]]], axis=1).astype(np.int32))
+        t = t[pair_bound[i] * pair_bound[j] >= threshold]
+        got = np.unique(np.concatenate([got, t]))
+    t = rng.permutation(got)[:n]
+    i = ((np.sqrt(8.0 * t + 1.0) - 1.0) // 2).astype(np.int64)
+    i -= (i * (i + 1) // 2 > t)
+    i += ((i + 1) * (i + 2) // 2 <= t)
+    j = t - i * (i + 1) // 2
+    return np.ascontiguousarray(np.concatenate([pairs[i], pairs[j]], axis=1).astype(np.int32))
