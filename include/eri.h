@@ -85,6 +85,7 @@ typedef struct {
 } eri_opts;
 
 typedef struct eri_plan_s eri_plan_t;
+typedef struct eri_mol_s eri_mol_t;
 
 /* Build a plan for nq shell quartets (quartets = [nq][4] shell indices, any
  * order, host memory).  Validates every input, canonicalises each quartet to
@@ -124,6 +125,29 @@ int eri_plan_mixed(const eri_shell* shells, int32_t nshell, const eri_basis* bas
 int eri_plan_on_stream(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
                        int64_t nq, const double* qbound, double fp32_below, const eri_opts* opts, void* stream,
                        eri_plan_t** plan_out);
+
+/* A molecule kept on the device, for many plans over the same basis (a
+ * serving loop's registered molecules): validates and copies the shells and
+ * basis, orients every shell pair a >= b (opts->orientation; the other
+ * options are ignored) and computes all of their primitive-pair records
+ * once on the device.  Synchronous; the handle owns its device memory
+ * (about 72 B per primitive pair of the basis).  Errors as eri_plan. */
+int eri_mol_create(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const eri_opts* opts,
+                   eri_mol_t** mol_out);
+
+/* Release a molecule (synchronises the device first).  Plans built on it
+ * must have been destroyed before. */
+int eri_mol_destroy(eri_mol_t* mol);
+
+/* A plan over a molecule's shells (quartets index its shells): like
+ * eri_plan_mixed (qbound may be NULL: all FP64), but the plan uses the
+ * molecule's primitive-pair records instead of building its own, so its
+ * construction touches only its quartets and eri_compute launches no pair
+ * set-up.  stream: NULL for ordinary allocation, else stream-ordered as in
+ * eri_plan_on_stream.  opts->orientation must equal the molecule's.  The
+ * plan must not outlive the molecule.  Errors as eri_plan_mixed. */
+int eri_plan_on_mol(const eri_mol_t* mol, const int32_t* quartets, int64_t nq, const double* qbound,
+                    double fp32_below, const eri_opts* opts, void* stream, eri_plan_t** plan_out);
 
 /* Total number of doubles eri_compute writes (sum of block sizes). */
 int64_t eri_output_count(const eri_plan_t* plan);

@@ -33,6 +33,8 @@ extern "C" cudaError_t eri_exec_launch(int shared, const EriLaunchArgs* a, const
 extern "C" cudaError_t eri_exec_set_smem(size_t bytes);
 
 struct EriDigestArgs {
+  const int64_t* list;
+  int64_t nlist;
   const int32_t* quartets;
   const int64_t* offsets;
   const int32_t* shell_bf;
@@ -43,7 +45,9 @@ struct EriDigestArgs {
   int64_t nq;
   int32_t nbf;
 };
-extern "C" cudaError_t eri_digest_launch(const EriDigestArgs* g, cudaStream_t stream);
+extern "C" cudaError_t eri_digest_launch(const EriDigestArgs* g, int small, cudaStream_t stream);
+// blocks of up to this many elements are digested by one thread each
+static const int64_t kSmallBlock = 128;
 
 struct EriCoopArgs {
   const uint4* ph1;
@@ -330,6 +334,86 @@ struct DevPairIn {
   int32_t pad;
 };
 
+// An oriented (partial) shell pair of a quartet: the pair record `pair`
+// recurs on shell `center`, with `nprim` primitive pairs.
+struct PairPart {
+  int center, other, pair, nprim;
+};
+struct SplitRes {
+  int n;
+  PairPart part[2];
+};
+
+// Shell pairs in recurrence orientation, and the list the pair set-up
+// kernel consumes (one DevPairIn per oriented partial pair).
+//   orientation 0: each primitive pair recurs on its tighter primitive's
+//   centre, so a contracted pair splits into at most two oriented partial
+//   pairs (kind 1: primitive pairs whose centre exponent is >= the other's,
+//   kind 2: > the other's); this keeps FP64 HRR cancellation bounded;
+//   orientation 1: the whole pair on the higher l; 2: on the shell holding
+//   the largest exponent.  Kind 0 = every primitive pair.
+struct PairBuilder {
+  const eri_shell* shells;
+  const eri_basis* basis;
+  const std::vector<double>* maxexp;
+  int orientation;
+  std::unordered_map<uint64_t, int> pair_id;
+  std::vector<DevPairIn> pin;
+  std::vector<uint32_t> plist;
+  int64_t pprim = 0;
+
+  int get_pair(int a, int b, int kind) {
+    uint64_t key = ((uint64_t)(uint32_t)a << 34) | ((uint64_t)(uint32_t)b << 2) | (uint64_t)kind;
+    auto it = pair_id.find(key);
+    if (it != pair_id.end()) return it->second;
+    int id = (int)pin.size();
+    DevPairIn d{a, b, (int32_t)pprim, -1, 0, 0};
+    if (kind == 0) {
+      pprim += (int64_t)shells[a].nprim * shells[b].nprim;
+    } else {
+      d.list_off = (int32_t)plist.size();
+      const double* ea = basis->exponents + shells[a].prim_offset;
+      const double* eb = basis->exponents + shells[b].prim_offset;
+      for (int i = 0; i < shells[a].nprim; ++i)
+        for (int j = 0; j < shells[b].nprim; ++j)
+          if (kind == 1 ? ea[i] >= eb[j] : ea[i] > eb[j]) plist.push_back((uint32_t)i | ((uint32_t)j << 16));
+      d.nlist = (int32_t)plist.size() - d.list_off;
+      pprim += d.nlist;
+    }
+    pin.push_back(d);
+    pair_id.emplace(key, id);
+    return id;
+  }
+
+  // the oriented parts of shell pair (s0, s1); callers pass s0 >= s1 so that
+  // ties between equal exponents of different shells break the same way
+  int split(int s0, int s1, PairPart* out) {
+    const int l0 = shells[s0].l, l1 = shells[s1].l;
+    if (orientation == 1 || orientation == 2) {
+      const std::vector<double>& mx = *maxexp;
+      bool first = orientation == 1 ? l0 >= l1 : (mx[s0] != mx[s1] ? mx[s0] > mx[s1] : l0 >= l1);
+      const int c = first ? s0 : s1, o = first ? s1 : s0;
+      out[0] = {c, o, get_pair(c, o, 0), shells[s0].nprim * shells[s1].nprim};
+      return 1;
+    }
+    const double* e0 = basis->exponents + shells[s0].prim_offset;
+    const double* e1 = basis->exponents + shells[s1].prim_offset;
+    int n0 = 0, n1 = 0;  // primitive pairs recurring on s0 / on s1
+    for (int i = 0; i < shells[s0].nprim; ++i)
+      for (int j = 0; j < shells[s1].nprim; ++j) (e0[i] >= e1[j] ? n0 : n1)++;
+    int k = 0;
+    if (n1 == 0) {
+      out[k++] = {s0, s1, get_pair(s0, s1, 0), n0};
+    } else if (n0 == 0) {
+      out[k++] = {s1, s0, get_pair(s1, s0, 0), n1};
+    } else {
+      out[k++] = {s0, s1, get_pair(s0, s1, 1), n0};
+      out[k++] = {s1, s0, get_pair(s1, s0, 2), n1};
+    }
+    return k;
+  }
+};
+
 }  // namespace
 
 // FusionRCG Algorithm 2, "GaussianPairs", once per primitive pair: zeta,
@@ -478,7 +562,28 @@ struct DevBuf {
 };
 }  // namespace
 
+// A molecule kept on the device (eri_mol_create): its shells, and every
+// shell pair (a >= b) in recurrence orientation with its primitive-pair
+// records computed once by the pair set-up kernel.
+struct eri_mol_s {
+  std::vector<eri_shell> shells;
+  std::vector<double> centers, exps, coefs, maxexp;
+  eri_basis view;                 // the vectors above as an eri_basis
+  int nshell = 0;
+  int orientation = 0;
+  PairBuilder pb{nullptr, nullptr, nullptr, 0, {}, {}, {}, 0};
+  std::vector<SplitRes> splits;   // per shell pair a >= b, at a (a + 1) / 2 + b
+  int npair = 0;                  // oriented partial pairs (records)
+  DevBuf<DevShell> shells_d;
+  DevBuf<double> exps_d, coefs_d;
+  DevBuf<DevPairIn> pin_d;
+  DevBuf<uint32_t> plist_d;
+  DevBuf<EriPairRec> pairs_d;
+  DevBuf<EriPairPrim> pprims_d;
+};
+
 struct eri_plan_s {
+  const eri_mol_s* mol = nullptr;  // molecule plans: pairs and primitive pairs of the molecule
   int64_t nq = 0;
   std::vector<int64_t> offsets;  // nq + 1
   std::vector<Bucket> buckets;
@@ -504,6 +609,7 @@ struct eri_plan_s {
   DevBuf<int64_t> d_offsets;         // block offsets, for (ab|ab) and digest plans
   DevBuf<int32_t> d_uq;              // digest plans: the caller's quartet list
   DevBuf<int32_t> d_shell_bf;        // digest plans: first basis function of each shell, and the total
+  DevBuf<int64_t> d_small, d_large;  // digest plans: quartets with small / large blocks
   int32_t nbf = 0;
   bool digest = false;
   DevBuf<int32_t> d_nab;
@@ -530,7 +636,7 @@ int preferred_tier(const int ls[4]);
 
 static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
                      int64_t nq, const double* qbound, double fp32_below, const eri_opts* opts_in,
-                     eri_plan_t** plan_out) {
+                     eri_plan_t** plan_out, const eri_mol_s* mol = nullptr) {
   if (!plan_out) return fail(ERI_EINVAL, "plan_out is NULL");
   *plan_out = nullptr;
   eri_opts opts;
@@ -540,6 +646,12 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       opts.sph_mode > 2 || opts.tier < 0 || opts.tier > 4 || opts.orientation < 0 || opts.orientation > 2 ||
       opts.streams < 0 || opts.streams > 8 || opts.digest < 0 || opts.digest > 1)
     return fail(ERI_EINVAL, "option out of range");
+  if (mol) {
+    shells = mol->shells.data();
+    nshell = mol->nshell;
+    basis = &mol->view;
+    if (opts.orientation != mol->orientation) return fail(ERI_EINVAL, "orientation differs from the molecule's");
+  }
   if (nq < 0 || nshell < 0 || (nq > 0 && (!shells || !basis || !quartets)))
     return fail(ERI_EINVAL, "NULL or negative argument");
   if (nq > (int64_t)1 << 31) return fail(ERI_EINVAL, "too many quartets for one plan");
@@ -591,37 +703,10 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   // primitive's centre (a contracted pair splits into at most two oriented
   // partial pairs), which keeps FP64 HRR cancellation bounded; options: the
   // whole pair on the shell with the largest exponent, or on the higher l.
-  std::unordered_map<uint64_t, int> pair_id;
-  std::vector<DevPairIn> pin;
-  std::vector<uint32_t> plist;
-  int64_t pprim = 0;
-  // kind 0 = every primitive pair; 1 = pairs whose centre exponent is >= the
-  // other's; 2 = pairs whose centre exponent is > the other's
-  auto get_pair = [&](int a, int b, int kind) {
-    uint64_t key = ((uint64_t)(uint32_t)a << 34) | ((uint64_t)(uint32_t)b << 2) | (uint64_t)kind;
-    auto it = pair_id.find(key);
-    if (it != pair_id.end()) return it->second;
-    int id = (int)pin.size();
-    DevPairIn d{a, b, (int32_t)pprim, -1, 0, 0};
-    if (kind == 0) {
-      pprim += (int64_t)shells[a].nprim * shells[b].nprim;
-    } else {
-      d.list_off = (int32_t)plist.size();
-      const double* ea = basis->exponents + shells[a].prim_offset;
-      const double* eb = basis->exponents + shells[b].prim_offset;
-      for (int i = 0; i < shells[a].nprim; ++i)
-        for (int j = 0; j < shells[b].nprim; ++j)
-          if (kind == 1 ? ea[i] >= eb[j] : ea[i] > eb[j]) plist.push_back((uint32_t)i | ((uint32_t)j << 16));
-      d.nlist = (int32_t)plist.size() - d.list_off;
-      pprim += d.nlist;
-    }
-    pin.push_back(d);
-    pair_id.emplace(key, id);
-    return id;
-  };
-  struct PairPart {
-    int center, other, pair, nprim;
-  };
+  PairBuilder pb{shells, basis, &maxexp, opts.orientation, {}, {}, {}, 0};
+  std::vector<DevPairIn>& pin = pb.pin;
+  // molecule plans: alias records of chunked pairs, after the molecule's pairs
+  std::vector<EriPairRec> mol_alias;
   // Chunks: a shell quartet of the team-cooperative tier evaluates its
   // primitive quartets one after another, so a deep contraction is cut into
   // chunks of about kCoopChunk primitive quartets (sub-ranges of the bra
@@ -645,6 +730,21 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     const uint64_t key = ((uint64_t)(uint32_t)parent << 32) | ((uint64_t)(uint32_t)start << 16) | (uint32_t)count;
     auto it = alias_id.find(key);
     if (it != alias_id.end()) return it->second;
+    if (mol) {
+      // a record pointing into the molecule's primitive pairs (its A - B as
+      // the pair set-up kernel computes it)
+      const DevPairIn& pd = mol->pb.pin[parent];
+      const double* A = basis->centers + 3 * shells[pd.a].center;
+      const double* Bc = basis->centers + 3 * shells[pd.b].center;
+      EriPairRec r;
+      r.prim_off = pd.prim_off + start;
+      r.nprim = count;
+      for (int d = 0; d < 3; ++d) r.AB[d] = A[d] - Bc[d];
+      const int id = mol->npair + (int)mol_alias.size();
+      mol_alias.push_back(r);
+      alias_id.emplace(key, id);
+      return id;
+    }
     DevPairIn d = pin[parent];
     d.prim_off += start;
     d.list_off = -2;
@@ -655,47 +755,25 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     return id;
   };
   bool any_reduce = false;
-  auto split_uncached = [&](int s0, int s1, PairPart* out) {
-    const int l0 = shells[s0].l, l1 = shells[s1].l;
-    if (opts.orientation == 1 || opts.orientation == 2) {
-      bool first = opts.orientation == 1 ? l0 >= l1
-                                         : (maxexp[s0] != maxexp[s1] ? maxexp[s0] > maxexp[s1] : l0 >= l1);
-      const int c = first ? s0 : s1, o = first ? s1 : s0;
-      out[0] = {c, o, get_pair(c, o, 0), shells[s0].nprim * shells[s1].nprim};
-      return 1;
-    }
-    const double* e0 = basis->exponents + shells[s0].prim_offset;
-    const double* e1 = basis->exponents + shells[s1].prim_offset;
-    int n0 = 0, n1 = 0;  // primitive pairs recurring on s0 / on s1
-    for (int i = 0; i < shells[s0].nprim; ++i)
-      for (int j = 0; j < shells[s1].nprim; ++j) (e0[i] >= e1[j] ? n0 : n1)++;
-    int k = 0;
-    if (n1 == 0) {
-      out[k++] = {s0, s1, get_pair(s0, s1, 0), n0};
-    } else if (n0 == 0) {
-      out[k++] = {s1, s0, get_pair(s1, s0, 0), n1};
-    } else {
-      out[k++] = {s0, s1, get_pair(s0, s1, 1), n0};
-      out[k++] = {s1, s0, get_pair(s1, s0, 2), n1};
-    }
-    return k;
-  };
-  struct SplitRes {
-    int n;
-    PairPart part[2];
-  };
   std::unordered_map<uint64_t, SplitRes> split_cache;
   auto split = [&](int s0, int s1, PairPart* out) {
-    const uint64_t key = ((uint64_t)(uint32_t)s0 << 32) | (uint32_t)s1;
-    auto it = split_cache.find(key);
-    if (it == split_cache.end()) {
-      SplitRes r;
-      r.n = split_uncached(s0, s1, r.part);
-      it = split_cache.emplace(key, r).first;
+    if (s0 < s1) std::swap(s0, s1);
+    const SplitRes* r;
+    if (mol) {
+      r = &mol->splits[(int64_t)s0 * (s0 + 1) / 2 + s1];
+    } else {
+      const uint64_t key = ((uint64_t)(uint32_t)s0 << 32) | (uint32_t)s1;
+      auto it = split_cache.find(key);
+      if (it == split_cache.end()) {
+        SplitRes x;
+        x.n = pb.split(s0, s1, x.part);
+        it = split_cache.emplace(key, x).first;
+      }
+      r = &it->second;
     }
-    out[0] = it->second.part[0];
-    out[1] = it->second.part[1];
-    return it->second.n;
+    out[0] = r->part[0];
+    out[1] = r->part[1];
+    return r->n;
   };
   struct QInfo {
     int cls;    // class key index
@@ -768,7 +846,7 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   }
   const int64_t nparts = (int64_t)qi.size();
   plan->zero_out = any_reduce;
-  if (pprim > ((int64_t)1 << 31) - 1) return fail(ERI_EINVAL, "too many primitive pairs");
+  if (pb.pprim > ((int64_t)1 << 31) - 1) return fail(ERI_EINVAL, "too many primitive pairs");
   // ---- buckets: by part round (a block is written before it is added to),
   // then class (heaviest first), precision, then contraction signature
   // (K4 descending, then bra depth descending).  One counting sort over a
@@ -1041,24 +1119,49 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       (rc = plan->coop_h.alloc(max_coop_h, "cooperative accumulators")))
     return rc;
   // ---- device data
-  std::vector<DevShell> dsh(nshell);
-  for (int s = 0; s < nshell; ++s) {
-    for (int d = 0; d < 3; ++d) dsh[s].ctr[d] = basis->centers[3 * shells[s].center + d];
-    dsh[s].l = shells[s].l;
-    dsh[s].nprim = shells[s].nprim;
-    dsh[s].prim = shells[s].prim_offset;
-    dsh[s].pad = 0;
+  std::vector<DevShell> dsh;
+  std::vector<double> ex, co;
+  if (mol) {
+    // the molecule's shells and primitive pairs stay where they are; the plan
+    // holds a copy of its pair records, followed by this plan's aliases
+    const size_t npr = (size_t)mol->npair + mol_alias.size();
+    if ((rc = plan->pairs.alloc(npr, "pairs")) || (rc = plan->quartets.upload(recs, "quartet records"))) return rc;
+    if (plan->pairs.async) {
+      CUDA_OR(cudaMemcpyAsync(plan->pairs.p, mol->pairs_d.p, (size_t)mol->npair * sizeof(EriPairRec),
+                              cudaMemcpyDeviceToDevice, plan->pairs.st), "copy molecule pairs");
+      if (!mol_alias.empty())
+        CUDA_OR(cudaMemcpyAsync(plan->pairs.p + mol->npair, mol_alias.data(), mol_alias.size() * sizeof(EriPairRec),
+                                cudaMemcpyHostToDevice, plan->pairs.st), "upload aliases");
+    } else {
+      CUDA_OR(cudaMemcpy(plan->pairs.p, mol->pairs_d.p, (size_t)mol->npair * sizeof(EriPairRec),
+                         cudaMemcpyDeviceToDevice), "copy molecule pairs");
+      if (!mol_alias.empty())
+        CUDA_OR(cudaMemcpy(plan->pairs.p + mol->npair, mol_alias.data(), mol_alias.size() * sizeof(EriPairRec),
+                           cudaMemcpyHostToDevice), "upload aliases");
+    }
+    plan->mol = mol;
+    plan->npair = 0;  // nothing for the pair set-up kernel
+    plan->npprim = mol->pb.pprim;
+  } else {
+    dsh.resize(nshell);
+    for (int s = 0; s < nshell; ++s) {
+      for (int d = 0; d < 3; ++d) dsh[s].ctr[d] = basis->centers[3 * shells[s].center + d];
+      dsh[s].l = shells[s].l;
+      dsh[s].nprim = shells[s].nprim;
+      dsh[s].prim = shells[s].prim_offset;
+      dsh[s].pad = 0;
+    }
+    ex.assign(basis->exponents, basis->exponents + basis->nprim_total);
+    co.assign(basis->coefs, basis->coefs + basis->nprim_total);
+    if ((rc = plan->shells.upload(dsh, "shells")) || (rc = plan->exps.upload(ex, "exponents")) ||
+        (rc = plan->coefs.upload(co, "coefficients")) || (rc = plan->pin.upload(pin, "pair list")) ||
+        (rc = plan->plist.upload(pb.plist, "primitive-pair lists")) ||
+        (rc = plan->pairs.alloc(pin.size(), "pairs")) || (rc = plan->pprims.alloc(pb.pprim, "primitive pairs")) ||
+        (rc = plan->quartets.upload(recs, "quartet records")))
+      return rc;
+    plan->npair = (int)pin.size();
+    plan->npprim = pb.pprim;
   }
-  std::vector<double> ex(basis->exponents, basis->exponents + basis->nprim_total);
-  std::vector<double> co(basis->coefs, basis->coefs + basis->nprim_total);
-  if ((rc = plan->shells.upload(dsh, "shells")) || (rc = plan->exps.upload(ex, "exponents")) ||
-      (rc = plan->coefs.upload(co, "coefficients")) || (rc = plan->pin.upload(pin, "pair list")) ||
-      (rc = plan->plist.upload(plist, "primitive-pair lists")) ||
-      (rc = plan->pairs.alloc(pin.size(), "pairs")) || (rc = plan->pprims.alloc(pprim, "primitive pairs")) ||
-      (rc = plan->quartets.upload(recs, "quartet records")))
-    return rc;
-  plan->npair = (int)pin.size();
-  plan->npprim = pprim;
   {
     // a plan whose every quartet is (ab|ab) can also produce Schwarz bounds
     bool diag = true;
@@ -1081,13 +1184,18 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     std::vector<int32_t> uq(quartets, quartets + 4 * nq);
     std::vector<int32_t> bf(nshell + 1, 0);
     for (int s = 0; s < nshell; ++s) bf[s + 1] = bf[s] + nfun(shells[s].l, cart);
-    if ((rc = plan->d_uq.upload(uq, "quartet list")) || (rc = plan->d_shell_bf.upload(bf, "shell offsets")))
+    std::vector<int64_t> small, large;
+    for (int64_t q = 0; q < nq; ++q)
+      (plan->offsets[q + 1] - plan->offsets[q] <= kSmallBlock ? small : large).push_back(q);
+    if ((rc = plan->d_uq.upload(uq, "quartet list")) || (rc = plan->d_shell_bf.upload(bf, "shell offsets")) ||
+        (rc = plan->d_small.upload(small, "digest list")) || (rc = plan->d_large.upload(large, "digest list")))
       return rc;
     plan->nbf = bf[nshell];
     plan->digest = true;
   }
   plan->h2d_bytes = (double)(dsh.size() * sizeof(DevShell) + 2 * ex.size() * sizeof(double) +
-                             pin.size() * sizeof(DevPairIn) + plist.size() * sizeof(uint32_t) +
+                             (mol ? mol_alias.size() * sizeof(EriPairRec)
+                                  : pin.size() * sizeof(DevPairIn) + pb.plist.size() * sizeof(uint32_t)) +
                              recs.size() * sizeof(EriQuartetRec));
   if (max_scratch_slots > 0) {
     plan->scratch_stride = (int64_t)max_grid_global * 128;
@@ -1116,6 +1224,106 @@ extern "C" int eri_plan_on_stream(const eri_shell* shells, int32_t nshell, const
     rc = plan_impl(shells, nshell, basis, quartets, nq, qbound, fp32_below, opts, plan_out);
   }
   if (rc == ERI_OK && *plan_out) {
+    (*plan_out)->stream_ordered = true;
+    (*plan_out)->alloc_stream = (cudaStream_t)stream;
+  }
+  return rc;
+}
+
+extern "C" int eri_mol_create(const eri_shell* shells, int32_t nshell, const eri_basis* basis,
+                                const eri_opts* opts_in, eri_mol_t** out) {
+  if (!out) return fail(ERI_EINVAL, "out is NULL");
+  *out = nullptr;
+  eri_opts opts;
+  memset(&opts, 0, sizeof opts);
+  if (opts_in) opts = *opts_in;
+  if (opts.orientation < 0 || opts.orientation > 2) return fail(ERI_EINVAL, "option out of range");
+  if (nshell < 1 || !shells || !basis || !basis->centers || !basis->exponents || !basis->coefs ||
+      basis->ncenter < 0 || basis->nprim_total < 0)
+    return fail(ERI_EINVAL, "NULL or empty basis");
+  auto m = std::make_unique<eri_mol_s>();
+  m->nshell = nshell;
+  m->orientation = opts.orientation;
+  m->shells.assign(shells, shells + nshell);
+  m->maxexp.assign(nshell, 0.0);
+  for (int s = 0; s < nshell; ++s) {
+    const eri_shell& S = shells[s];
+    if (S.l < 0) return fail(ERI_EINVAL, "shell " + std::to_string(s) + ": negative l");
+    if (S.l > ERI_MAX_L) return fail(ERI_EUNSUPPORTED, "shell " + std::to_string(s) + ": l > 4");
+    if (S.nprim < 1 || S.nprim > ERI_MAX_NPRIM) return fail(ERI_EINVAL, "shell " + std::to_string(s) + ": bad nprim");
+    if (S.center < 0 || S.center >= basis->ncenter) return fail(ERI_EINVAL, "shell " + std::to_string(s) + ": bad centre");
+    if (S.prim_offset < 0 || (int64_t)S.prim_offset + S.nprim > basis->nprim_total)
+      return fail(ERI_EINVAL, "shell " + std::to_string(s) + ": primitives out of range");
+    for (int k = 0; k < S.nprim; ++k) {
+      const double a = basis->exponents[S.prim_offset + k], c = basis->coefs[S.prim_offset + k];
+      if (!(a > 0) || !std::isfinite(a) || !std::isfinite(c))
+        return fail(ERI_EINVAL, "shell " + std::to_string(s) + ": non-positive or non-finite exponent/coefficient");
+      m->maxexp[s] = std::max(m->maxexp[s], a);
+    }
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(basis->centers[3 * S.center + d])) return fail(ERI_EINVAL, "non-finite centre");
+  }
+  m->centers.assign(basis->centers, basis->centers + 3 * (size_t)basis->ncenter);
+  m->exps.assign(basis->exponents, basis->exponents + basis->nprim_total);
+  m->coefs.assign(basis->coefs, basis->coefs + basis->nprim_total);
+  m->view = eri_basis{m->centers.data(), basis->ncenter, m->exps.data(), m->coefs.data(), basis->nprim_total};
+  int rc = ensure_library();
+  if (rc) return rc;
+  m->pb.shells = m->shells.data();
+  m->pb.basis = &m->view;
+  m->pb.maxexp = &m->maxexp;
+  m->pb.orientation = opts.orientation;
+  const int64_t npairs = (int64_t)nshell * (nshell + 1) / 2;
+  m->splits.resize(npairs);
+  for (int a = 0; a < nshell; ++a)
+    for (int b = 0; b <= a; ++b) {
+      SplitRes& r = m->splits[(int64_t)a * (a + 1) / 2 + b];
+      r.n = m->pb.split(a, b, r.part);
+    }
+  if (m->pb.pprim > ((int64_t)1 << 31) - 1) return fail(ERI_EINVAL, "too many primitive pairs");
+  m->npair = (int)m->pb.pin.size();
+  std::vector<DevShell> dsh(nshell);
+  for (int s = 0; s < nshell; ++s) {
+    for (int d = 0; d < 3; ++d) dsh[s].ctr[d] = m->centers[3 * shells[s].center + d];
+    dsh[s].l = shells[s].l;
+    dsh[s].nprim = shells[s].nprim;
+    dsh[s].prim = shells[s].prim_offset;
+    dsh[s].pad = 0;
+  }
+  if ((rc = m->shells_d.upload(dsh, "shells")) || (rc = m->exps_d.upload(m->exps, "exponents")) ||
+      (rc = m->coefs_d.upload(m->coefs, "coefficients")) || (rc = m->pin_d.upload(m->pb.pin, "pair list")) ||
+      (rc = m->plist_d.upload(m->pb.plist, "primitive-pair lists")) ||
+      (rc = m->pairs_d.alloc(m->npair, "pairs")) || (rc = m->pprims_d.alloc(m->pb.pprim, "primitive pairs")))
+    return rc;
+  const int threads = 128;
+  eri_pair_setup_kernel<<<(m->npair + threads - 1) / threads, threads>>>(
+      m->pin_d.p, m->npair, m->shells_d.p, m->exps_d.p, m->coefs_d.p, m->plist_d.p, m->pairs_d.p, m->pprims_d.p);
+  CUDA_OR(cudaGetLastError(), "pair set-up launch");
+  CUDA_OR(cudaDeviceSynchronize(), "pair set-up");
+  *out = m.release();
+  return ERI_OK;
+}
+
+extern "C" int eri_mol_destroy(eri_mol_t* mol) {
+  if (!mol) return ERI_OK;
+  cudaDeviceSynchronize();
+  delete mol;
+  return ERI_OK;
+}
+
+extern "C" int eri_plan_on_mol(const eri_mol_t* mol, const int32_t* quartets, int64_t nq, const double* qbound,
+                                 double fp32_below, const eri_opts* opts, void* stream, eri_plan_t** plan_out) {
+  if (!mol) return fail(ERI_EINVAL, "NULL molecule");
+  if (qbound)
+    for (int64_t q = 0; q < nq; ++q)
+      if (!(qbound[q] >= 0)) return fail(ERI_EINVAL, "negative or NaN Schwarz bound");
+  if (qbound && (!(fp32_below >= 0) || !std::isfinite(fp32_below))) return fail(ERI_EINVAL, "bad FP32 threshold");
+  int rc;
+  {
+    AllocStreamScope scope((cudaStream_t)stream, stream != nullptr);
+    rc = plan_impl(nullptr, 0, nullptr, quartets, nq, qbound, fp32_below, opts, plan_out, mol);
+  }
+  if (rc == ERI_OK && *plan_out && stream) {
     (*plan_out)->stream_ordered = true;
     (*plan_out)->alloc_stream = (cudaStream_t)stream;
   }
@@ -1176,12 +1384,15 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
     CUDA_OR(cudaMemsetAsync(out, 0, (size_t)plan->offsets.back() * sizeof(double), stream), "zero output");
   {
     CUDA_OR(mark(0), "cudaEventRecord");
+    // molecule plans have their primitive pairs already (npair = 0)
     const int threads = 128;
     const int blocks = (plan->npair + threads - 1) / threads;
-    eri_pair_setup_kernel<<<blocks, threads, 0, stream>>>(plan->pin.p, plan->npair, plan->shells.p, plan->exps.p,
-                                                          plan->coefs.p, plan->plist.p, plan->pairs.p,
-                                                          plan->pprims.p);
-    CUDA_OR(cudaGetLastError(), "pair set-up launch");
+    if (blocks > 0) {
+      eri_pair_setup_kernel<<<blocks, threads, 0, stream>>>(plan->pin.p, plan->npair, plan->shells.p, plan->exps.p,
+                                                            plan->coefs.p, plan->plist.p, plan->pairs.p,
+                                                            plan->pprims.p);
+      CUDA_OR(cudaGetLastError(), "pair set-up launch");
+    }
     CUDA_OR(mark(1), "cudaEventRecord");
     ++li;
   }
@@ -1204,7 +1415,7 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
     EriLaunchArgs a;
     a.quartets = plan->quartets.p + b.first;
     a.pairs = plan->pairs.p;
-    a.pprims = plan->pprims.p;
+    a.pprims = plan->mol ? plan->mol->pprims_d.p : plan->pprims.p;
     a.boys_tab = L.d_boys;
     a.out = out;
     a.scratch = plan->scratch.p;
@@ -1270,7 +1481,12 @@ extern "C" int eri_digest_jk(eri_plan_t* plan, const double* blocks, const doubl
   g.K = K;
   g.nq = plan->nq;
   g.nbf = nbf;
-  CUDA_OR(eri_digest_launch(&g, (cudaStream_t)stream), "digest launch");
+  g.list = plan->d_small.p;
+  g.nlist = (int64_t)plan->d_small.n;
+  CUDA_OR(eri_digest_launch(&g, 1, (cudaStream_t)stream), "digest launch");
+  g.list = plan->d_large.p;
+  g.nlist = (int64_t)plan->d_large.n;
+  CUDA_OR(eri_digest_launch(&g, 0, (cudaStream_t)stream), "digest launch");
   return ERI_OK;
 }
 
@@ -1428,12 +1644,15 @@ extern "C" int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* st
   cudaStream_t stream = (cudaStream_t)stream_;
   Library& L = lib();
   {
+    // molecule plans have their primitive pairs already (npair = 0)
     const int threads = 128;
     const int blocks = (plan->npair + threads - 1) / threads;
-    eri_pair_setup_kernel<<<blocks, threads, 0, stream>>>(plan->pin.p, plan->npair, plan->shells.p, plan->exps.p,
-                                                          plan->coefs.p, plan->plist.p, plan->pairs.p,
-                                                          plan->pprims.p);
-    CUDA_OR(cudaGetLastError(), "pair set-up launch");
+    if (blocks > 0) {
+      eri_pair_setup_kernel<<<blocks, threads, 0, stream>>>(plan->pin.p, plan->npair, plan->shells.p, plan->exps.p,
+                                                            plan->coefs.p, plan->plist.p, plan->pairs.p,
+                                                            plan->pprims.p);
+      CUDA_OR(cudaGetLastError(), "pair set-up launch");
+    }
   }
   for (const Bucket& b : plan->buckets) {
     // as many 128-thread blocks as the fixed array holds, at most the plan's
@@ -1443,7 +1662,7 @@ extern "C" int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* st
     EriLaunchArgs a;
     a.quartets = plan->quartets.p + b.first;
     a.pairs = plan->pairs.p;
-    a.pprims = plan->pprims.p;
+    a.pprims = plan->mol ? plan->mol->pprims_d.p : plan->pprims.p;
     a.boys_tab = L.d_boys;
     a.out = out;
     a.scratch = scratch;

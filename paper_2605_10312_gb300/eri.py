@@ -72,6 +72,15 @@ def library(path: str = LIB):
         lib.eri_compute_jk.restype = ctypes.c_int
         lib.eri_compute_jk.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_mol_create.restype = ctypes.c_int
+        lib.eri_mol_create.argtypes = [ctypes.POINTER(_Shell), ctypes.c_int32, ctypes.POINTER(_Basis),
+                                       ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_void_p)]
+        lib.eri_mol_destroy.restype = ctypes.c_int
+        lib.eri_mol_destroy.argtypes = [ctypes.c_void_p]
+        lib.eri_plan_on_mol.restype = ctypes.c_int
+        lib.eri_plan_on_mol.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_double, ctypes.POINTER(_Opts), ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]
         lib.eri_plan_launch_precision.restype = ctypes.c_int
         lib.eri_plan_launch_precision.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.eri_output_count.restype = ctypes.c_int64
@@ -121,31 +130,64 @@ def _stream_handle(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+def _marshal_basis(basis):
+    """(shell array, eri_basis struct, arrays to keep alive) for a Basis."""
+    ns = int(basis.shell_l.shape[0])
+    # eri_shell records {l, nprim, center, prim_offset}, int32 each
+    shv = np.empty((max(ns, 1), 4), dtype=np.int32)
+    if ns:
+        shv[:, 0] = basis.shell_l
+        shv[:, 1] = basis.shell_nprim
+        shv[:, 2] = basis.shell_center
+        shv[:, 3] = basis.shell_prim
+    keep = [np.ascontiguousarray(basis.centers, dtype=np.float64), np.ascontiguousarray(basis.exps, dtype=np.float64),
+            np.ascontiguousarray(basis.coefs, dtype=np.float64), shv]
+    b = _Basis(keep[0].ctypes.data, int(keep[0].shape[0]), keep[1].ctypes.data, keep[2].ctypes.data,
+               int(keep[1].shape[0]))
+    return shv.ctypes.data_as(ctypes.POINTER(_Shell)), ns, b, keep
+
+
+class Mol:
+    """A molecule kept on the device (eri_mol_create): shells and the
+    primitive-pair records of every shell pair, computed once."""
+
+    def __init__(self, basis, orientation="split"):
+        lib = library()
+        sh, ns, b, keep = _marshal_basis(basis)
+        o = _Opts(0, 0, 0, 0, ORIENTATIONS[orientation], 0, 0)
+        h = ctypes.c_void_p()
+        _check(lib.eri_mol_create(sh, ns, ctypes.byref(b), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.basis = basis
+        self.orientation = orientation
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            library().eri_mol_destroy(self._h)
+            self._h = None
+
+
 class Plan:
     """A device-resident plan for one quartet list (see eri_plan)."""
 
     def __init__(self, basis, quartets, axis_rule="prose", schedule="dsa", sph_mode="stepwise", tier="auto",
-                 orientation="split", qbound=None, fp32_below=None, streams=0, stream=None, digest=False):
+                 orientation="split", qbound=None, fp32_below=None, streams=0, stream=None, digest=False,
+                 mol=None):
         """qbound/fp32_below: mixed precision (eri_plan_mixed) -- quartets whose
         bound is below fp32_below run their recurrences in FP32.  stream: a
         stream-ordered plan (eri_plan_on_stream) whose device memory lives and
-        dies on that stream; compute it on the same stream."""
+        dies on that stream; compute it on the same stream.  mol: a Mol whose
+        shells the quartets index (eri_plan_on_mol); basis is then ignored."""
         lib = library()
         q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
-        ns = int(basis.shell_l.shape[0])
-        # eri_shell records {l, nprim, center, prim_offset}, int32 each
-        shv = np.empty((max(ns, 1), 4), dtype=np.int32)
-        if ns:
-            shv[:, 0] = basis.shell_l
-            shv[:, 1] = basis.shell_nprim
-            shv[:, 2] = basis.shell_center
-            shv[:, 3] = basis.shell_prim
-        sh = shv.ctypes.data_as(ctypes.POINTER(_Shell))
-        self._keep = [np.ascontiguousarray(basis.centers, dtype=np.float64),
-                      np.ascontiguousarray(basis.exps, dtype=np.float64),
-                      np.ascontiguousarray(basis.coefs, dtype=np.float64), q, shv]
-        b = _Basis(self._keep[0].ctypes.data, int(self._keep[0].shape[0]), self._keep[1].ctypes.data,
-                   self._keep[2].ctypes.data, int(self._keep[1].shape[0]))
+        if mol is not None:
+            self._keep = [q]
+        else:
+            sh, ns, b, keep = _marshal_basis(basis)
+            self._keep = keep + [q]
         o = _Opts(AXIS_RULES[axis_rule], SCHEDULES[schedule], SPH_MODES[sph_mode], TIERS[tier],
                   ORIENTATIONS[orientation], int(streams), 1 if digest else 0)
         h = ctypes.c_void_p()
@@ -154,7 +196,14 @@ class Plan:
             qb = np.ascontiguousarray(np.asarray(qbound, dtype=np.float64).reshape(-1))
             if qb.shape[0] != q.shape[0]:
                 raise ValueError("qbound needs one entry per quartet")
-        if stream is not None:
+        if mol is not None:
+            if orientation != mol.orientation:
+                raise ValueError("orientation differs from the molecule's")
+            _check(lib.eri_plan_on_mol(mol._h, q.ctypes.data, q.shape[0], None if qb is None else qb.ctypes.data,
+                                       float(fp32_below if fp32_below is not None else 0.0), ctypes.byref(o),
+                                       None if stream is None else _stream_handle(stream), ctypes.byref(h)))
+            self._mol = mol  # the plan must not outlive the molecule
+        elif stream is not None:
             _check(lib.eri_plan_on_stream(sh, ns, ctypes.byref(b), q.ctypes.data, q.shape[0],
                                           None if qb is None else qb.ctypes.data,
                                           float(fp32_below if fp32_below is not None else 0.0), ctypes.byref(o),

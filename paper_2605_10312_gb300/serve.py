@@ -8,9 +8,10 @@ arrive:
   * admission: a request enters when a slot (a CUDA stream) is free and its
     device-memory footprint (output blocks, quartet records, pair data) fits
     in the remaining budget; requests are admitted in arrival order;
-  * planning: a pool of host threads builds each admitted request's plan
-    (eri_plan_on_stream: stream-ordered device memory, so that retiring one
-    request never synchronises the device under the others); the native
+  * planning: a pool of host threads builds each admitted request's plan on
+    its molecule (eri_plan_on_mol: the molecule's primitive-pair records are
+    reused, and the plan's device memory is stream-ordered, so that retiring
+    one request never synchronises the device under the others); the native
     planner releases the interpreter lock;
   * execution: each plan runs on its slot's stream, so requests that arrive
     while others are on the device overlap with them;
@@ -44,6 +45,8 @@ class Molecule:
     pairs: np.ndarray     # [npair, 2] shell pairs (a >= b)
     pair_q: np.ndarray    # Schwarz factor per pair (host copy)
     pair_q_dev: object    # the same on the device
+    mol: object = None    # eri.Mol: shells and primitive-pair records on the device
+    nsph: np.ndarray = None  # spherical components per shell (int64)
 
 
 @dataclasses.dataclass
@@ -87,13 +90,17 @@ class Server:
 
     def close(self):
         self.pool.shutdown(wait=True)
+        for m in self.molecules.values():
+            if m.mol is not None:
+                m.mol.close()
 
     # -- molecules ----------------------------------------------------------
     def register(self, key, basis):
         """Keep a molecule resident: Schwarz factors of every shell pair,
         computed on the device."""
         pairs, q = screen.pair_bounds(basis)
-        mol = Molecule(key, basis, pairs, q, self.torch.from_numpy(q).to("cuda"))
+        mol = Molecule(key, basis, pairs, q, self.torch.from_numpy(q).to("cuda"), eri.Mol(basis),
+                       NSPH[basis.shell_l].astype(np.int64))
         self.molecules[key] = mol
         return mol
 
@@ -101,13 +108,13 @@ class Server:
     @staticmethod
     def footprint(mol, quartets):
         """Device bytes a request holds while it runs: its output blocks, up
-        to four quartet-part records per quartet and its pair data."""
+        to four quartet-part records per quartet and its copy of the
+        molecule's pair records."""
         q = np.asarray(quartets)
-        l = mol.basis.shell_l[q]
-        out = int(np.prod(NSPH[l], axis=1).sum())
-        kp = mol.basis.shell_nprim[q]
-        pair_prims = int((kp[:, 0] * kp[:, 1] + kp[:, 2] * kp[:, 3]).sum())
-        return 8 * out + 4 * 32 * q.shape[0] + 80 * pair_prims + (1 << 16)
+        ns = mol.nsph if mol.nsph is not None else NSPH[mol.basis.shell_l].astype(np.int64)
+        out = int((ns[q[:, 0]] * ns[q[:, 1]] * ns[q[:, 2]] * ns[q[:, 3]]).sum())
+        npair = 2 * mol.pairs.shape[0]
+        return 8 * out + 4 * 32 * q.shape[0] + 32 * npair + (1 << 16)
 
     def bounds(self, mol, quartets):
         return screen.quartet_bounds(mol.pair_q, quartets)
@@ -116,9 +123,9 @@ class Server:
     def _build(self, req, stream):
         mol = self.molecules[req.mol]
         if self.fp32_below is None:
-            return eri.Plan(mol.basis, req.quartets, stream=stream)
+            return eri.Plan(None, req.quartets, mol=mol.mol, stream=stream)
         qb = self.bounds(mol, req.quartets)
-        return eri.Plan(mol.basis, req.quartets, qbound=qb, fp32_below=self.fp32_below, stream=stream)
+        return eri.Plan(None, req.quartets, qbound=qb, fp32_below=self.fp32_below, mol=mol.mol, stream=stream)
 
     def run_alone(self, req):
         """The request evaluated by itself (plain plan, default stream

@@ -116,3 +116,31 @@ def test_concurrent_lanes_match_serial(eri):
         stream.synchronize()
     assert within(b.cpu().numpy(), a.cpu().numpy(), atol=1e-15, rtol=1e-13).all()
     assert within(b2.cpu().numpy(), a.cpu().numpy(), atol=1e-15, rtol=1e-13).all()
+
+
+def test_molecule_plans_match_plain_plans(eri):
+    """Plans on a device-resident molecule (shared primitive-pair records,
+    plan-local chunk aliases) give the blocks of ordinary plans, in FP64 and
+    in mixed precision, with ordinary and stream-ordered memory."""
+    import torch
+    classes = [(1, 0, 0, 0), (2, 1, 1, 0), (2, 2, 1, 1), (3, 3, 2, 2), (4, 3, 2, 1)]
+    basis, q = synth.mixed_class_set(classes, 150, kset=(1, 3, 6), seed=31)
+    mol = eri.Mol(basis)
+    stream = torch.cuda.Stream()
+    qb = np.random.default_rng(0).uniform(0, 2e-6, q.shape[0])
+    for kw in ({}, {"qbound": qb, "fp32_below": 1e-6}):
+        pp = eri.Plan(basis, q, **kw)
+        pm = eri.Plan(None, q, mol=mol, **kw)
+        ps = eri.Plan(None, q, mol=mol, stream=stream, **kw)
+        a = torch.empty(pp.output_count, dtype=torch.float64, device="cuda")
+        b, c = torch.empty_like(a), torch.empty_like(a)
+        with torch.cuda.stream(stream):
+            pp.compute(a, stream)
+            pm.compute(b, stream)
+            ps.compute(c, stream)
+            stream.synchronize()
+        assert within(b.cpu().numpy(), a.cpu().numpy(), atol=1e-15, rtol=1e-13).all()
+        assert within(c.cpu().numpy(), a.cpu().numpy(), atol=1e-15, rtol=1e-13).all()
+        for p in (pp, pm, ps):
+            p.close()
+    mol.close()

@@ -52,7 +52,7 @@ def test_admission_by_memory_and_rejection(server_mod):
     probe = serve.Server(budget_bytes=1 << 30, slots=2, planners=1, fp32_below=None)
     reqs = _setup(serve, probe, sizes=(2,), nq=(500, 3000), nreq=6, seed=1)
     sizes = [probe.footprint(probe.molecules[r.mol], r.quartets) for r in reqs]
-    probe.close()
+    probe.pool.shutdown()
     # a budget that holds the largest request alone: requests run one by one
     srv = serve.Server(budget_bytes=max(sizes), slots=4, planners=2, fp32_below=None, keep_outputs=True)
     srv.molecules = dict(probe.molecules)
@@ -67,8 +67,8 @@ def test_admission_by_memory_and_rejection(server_mod):
     tiny.molecules = dict(probe.molecules)
     res = tiny.serve(reqs)
     assert all(r.status == "rejected" for r in res)
+    tiny.pool.shutdown()
     srv.close()
-    tiny.close()
 
 
 def test_timeout_status_is_bounded(server_mod):
