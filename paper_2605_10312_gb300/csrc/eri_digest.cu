@@ -18,15 +18,18 @@
 //   Kad[i][l] =   f sum_jk v D_jk   -> K_il and K_li
 //   Kbc[j][k] =   f sum_il v D_il   -> K_jk and K_kj
 //   Kbd[j][l] =   f sum_ik v D_ik   -> K_jl and K_lj
-// One warp per quartet; each lane owns output entries of one contraction at
-// a time (no two lanes add to the same entry), reads the block through L1
-// and adds its entries to J and K with FP64 reductions.
+// Blocks of up to 128 elements are digested by one thread each (a warp
+// covers 32 quartets); larger blocks by one warp each, whose lanes own output
+// entries of one contraction at a time (no two lanes add to the same entry).
+// Blocks are read through L1; J and K receive FP64 reductions.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 struct EriDigestArgs {
+  const int64_t* __restrict__ list;      // quartets this launch digests (indices into quartets)
+  int64_t nlist;
   const int32_t* __restrict__ quartets;  // [nq][4] shell indices, the caller's order
-  const int64_t* __restrict__ offsets;   // [nq] first element of each block
+  const int64_t* __restrict__ offsets;   // [nq + 1] first element of each block, and the total
   const int32_t* __restrict__ shell_bf;  // [nshell + 1] first basis function of each shell
   const double* __restrict__ blocks;
   const double* __restrict__ D;          // [nbf][nbf], symmetric
@@ -49,22 +52,22 @@ __device__ __forceinline__ int eri_stabilizer(int a, int b, int c, int d) {
   return n;
 }
 
-__global__ void __launch_bounds__(128) eri_digest_jk_kernel(const EriDigestArgs g) {
-  const int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (q >= g.nq) return;
+// Digest quartet q from its block v; the W threads lane = 0..W-1 of a group
+// share its output entries (W = 1: one thread does all of them).
+template <int W>
+__device__ __forceinline__ void eri_digest_quartet(const EriDigestArgs& g, int64_t q, int lane,
+                                                   const double* __restrict__ v) {
   const int a = g.quartets[4 * q], b = g.quartets[4 * q + 1], c = g.quartets[4 * q + 2], d = g.quartets[4 * q + 3];
   const int A = g.shell_bf[a], B = g.shell_bf[b], C = g.shell_bf[c], Dd = g.shell_bf[d];
   const int na = g.shell_bf[a + 1] - A, nb = g.shell_bf[b + 1] - B, nc = g.shell_bf[c + 1] - C,
             nd = g.shell_bf[d + 1] - Dd;
   const double f = 1.0 / (double)eri_stabilizer(a, b, c, d);
-  const double* __restrict__ v = g.blocks + g.offsets[q];
   const double* __restrict__ Dm = g.D;
   const int64_t n = g.nbf;
   const int sj = nc * nd, si = nb * sj;  // strides of i and j in the block; k stride nd
   if (g.J) {
     // Jab[i][j] = 2 f sum_kl v D_kl
-    for (int o = lane; o < na * nb; o += 32) {
+    for (int o = lane; o < na * nb; o += W) {
       const int i = o / nb, j = o - i * nb;
       const double* r = v + (int64_t)i * si + (int64_t)j * sj;
       double s = 0.0;
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(128) eri_digest_jk_kernel(const EriDigestArgs 
       atomicAdd(g.J + (B + j) * n + A + i, s);
     }
     // Jcd[k][l] = 2 f sum_ij v D_ij
-    for (int o = lane; o < nc * nd; o += 32) {
+    for (int o = lane; o < nc * nd; o += W) {
       const int k = o / nd, l = o - k * nd;
       double s = 0.0;
       for (int i = 0; i < na; ++i)
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(128) eri_digest_jk_kernel(const EriDigestArgs 
   }
   if (g.K) {
     // Kac[i][k] = f sum_jl v D_jl
-    for (int o = lane; o < na * nc; o += 32) {
+    for (int o = lane; o < na * nc; o += W) {
       const int i = o / nc, k = o - i * nc;
       double s = 0.0;
       for (int j = 0; j < nb; ++j)
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(128) eri_digest_jk_kernel(const EriDigestArgs 
       atomicAdd(g.K + (C + k) * n + A + i, s);
     }
     // Kad[i][l] = f sum_jk v D_jk
-    for (int o = lane; o < na * nd; o += 32) {
+    for (int o = lane; o < na * nd; o += W) {
       const int i = o / nd, l = o - i * nd;
       double s = 0.0;
       for (int j = 0; j < nb; ++j)
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(128) eri_digest_jk_kernel(const EriDigestArgs 
       atomicAdd(g.K + (Dd + l) * n + A + i, s);
     }
     // Kbc[j][k] = f sum_il v D_il
-    for (int o = lane; o < nb * nc; o += 32) {
+    for (int o = lane; o < nb * nc; o += W) {
       const int j = o / nc, k = o - j * nc;
       double s = 0.0;
       for (int i = 0; i < na; ++i)
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(128) eri_digest_jk_kernel(const EriDigestArgs 
       atomicAdd(g.K + (C + k) * n + B + j, s);
     }
     // Kbd[j][l] = f sum_ik v D_ik
-    for (int o = lane; o < nb * nd; o += 32) {
+    for (int o = lane; o < nb * nd; o += W) {
       const int j = o / nd, l = o - j * nd;
       double s = 0.0;
       for (int i = 0; i < na; ++i)
@@ -134,10 +137,30 @@ __global__ void __launch_bounds__(128) eri_digest_jk_kernel(const EriDigestArgs 
   }
 }
 
-extern "C" cudaError_t eri_digest_launch(const EriDigestArgs* g, cudaStream_t stream) {
-  if (g->nq == 0) return cudaSuccess;
-  const int warps = 4;
-  const int64_t grid = (g->nq + warps - 1) / warps;
-  eri_digest_jk_kernel<<<(unsigned)grid, 32 * warps, 0, stream>>>(*g);
+__global__ void __launch_bounds__(128) eri_digest_small_kernel(const EriDigestArgs g) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < g.nlist) {
+    const int64_t q = g.list[t];
+    eri_digest_quartet<1>(g, q, 0, g.blocks + g.offsets[q]);
+  }
+}
+
+__global__ void __launch_bounds__(128) eri_digest_warp_kernel(const EriDigestArgs g) {
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (w < g.nlist) {
+    const int64_t q = g.list[w];
+    eri_digest_quartet<32>(g, q, threadIdx.x & 31, g.blocks + g.offsets[q]);
+  }
+}
+
+// small = 1: one thread per quartet of the list (32 per warp), else one warp
+// per quartet
+extern "C" cudaError_t eri_digest_launch(const EriDigestArgs* g, int small, cudaStream_t stream) {
+  if (g->nlist == 0) return cudaSuccess;
+  const int64_t grid = small ? (g->nlist + 127) / 128 : (g->nlist + 3) / 4;
+  if (small)
+    eri_digest_small_kernel<<<(unsigned)grid, 128, 0, stream>>>(*g);
+  else
+    eri_digest_warp_kernel<<<(unsigned)grid, 128, 0, stream>>>(*g);
   return cudaGetLastError();
 }

@@ -1172,8 +1172,8 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       nab[q] = nfun(shells[s4[0]].l, cart) * nfun(shells[s4[1]].l, cart);
     }
     if (diag || opts.digest) {
-      std::vector<int64_t> offs(plan->offsets.begin(), plan->offsets.end() - 1);
-      if ((rc = plan->d_offsets.upload(offs, "offsets"))) return rc;
+      // nq + 1 entries: block starts and the total
+      if ((rc = plan->d_offsets.upload(plan->offsets, "offsets"))) return rc;
     }
     if (diag) {
       plan->nab = nab;

@@ -122,10 +122,12 @@ class Server:
     # -- one request --------------------------------------------------------
     def _build(self, req, stream):
         mol = self.molecules[req.mol]
+        # one stream per plan: requests already overlap across slots
         if self.fp32_below is None:
-            return eri.Plan(None, req.quartets, mol=mol.mol, stream=stream)
+            return eri.Plan(None, req.quartets, mol=mol.mol, stream=stream, streams=1)
         qb = self.bounds(mol, req.quartets)
-        return eri.Plan(None, req.quartets, qbound=qb, fp32_below=self.fp32_below, mol=mol.mol, stream=stream)
+        return eri.Plan(None, req.quartets, qbound=qb, fp32_below=self.fp32_below, mol=mol.mol, stream=stream,
+                        streams=1)
 
     def run_alone(self, req):
         """The request evaluated by itself (plain plan, default stream

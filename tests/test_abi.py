@@ -66,3 +66,13 @@ def test_argument_errors_without_gpu():
     p = eri.Plan(basis, np.zeros((0, 4), dtype=np.int32))
     assert p.output_count == 0
     p.close()
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """The binding has no CPU fallback: without the built library it raises."""
+    import importlib
+    from paper_2605_10312_gb300 import eri
+    monkeypatch.setattr(eri, "_lib", None)
+    with pytest.raises(RuntimeError):
+        eri.library(str(tmp_path / "liberi.so"))
+    importlib.reload(eri)

@@ -139,6 +139,22 @@ def test_coop_program_matches_oracle(ls, T, ilp):
     assert within(got, ref.reshape(q.shape[0], -1)).all()
 
 
+@pytest.mark.parametrize("T,ilp,k", [(32, 2, 4), (64, 2, 2), (32, 4, 3)])
+@pytest.mark.parametrize("ls", [(2, 2, 1, 1), (3, 1, 2, 0)])
+def test_coop_multistep_waves_match_oracle(ls, T, ilp, k):
+    """Waves of several steps (no barrier between the steps of a wave) keep
+    the program exact: nodes of a wave are independent and a slot is reused
+    only after the wave of its last reader."""
+    prog = program.make(*ls)
+    cp = coop.build(prog, T, ilp, k)
+    assert int(cp.steps1.max()) > 1
+    assert (int(cp.steps1.sum()) + coop.PREFETCH_STEPS) * T * ilp == cp.ph1.shape[0]
+    basis, q = synth.class_sweep(ls, 3, kset=(1, 2), seed=17, box_angstrom=3.0, exp_range=(0.1, 30))
+    ref, _ = blocks(basis, q)
+    got = run_coop(cp, prog, basis, q)
+    assert within(got, ref.reshape(q.shape[0], -1)).all()
+
+
 def test_wave_schedule_respects_dependencies_and_width():
     g = vrr.build(2, 2, 2, 1)
     order = vrr.schedule(g)
