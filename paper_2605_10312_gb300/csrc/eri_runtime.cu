@@ -334,6 +334,66 @@ struct DevPairIn {
   int32_t pad;
 };
 
+// uint64 -> int32 hash map with open addressing (linear probing): the plan's
+// pair, split, alias and signature tables see one lookup per quartet part.
+class FlatMap {
+ public:
+  explicit FlatMap(size_t expect = 16) { rehash(cap_for(expect)); }
+  // index of key, inserting make() when absent
+  template <typename Make>
+  int32_t get_or_insert(uint64_t key, Make make) {
+    if (2 * (size_ + 1) > keys_.size()) rehash(keys_.size() * 2);
+    size_t i = slot(key);
+    while (keys_[i] != kEmpty) {
+      if (keys_[i] == key) return vals_[i];
+      i = (i + 1) & (keys_.size() - 1);
+    }
+    const int32_t v = make();
+    keys_[i] = key;
+    vals_[i] = v;
+    ++size_;
+    return v;
+  }
+  // value of key, or -1
+  int32_t find(uint64_t key) const {
+    size_t i = slot(key);
+    while (keys_[i] != kEmpty) {
+      if (keys_[i] == key) return vals_[i];
+      i = (i + 1) & (keys_.size() - 1);
+    }
+    return -1;
+  }
+
+ private:
+  static constexpr uint64_t kEmpty = ~(uint64_t)0;
+  std::vector<uint64_t> keys_;
+  std::vector<int32_t> vals_;
+  size_t size_ = 0;
+  static size_t cap_for(size_t n) {
+    size_t c = 16;
+    while (c < 2 * n) c <<= 1;
+    return c;
+  }
+  size_t slot(uint64_t k) const {
+    k += 0x9e3779b97f4a7c15ull;  // splitmix64 finaliser
+    k = (k ^ (k >> 30)) * 0xbf58476d1ce4e5b9ull;
+    k = (k ^ (k >> 27)) * 0x94d049bb133111ebull;
+    k ^= k >> 31;
+    return (size_t)k & (keys_.size() - 1);
+  }
+  void rehash(size_t cap) {
+    std::vector<uint64_t> ok;
+    std::vector<int32_t> ov;
+    ok.swap(keys_);
+    ov.swap(vals_);
+    keys_.assign(cap, kEmpty);
+    vals_.assign(cap, 0);
+    size_ = 0;
+    for (size_t i = 0; i < ok.size(); ++i)
+      if (ok[i] != kEmpty) get_or_insert(ok[i], [&] { return ov[i]; });
+  }
+};
+
 // An oriented (partial) shell pair of a quartet: the pair record `pair`
 // recurs on shell `center`, with `nprim` primitive pairs.
 struct PairPart {
@@ -357,15 +417,17 @@ struct PairBuilder {
   const eri_basis* basis;
   const std::vector<double>* maxexp;
   int orientation;
-  std::unordered_map<uint64_t, int> pair_id;
+  FlatMap pair_id;
   std::vector<DevPairIn> pin;
   std::vector<uint32_t> plist;
   int64_t pprim = 0;
 
   int get_pair(int a, int b, int kind) {
-    uint64_t key = ((uint64_t)(uint32_t)a << 34) | ((uint64_t)(uint32_t)b << 2) | (uint64_t)kind;
-    auto it = pair_id.find(key);
-    if (it != pair_id.end()) return it->second;
+    const uint64_t key = ((uint64_t)(uint32_t)a << 34) | ((uint64_t)(uint32_t)b << 2) | (uint64_t)kind;
+    return pair_id.get_or_insert(key, [&] { return make_pair(a, b, kind); });
+  }
+
+  int make_pair(int a, int b, int kind) {
     int id = (int)pin.size();
     DevPairIn d{a, b, (int32_t)pprim, -1, 0, 0};
     if (kind == 0) {
@@ -381,7 +443,6 @@ struct PairBuilder {
       pprim += d.nlist;
     }
     pin.push_back(d);
-    pair_id.emplace(key, id);
     return id;
   }
 
@@ -571,7 +632,7 @@ struct eri_mol_s {
   eri_basis view;                 // the vectors above as an eri_basis
   int nshell = 0;
   int orientation = 0;
-  PairBuilder pb{nullptr, nullptr, nullptr, 0, {}, {}, {}, 0};
+  PairBuilder pb{nullptr, nullptr, nullptr, 0, FlatMap(), {}, {}, 0};
   std::vector<SplitRes> splits;   // per shell pair a >= b, at a (a + 1) / 2 + b
   int npair = 0;                  // oriented partial pairs (records)
   DevBuf<DevShell> shells_d;
@@ -703,7 +764,7 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   // primitive's centre (a contracted pair splits into at most two oriented
   // partial pairs), which keeps FP64 HRR cancellation bounded; options: the
   // whole pair on the shell with the largest exponent, or on the higher l.
-  PairBuilder pb{shells, basis, &maxexp, opts.orientation, {}, {}, {}, 0};
+  PairBuilder pb{shells, basis, &maxexp, opts.orientation, FlatMap(), {}, {}, 0};
   std::vector<DevPairIn>& pin = pb.pin;
   // molecule plans: alias records of chunked pairs, after the molecule's pairs
   std::vector<EriPairRec> mol_alias;
@@ -725,11 +786,11 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     }
     return c == 1;
   };
-  std::unordered_map<uint64_t, int> alias_id;
+  FlatMap alias_id;
   auto get_alias = [&](int parent, int start, int count) {
     const uint64_t key = ((uint64_t)(uint32_t)parent << 32) | ((uint64_t)(uint32_t)start << 16) | (uint32_t)count;
-    auto it = alias_id.find(key);
-    if (it != alias_id.end()) return it->second;
+    const int32_t found = alias_id.find(key);
+    if (found >= 0) return (int)found;
     if (mol) {
       // a record pointing into the molecule's primitive pairs (its A - B as
       // the pair set-up kernel computes it)
@@ -742,7 +803,7 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       for (int d = 0; d < 3; ++d) r.AB[d] = A[d] - Bc[d];
       const int id = mol->npair + (int)mol_alias.size();
       mol_alias.push_back(r);
-      alias_id.emplace(key, id);
+      alias_id.get_or_insert(key, [&] { return (int32_t)id; });
       return id;
     }
     DevPairIn d = pin[parent];
@@ -751,11 +812,12 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     d.nlist = count;
     const int id = (int)pin.size();
     pin.push_back(d);
-    alias_id.emplace(key, id);
+    alias_id.get_or_insert(key, [&] { return (int32_t)id; });
     return id;
   };
   bool any_reduce = false;
-  std::unordered_map<uint64_t, SplitRes> split_cache;
+  FlatMap split_id;
+  std::vector<SplitRes> split_res;
   auto split = [&](int s0, int s1, PairPart* out) {
     if (s0 < s1) std::swap(s0, s1);
     const SplitRes* r;
@@ -763,13 +825,13 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       r = &mol->splits[(int64_t)s0 * (s0 + 1) / 2 + s1];
     } else {
       const uint64_t key = ((uint64_t)(uint32_t)s0 << 32) | (uint32_t)s1;
-      auto it = split_cache.find(key);
-      if (it == split_cache.end()) {
+      const int32_t k = split_id.get_or_insert(key, [&] {
         SplitRes x;
         x.n = pb.split(s0, s1, x.part);
-        it = split_cache.emplace(key, x).first;
-      }
-      r = &it->second;
+        split_res.push_back(x);
+        return (int32_t)split_res.size() - 1;
+      });
+      r = &split_res[k];
     }
     out[0] = r->part[0];
     out[1] = r->part[1];
@@ -875,19 +937,17 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   {
     // dense ids: used (round, class, precision) groups and (K4, kb) signatures
     std::vector<int32_t> gdense(4 * ncls * 2, -1);
-    std::unordered_map<uint64_t, int32_t> sig_id;
+    FlatMap sig_id;
     std::vector<std::pair<int64_t, int32_t>> sigs;  // (K4, kb)
     std::vector<uint32_t> key(nparts);
     for (int64_t q = 0; q < nparts; ++q) {
       const QInfo& x = qi[q];
       gdense[gid(x)] = 0;
       const uint64_t sk = ((uint64_t)(uint32_t)x.kb << 32) | (uint32_t)x.kk;
-      auto it = sig_id.find(sk);
-      if (it == sig_id.end()) {
-        it = sig_id.emplace(sk, (int32_t)sigs.size()).first;
+      key[q] = (uint32_t)sig_id.get_or_insert(sk, [&] {
         sigs.push_back({(int64_t)x.kb * x.kk, x.kb});
-      }
-      key[q] = (uint32_t)it->second;
+        return (int32_t)sigs.size() - 1;
+      });
     }
     int32_t ng = 0;
     for (int32_t& g : gdense)
