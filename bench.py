@@ -665,6 +665,47 @@ def run_water_mixed(args):
     return 0
 
 
+def run_per_k(args):
+    """Per class and fixed contraction depth K in {1, 3, 6} (all four shells
+    the same K): quartets/s and FP64 fraction, L2 flushed between repeats."""
+    import torch
+    from paper_2605_10312_gb300 import eri
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # quartets per run: about half a second of work at the measured rates
+    counts = {1: {1: 2_000_000, 3: 400_000, 6: 40_000}, 2: {1: 1_000_000, 3: 200_000, 6: 20_000},
+              3: {1: 200_000, 3: 20_000, 6: 2_000}, 4: {1: 40_000, 3: 4_000, 6: 400}}
+    rows = {}
+    for ls, _ in SWEEP:
+        for K in (1, 3, 6):
+            n = max(1, int(counts[ls[0]][K] * SCALE))
+            basis, q = synth.class_sweep(ls, n, kset=(K,), seed=SEED + 10 * ls[0] + K)
+            p = eri.Plan(basis, q)
+            out = torch.empty(p.output_count, dtype=torch.float64, device="cuda")
+            ms = []
+            for it in range(args.warmup + args.steps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                p.compute(out, stream)
+                e1.record(stream)
+                e1.synchronize()
+                if it >= args.warmup:
+                    ms.append(e0.elapsed_time(e1))
+            t = statistics.mean(ms)
+            fl = p.stats()["flops"]
+            rows["{}_K{}".format("".join("spdfg"[x] for x in ls), K)] = {
+                "quartets": n, "ms": t, "quartets_per_s": n / (t * 1e-3),
+                "fp64_frac_of_peak": fl / (t * 1e-3) / 1e12 / fp64_peak_tflops(),
+                "flops_per_quartet": fl / n}
+            p.close()
+            del out
+    print(json.dumps({"workload": "per-class sweep at fixed K (all four shells), 10 Angstrom box",
+                      "l2": "flushed between repeats", "steps": args.steps, "per_class_k": rows}))
+    return 0
+
+
 def run_serve(args):
     """Serving loop with continuous batching: a pool of seeded water clusters
     (dz layout, 4-66 waters) registered on the device, requests of a seeded
@@ -721,7 +762,7 @@ def main():
     ap.add_argument("--classes", default="", help="comma-separated subset, e.g. gggg (profiling runs)")
     ap.add_argument("--scale", type=float, default=1.0, help="multiply the quartet counts (profiling runs)")
     ap.add_argument("--ablation", action="store_true", help="axis / DSA / spherical / tier ablations instead")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "water", "serve"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "water", "serve", "per-k"])
     ap.add_argument("--rate", type=float, default=50.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per phase")
     ap.add_argument("--molecules", type=int, default=8, help="serve: molecules in the pool")
@@ -747,6 +788,8 @@ def main():
         return run_water_mixed(args) if args.fp32_below is not None else run_water(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "per-k":
+        return run_per_k(args)
     return run_ours(args)
 
 

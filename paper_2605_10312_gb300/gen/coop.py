@@ -123,9 +123,13 @@ class CoopProgram:
 PREFETCH_STEPS = 2  # no-op steps after the last wave: the executor loads ahead
 
 
-def _pack(waves, rows_of, T, nop, ilp):
+def _pack(waves, rows_of, T, nop, ilp, shape_of=None):
     """A step is ilp * T descriptors: lane l takes descriptors ilp*l .. ilp*l +
-    ilp - 1 of the step, so a wave of n nodes spreads over the lanes first."""
+    ilp - 1 of the step, so a wave of n nodes spreads over the lanes first.
+    shape_of(descriptor): the nodes of a wave are independent, so they are
+    placed in order of their shape (which optional terms they evaluate):
+    the 32 lanes of a warp then mostly share one shape, and a warp issues the
+    optional FP64 instructions only when some lane needs them."""
     ILP = ilp
     W = ILP * T
     steps = []
@@ -134,10 +138,13 @@ def _pack(waves, rows_of, T, nop, ilp):
         st = (len(vs) + W - 1) // W
         steps.append(st)
         block = np.tile(nop, (st * W, 1))
-        for k, v in enumerate(vs):
+        rows = [rows_of(v) for v in vs]
+        if shape_of is not None:
+            rows.sort(key=shape_of)   # stable: DSA order within a shape
+        for k, row in enumerate(rows):
             s, r = divmod(k, W)
             lane, j = r % T, r // T       # fill every lane's first node before second nodes
-            block[s * W + lane * ILP + j] = rows_of(v)
+            block[s * W + lane * ILP + j] = row
         out.append(block)
     out.append(np.tile(nop, (PREFETCH_STEPS * W, 1)))
     arr = np.concatenate(out)
@@ -188,7 +195,12 @@ def build(prog, T=128, ilp=ILP, wave_steps=1):
         return np.array([dst | ((h + 1) << 16 if h is not None else 0), src[0] | (src[1] << 16),
                          src[2] | (src[3] << 16), src[4] | (meta << 16)], dtype=np.uint32)
 
-    ph1, steps1 = _pack(waves1, row1, T, NOP1, ilp)
+    def shape1(row):
+        # base node; c1/c2 pair present; c3 term present
+        meta = int(row[3]) >> 16
+        return ((meta >> 14) & 1, ((meta >> 4) & 31) > 0, ((meta >> 9) & 15) > 0)
+
+    ph1, steps1 = _pack(waves1, row1, T, NOP1, ilp, shape1)
 
     # ---------------- Phase 2: graph of operations and output stores
     p2 = prog.p2
@@ -282,7 +294,11 @@ def build(prog, T=128, ilp=ILP, wave_steps=1):
         return np.array([2 | (oid(val_node[val]) << 16), k,
                          int(i[0]) | (int(i[1]) << 8) | (int(i[2]) << 16) | (int(i[3]) << 24), 0], dtype=np.uint32)
 
-    ph2, steps2 = _pack(waves2, row2, T, NOP2, ilp)
+    def shape2(row):
+        # kind (HRR, linear combination, store) and number of terms
+        return (int(row[0]) & 3, (int(row[0]) >> 2) & 7)
+
+    ph2, steps2 = _pack(waves2, row2, T, NOP2, ilp, shape2)
     nslot = max(int(nslot1), int(nslot2))
     if nslot >= 0xFFFF or nh + nslot > MAX_ID:
         raise ValueError("class {} needs {} ids".format(prog.ls, nh + nslot))
