@@ -31,6 +31,8 @@ struct EriCoopArgs {
   int32_t h_in_smem;
   int32_t nteams;                     // teams in the grid
   int32_t batch;                      // coefficient rows per team (1..ERI_COOP_BATCH)
+  int32_t single;                     // every quartet has one primitive quartet: the rows of
+                                      // `batch` consecutive quartets of a team are computed together
 };
 
 __device__ __forceinline__ double eri_coop_pick8(int k, const double (&t)[8]) {
@@ -230,18 +232,31 @@ __global__ void __launch_bounds__(T > 128 ? T : 128, T > 128 ? (ILP == 4 ? 1 : 2
   const unsigned nh = (unsigned)p.nh;
   // Phase-2 operand id -> address: H below nh, value slots above
   auto ptr = [&](unsigned id) -> R* { return id < nh ? Hs + id : V + (id - nh); };
+  // single: every quartet of the launch has one primitive quartet; a team
+  // then computes the coefficient rows of its next p.batch quartets at once
+  // (one lane each) rather than one row per quartet on one lane
+  const bool single = p.single != 0;
+  int gi = 0;  // single: position of quartet q in its group of rows
   for (int q = team; q < a.nq; q += p.nteams) {
     const EriQuartetRec qr = a.quartets[q];
     const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];
     const bool acc = ERI_ACCUMULATE(qr.bra);
     const bool red = ERI_REDUCE(qr.bra);
     const EriPairRec ket = a.pairs[qr.ket];
+    if (single && gi == 0) {
+      const int qi = q + l * p.nteams;
+      if (l < p.batch && qi < a.nq) {
+        const EriQuartetRec r = a.quartets[qi];
+        eri_coop_row(a.pprims[a.pairs[ERI_PAIR_INDEX(r.bra)].prim_off], a.pprims[a.pairs[r.ket].prim_off], p.L,
+                     a.boys_tab, rows + l * ERI_COOP_NC);
+      }
+    }
     for (int h = l; h < p.nh; h += T) Hs[h] = (R)0;
     const int kk = ket.nprim;
     const int k4 = bra.nprim * kk;
     for (int b0 = 0; b0 < k4; b0 += p.batch) {
       const int nb = min(p.batch, k4 - b0);
-      if (l < nb) {
+      if (!single && l < nb) {
         const int pidx = b0 + l;
         const int i = pidx / kk, j = pidx - (pidx / kk) * kk;
         eri_coop_row(a.pprims[bra.prim_off + i], a.pprims[ket.prim_off + j], p.L, a.boys_tab,
@@ -249,7 +264,7 @@ __global__ void __launch_bounds__(T > 128 ? T : 128, T > 128 ? (ILP == 4 ? 1 : 2
       }
       eri_team_sync<T>();
       for (int pi = 0; pi < nb; ++pi) {
-        const R* const row = rows + pi * ERI_COOP_NC;
+        const R* const row = rows + (single ? gi : pi) * ERI_COOP_NC;
         // a step gives each lane ILP descriptors (independent nodes of the
         // same wave); they are loaded two steps ahead -- the stream ends in
         // two no-op steps -- so the L2 latency overlaps the previous step
@@ -319,6 +334,7 @@ __global__ void __launch_bounds__(T > 128 ? T : 128, T > 128 ? (ILP == 4 ? 1 : 2
       }
       eri_team_sync<T>();
     }
+    if (single && ++gi == p.batch) gi = 0;
   }
 }
 

@@ -63,6 +63,7 @@ struct EriCoopArgs {
   int32_t h_in_smem;
   int32_t nteams;
   int32_t batch;
+  int32_t single;
 };
 extern "C" cudaError_t eri_coop_launch(int T, int ilp, int fp32, const EriLaunchArgs* a, const EriCoopArgs* p,
                                        int grid, int block, size_t smem, cudaStream_t stream);
@@ -556,6 +557,7 @@ struct Bucket {
   CoopProg* coop = nullptr;      // team-cooperative tier
   int smem_slots = 0, h_in_smem = 0, nteams = 0;
   int batch = 0;                 // cooperative tier: coefficient rows per team
+  int single = 0;                // cooperative tier: every part has one primitive quartet
   int fp32 = 0;                  // recurrences in FP32 (quartets with a small Schwarz bound)
   int round = 0;                 // part round: buckets of a round are independent
   int lane = 0;                  // stream of its round (0 = the caller's stream)
@@ -1046,12 +1048,14 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     const int g = tier == TIER_COOP ? 1 : group_at(i);
     // K4 of the bucket's first (deepest) part; cooperative buckets split at
     // the shallow-contraction boundary
+    // (deep > kShallowK4 >= shallow > 1 = single primitive quartet)
     const int64_t k4_first = (int64_t)pk[i].kb * pk[i].kk;
+    auto coop_cat = [](int64_t k4) { return k4 == 1 ? 2 : (k4 <= kShallowK4 ? 1 : 0); };
     const bool shallow = tier == TIER_COOP && k4_first <= kShallowK4;
     int64_t j = i;
     double kprim = 0;
     while (j < nparts && pk[j].cls == c && pk[j].round == round && pk[j].prec == prec &&
-           (tier == TIER_COOP ? ((int64_t)pk[j].kb * pk[j].kk <= kShallowK4) == shallow
+           (tier == TIER_COOP ? coop_cat((int64_t)pk[j].kb * pk[j].kk) == coop_cat(k4_first)
                               : group_at(j) == g)) {
       kprim += (double)pk[j].kb * pk[j].kk;
       ++j;
@@ -1083,7 +1087,11 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
         if (sit != L.coops_shallow.end()) cp = sit->second.get();
       }
       b.coop = cp;
-      b.batch = (int)std::min<int64_t>(eri_coop_max_batch(), std::max<int64_t>(1, k4_first));
+      // single-primitive parts: a team computes the rows of kShallowK4
+      // consecutive quartets at once
+      b.single = k4_first == 1 ? 1 : 0;
+      b.batch = b.single ? kShallowK4
+                         : (int)std::min<int64_t>(eri_coop_max_batch(), std::max<int64_t>(1, k4_first));
       const size_t smem_sm = L.smem_per_sm, reserve = 1024;
       int best_warps = -1;
       const size_t rows = eri_coop_row_elems() * (size_t)b.batch;
@@ -1504,6 +1512,7 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
       p.h_in_smem = b.h_in_smem;
       p.nteams = b.nteams;
       p.batch = b.batch;
+      p.single = b.single;
       CUDA_OR(eri_coop_launch(cp->T, cp->ilp, b.fp32, &a, &p, b.grid, b.block, b.smem, cur),
               "cooperative launch");
     } else {
