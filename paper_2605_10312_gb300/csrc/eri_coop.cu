@@ -1,7 +1,7 @@
 // Team-cooperative executor: the tier for large classes (FusionRCG Sec.
 // III-C, Regime II, re-derived for GB300).
 //
-// A team of T lanes (T = 32, 64 or 128; one to four warps) evaluates one
+// A team of T lanes (T = 32 to 512; one to sixteen warps) evaluates one
 // shell quartet: it walks the quartet's primitive quartets one at a time
 // (Algorithm 2's loops, accumulate-then-transform), and for each it runs the
 // Phase-1 graph wave by wave -- every wave is a set of up to T mutually
@@ -216,9 +216,12 @@ __device__ __forceinline__ void eri_coop_exec2(const uint4& d, const R (&v)[4], 
 // R: value type of the recurrences, the contraction sums H, HRR and the
 // transform -- double, or float for the reduced-precision form (coefficient
 // rows and the Boys function are still formed in FP64; stores are FP64).
-// Blocks are 128 threads (teams of up to 128 lanes) or one 256-lane team.
+// Blocks are 128 threads (teams of up to 128 lanes) or one team of 256 or
+// 512 lanes; every shape keeps the 128 registers per thread that two nodes
+// per lane need (four nodes per lane: 255, at most 256 threads per SM).
 template <typename R, int T, bool HSM, int ILP>
-__global__ void __launch_bounds__(T > 128 ? T : 128, T > 128 ? (ILP == 4 ? 1 : 2) : (ILP == 4 ? 2 : 4))
+__global__ void __launch_bounds__(T > 128 ? T : 128,
+                                  T > 256 ? 1 : T > 128 ? (ILP == 4 ? 1 : 2) : (ILP == 4 ? 2 : 4))
     eri_coop_kernel(const EriLaunchArgs a, const EriCoopArgs p) {
   extern __shared__ double eri_coop_smem[];
   const int tb = threadIdx.x / T;           // team within the block
@@ -343,17 +346,22 @@ __global__ void __launch_bounds__(T > 128 ? T : 128, T > 128 ? (ILP == 4 ? 1 : 2
       (const void*)eri_coop_kernel<R, 64, true, I>, (const void*)eri_coop_kernel<R, 64, false, I>, \
       (const void*)eri_coop_kernel<R, 128, true, I>, (const void*)eri_coop_kernel<R, 128, false, I>, \
       (const void*)eri_coop_kernel<R, 256, true, I>, (const void*)eri_coop_kernel<R, 256, false, I>
-#define ERI_COOP_FNS(R) ERI_COOP_FNS_T(R, 2), ERI_COOP_FNS_T(R, 4)
+// 512-lane teams exist with two nodes per lane only (four would need more
+// registers than a 512-thread block can hold)
+#define ERI_COOP_FNS(R)                                                                                     \
+  ERI_COOP_FNS_T(R, 2), (const void*)eri_coop_kernel<R, 512, true, 2>, (const void*)eri_coop_kernel<R, 512, false, 2>, \
+      ERI_COOP_FNS_T(R, 4), nullptr, nullptr
 
-// every instantiation, indexed [fp32][ilp 4][T 32/64/128/256][H not in shared memory]
+// every instantiation, indexed [fp32][ilp 4][T 32/64/128/256/512][H not in shared memory]
 static const void* const eri_coop_fns[] = {ERI_COOP_FNS(double), ERI_COOP_FNS(float)};
 
 extern "C" cudaError_t eri_coop_launch(int T, int ilp, int fp32, const EriLaunchArgs* a, const EriCoopArgs* p,
                                        int grid, int block, size_t smem, cudaStream_t stream) {
-  const int ti = T == 32 ? 0 : T == 64 ? 1 : T == 128 ? 2 : T == 256 ? 3 : -1;
+  const int ti = T == 32 ? 0 : T == 64 ? 1 : T == 128 ? 2 : T == 256 ? 3 : T == 512 ? 4 : -1;
   if (ti < 0 || (ilp != 2 && ilp != 4)) return cudaErrorInvalidValue;
   if (block != (T > 128 ? T : 128) && !(T <= 128 && block % T == 0 && block <= 128)) return cudaErrorInvalidValue;
-  const int idx = (fp32 ? 16 : 0) + (ilp == 4 ? 8 : 0) + 2 * ti + (p->h_in_smem ? 0 : 1);
+  const int idx = (fp32 ? 20 : 0) + (ilp == 4 ? 10 : 0) + 2 * ti + (p->h_in_smem ? 0 : 1);
+  if (eri_coop_fns[idx] == nullptr) return cudaErrorInvalidValue;
   EriLaunchArgs aa = *a;
   EriCoopArgs pp = *p;
   void* args[] = {&aa, &pp};
@@ -366,6 +374,7 @@ extern "C" int eri_coop_max_batch(void) { return ERI_COOP_BATCH; }
 
 extern "C" cudaError_t eri_coop_set_smem(size_t bytes) {
   for (const void* f : eri_coop_fns) {
+    if (f == nullptr) continue;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
   }

@@ -339,25 +339,34 @@ def _score(cp, rows):
 
 
 WIDE_SHAPES = ((256, 2), (256, 4))
+# sixteen warps on one live set: 512 lanes, two nodes per lane (the register
+# file holds 128 registers for each of 512 threads)
+WIDEST_SHAPE = (512, 2)
+WAVE_NODES_MAX = 2048   # nodes in a multi-step wave of a 512-lane team
 
 
-def _teams_per_sm(cp, rows):
+def _teams_per_sm(cp, rows, h_in_smem=True):
     vals = cp.nslot * 8 + rows * ROW_BYTES
     with_h = vals + cp.nh * 8
-    per_team = with_h if with_h <= 227 * 1024 else vals
+    per_team = with_h if h_in_smem and with_h <= 227 * 1024 else vals
     return SMEM_PER_SM // (per_team + 1024)
 
 
 def _wide_waves(prog, cp, rows):
-    """A 256-lane team is alone on its SM and meets a barrier after every
-    step; waves of up to four steps of independent nodes cut the barriers
-    about fourfold (measured: (gg|gg) 0.45 -> 0.52 of the FP64 rate) at the
-    cost of a larger live set.  Take the widest of 4 and 2 steps that keeps
-    the teams per SM; narrower teams keep one step per wave (measured: the
-    larger live set costs them residency or lane efficiency)."""
+    """A team of 256 or more lanes is alone on its SM and meets a barrier
+    after every step; waves of up to four steps of independent nodes cut the
+    barriers about fourfold (measured: (gg|gg) 0.45 -> 0.52 of the FP64 rate
+    with 256 lanes) at the cost of a larger live set.  Take the widest of 4
+    and 2 steps that keeps the teams per SM, with at most WAVE_NODES_MAX nodes
+    in a wave (512 lanes x 2 nodes x 2 steps: the live set and the barrier
+    count of the 256-lane, 4-step waves); narrower teams keep one step per
+    wave (measured: the larger live set costs them residency or lane
+    efficiency)."""
     if cp is None or cp.T < 256:
         return cp
     for k in (4, 2):
+        if cp.T == 512 and cp.T * cp.ilp * k > WAVE_NODES_MAX:
+            continue
         ck = build(prog, cp.T, cp.ilp, k)
         if _score(ck, rows) is not None and _teams_per_sm(ck, rows) >= _teams_per_sm(cp, rows):
             return ck
@@ -369,10 +378,21 @@ def choose_both(prog, shapes=SHAPES):
     team holds DEEP_ROWS coefficient rows, and when it holds SHALLOW_ROWS
     (shallow contractions: fewer rows leave shared memory for more teams).
     Classes whose 128-lane team is alone on an SM also try one 256-lane team
-    (eight warps on the same shared-memory live set)."""
+    (eight warps on the same shared-memory live set), and those whose
+    256-lane team is alone even with H in global memory one 512-lane team
+    (sixteen warps)."""
     built = [build(prog, T, ilp) for T, ilp in shapes]
     if any(cp.T == 128 and _teams_per_sm(cp, DEEP_ROWS) <= 1 for cp in built):
         built += [build(prog, T, ilp) for T, ilp in WIDE_SHAPES]
+        # a 512-lane team only where a 256-lane team is alone on its SM even
+        # with H in global memory (the runtime then holds eight warps per SM,
+        # the 512-lane team sixteen).  Measured with K per shell from
+        # {1, 3, 6}: (gg|gg) 0.546 -> 0.602 of the FP64 rate, (gg|gf) 0.521
+        # -> 0.575; where two 256-lane teams (or three 128-lane ones) fit, the
+        # wider team only costs lane efficiency ((fg|dg) 0.638 -> 0.466).
+        if any(cp.T == 256 and cp.ilp == 2 and _teams_per_sm(cp, DEEP_ROWS, h_in_smem=False) <= 1
+               for cp in built):
+            built.append(build(prog, *WIDEST_SHAPE))
     out = []
     for rows in (DEEP_ROWS, SHALLOW_ROWS):
         scored = [(sc, k) for k, cp in enumerate(built) for sc in [_score(cp, rows)] if sc is not None]
