@@ -4,8 +4,8 @@
 // A team of T lanes (T = 32 to 512; one to sixteen warps) evaluates one
 // shell quartet: it walks the quartet's primitive quartets one at a time
 // (Algorithm 2's loops, accumulate-then-transform), and for each it runs the
-// Phase-1 graph wave by wave -- every wave is a set of up to T mutually
-// independent nodes in DSA order (Eq. 7), lane l takes node l -- with a team
+// Phase-1 graph wave by wave -- a wave is a set of mutually independent nodes
+// in DSA order (Eq. 7), cut into steps of ILP nodes per lane -- with a team
 // barrier between waves.  Phase 2 (HRR + stepwise transform, Eq. 16) and the
 // output stores run the same way once per shell quartet.
 //

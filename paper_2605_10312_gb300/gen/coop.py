@@ -1,11 +1,12 @@
 """Team-cooperative form of a class program (the tier for large classes).
 
-A team of T lanes (one to four warps) evaluates ONE primitive quartet at a
-time: the Phase-1 graph is cut into waves of at most T mutually independent
-nodes, taken in DSA order (FusionRCG Eq. 7) by a bounded-width list
-scheduler, and lane l evaluates node l of each wave; a team barrier separates
-waves.  Phase 2 is scheduled the same way, with its operations in their
-liveness-friendly build order as priority.  Values live in one slot space
+A team of T lanes (one to sixteen warps) evaluates ONE primitive quartet at a
+time: the Phase-1 graph is cut into waves of mutually independent nodes,
+taken in DSA order (FusionRCG Eq. 7) by a bounded-width list scheduler; a
+wave is one or more steps of ilp nodes per lane (several steps only for
+teams of 256 or more lanes), and a team barrier separates waves.  Phase 2
+is scheduled the same way, with its operations in their liveness-friendly
+build order as priority.  Values live in one slot space
 per team (not per lane), so a class whose sequential PeakLive (Eq. 4) is
 thousands of values still fits in shared memory; the accumulator bank H is
 addressed separately (shared memory when it fits, else a team-private global
