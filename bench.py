@@ -566,8 +566,8 @@ def run_water_jk(args, basis, plan, out, stream):
 
 
 def hbm_peak_gbs():
-    """Measured HBM copy bandwidth of the GB300s (MEASURED_PEAKS.json),
-    else the recipe's fallback."""
+    """Measured HBM copy bandwidth of the GB300 (MEASURED_PEAKS.json), else
+    6.8 TB/s, an earlier copy measurement on a GB300."""
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except (OSError, ValueError, KeyError):

@@ -217,11 +217,12 @@ int eri_digest_jk(eri_plan_t* plan, const double* blocks, const double* density,
 int eri_compute_jk(eri_plan_t* plan, const double* density, int32_t nbf, double* J, double* K, void* stream);
 
 /* Evaluate like eri_compute without allocating: for callers that may not
- * allocate device memory while they evaluate (stream capture without
- * graph-safe allocation, or a device-memory budget owned by another
- * framework).  The paper has no counterpart; this is a deployment entry
- * point.  The plan must have been built with opts.tier = 3 (global-scratch
- * program tier); its kernels then take their per-thread value slots from a
+ * allocate device memory while they evaluate (a device-memory budget owned
+ * by another framework, or a latency-critical loop that must not enter the
+ * allocator, which can synchronise the device).  The paper has no
+ * counterpart; this is a deployment entry point.  The plan must have been
+ * built with opts.tier = 3 (global-scratch program tier); its kernels then
+ * take their per-thread value slots from a
  * fixed 64 MiB device array that the library holds on every GPU that loads it
  * until the process exits, so the call itself performs no cudaMalloc,
  * cudaFree or other allocation.  Inputs are the plan's device data, out is

@@ -1658,10 +1658,11 @@ extern "C" int eri_plan_destroy(eri_plan_t* plan) {
 // ---------------------------------------------------------------------------
 // Allocation-free evaluation (eri_compute_fixed_scratch)
 //
-// Some callers must not allocate device memory when they evaluate: code that
-// runs while a stream is being captured into a CUDA graph without
-// graph-safe allocation, or code whose device memory is budgeted and owned by
-// another framework.  For them the global-scratch program tier can take its
+// Some callers must not allocate device memory when they evaluate: code whose
+// device memory is budgeted and owned by another framework (an application
+// that hands out all of the device memory up front), or a latency-critical
+// loop that must not enter the allocator (cudaMalloc and cudaFree can
+// synchronise the device).  For them the global-scratch program tier can take its
 // per-thread value slots from this fixed array instead of the plan's
 // scratch.  The array is a file-scope device variable: every GPU that loads
 // the library holds its 64 MiB until the process exits.

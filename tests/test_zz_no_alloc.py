@@ -1,11 +1,12 @@
 """The allocation-free entry point eri_compute_fixed_scratch.
 
-Callers that cannot allocate device memory while they evaluate (stream
-capture without graph-safe allocation, or a device-memory budget owned by
-another framework) use this variant of the global-scratch executor, whose
-per-thread value slots live in a fixed device array the library holds.  It
-must give the same integrals as eri_compute on the same plan, on two calls in
-a row (the array keeps the previous call's contents)."""
+Callers that cannot allocate device memory while they evaluate (a
+device-memory budget owned by another framework, or a latency-critical loop
+that must not enter the allocator, which can synchronise the device) use this
+variant of the global-scratch executor, whose per-thread value slots live in a
+fixed device array the library holds.  It must give the same integrals as
+eri_compute on the same plan, on two calls in a row (the array keeps the
+previous call's contents)."""
 import numpy as np
 import pytest
 
