@@ -155,6 +155,59 @@ def test_coop_multistep_waves_match_oracle(ls, T, ilp, k):
     assert within(got, ref.reshape(q.shape[0], -1)).all()
 
 
+@pytest.mark.parametrize("ls", [(2, 2, 1, 1), (3, 1, 2, 0)])
+def test_coop_512_lane_program_matches_oracle(ls):
+    """The widest team (512 lanes, two nodes per lane, waves of up to two
+    steps of 1024 nodes) is the same program form: every wave fits in a few
+    lane slots of one step, most lanes are no-ops, and the result is exact."""
+    prog = program.make(*ls)
+    cp = coop.build(prog, *coop.WIDEST_SHAPE, 2)
+    assert cp.T * cp.ilp * 2 <= coop.WAVE_NODES_MAX
+    assert (int(cp.steps1.sum()) + coop.PREFETCH_STEPS) * cp.T * cp.ilp == cp.ph1.shape[0]
+    basis, q = synth.class_sweep(ls, 3, kset=(1, 2), seed=19, box_angstrom=3.0, exp_range=(0.1, 30))
+    ref, _ = blocks(basis, q)
+    got = run_coop(cp, prog, basis, q)
+    assert within(got, ref.reshape(q.shape[0], -1)).all()
+
+
+class _FakeProg:
+    """Stands in for a class program in the shape-selection test: a live
+    set of `slots` values at a 64-node wave, growing with the wave width."""
+
+    def __init__(self, slots, nh):
+        self.slots, self.nh = slots, nh
+
+
+def test_widest_team_only_where_a_256_lane_team_is_alone(monkeypatch):
+    """choose_both builds the 512-lane shape only when a 256-lane team holds
+    its SM alone even with H in global memory (the runtime then keeps eight
+    warps per SM; the wider team keeps sixteen).  Where two 256-lane teams
+    fit, the wider team would only lose lane efficiency."""
+    built = []
+
+    def fake_build(prog, T, ilp, k=1):
+        built.append((T, ilp, k))
+        width = T * ilp * k
+        nslot = prog.slots + width
+        eff = 0.98 - 0.00015 * width
+        z = np.zeros((1, 4), dtype=np.uint32)
+        s = np.ones(1, dtype=np.uint32)
+        return coop.CoopProgram(T, ilp, z, s, z, s, prog.nh, nslot, 16, (9, 9, 9, 9), eff, eff)
+
+    monkeypatch.setattr(coop, "build", fake_build)
+    # (gg|gg)-sized live set: a 256-lane team is alone even without H
+    deep, shallow = coop.choose_both(_FakeProg(21000, 21025))
+    assert coop.WIDEST_SHAPE + (1,) in built
+    assert (deep.T, deep.ilp) == coop.WIDEST_SHAPE
+    # its waves hold at most WAVE_NODES_MAX nodes: two steps, never four
+    assert coop.WIDEST_SHAPE + (2,) in built and coop.WIDEST_SHAPE + (4,) not in built
+    # a live set two 256-lane teams can share (H in global memory): no 512
+    built.clear()
+    deep, shallow = coop.choose_both(_FakeProg(11000, 12000))
+    assert all(T < 512 for T, _, _ in built)
+    assert deep.T < 512 and shallow.T < 512
+
+
 def test_wave_schedule_respects_dependencies_and_width():
     g = vrr.build(2, 2, 2, 1)
     order = vrr.schedule(g)
