@@ -40,10 +40,8 @@ NOP2 = np.array([3, 0, 0, 0], dtype=np.uint32)
 MAX_ID = 65535
 
 
-def wave_schedule(parents, priority, width):
-    """Bounded-width list scheduling: each wave takes up to ``width`` ready
-    nodes with the smallest priority.  parents[v] = list of node ids."""
-    n = len(parents)
+def _consumer_lists(parents, n):
+    """Distinct-parent counts and consumer lists of a node list."""
     cons = [[] for _ in range(n)]
     npar = [0] * n
     for v, ps in enumerate(parents):
@@ -51,55 +49,95 @@ def wave_schedule(parents, priority, width):
         npar[v] = len(ps)
         for p in ps:
             cons[p].append(v)
-    ready = [(priority[v], v) for v in range(n) if npar[v] == 0]
+    return cons, npar
+
+
+def _waves(cons, npar, priority, width):
+    """Bounded-width list scheduling over consumer lists (npar is consumed):
+    each wave takes up to ``width`` ready nodes, smallest (priority, node)
+    first, in that order."""
+    ready = [(priority[v], v) for v in range(len(npar)) if npar[v] == 0]
     heapq.heapify(ready)
+    pop, push = heapq.heappop, heapq.heappush
     waves = []
     while ready:
-        cur = []
-        while ready and len(cur) < width:
-            cur.append(heapq.heappop(ready)[1])
+        cur = [pop(ready)[1] for _ in range(min(width, len(ready)))]
         for v in cur:
             for c in cons[v]:
                 npar[c] -= 1
                 if npar[c] == 0:
-                    heapq.heappush(ready, (priority[c], c))
+                    push(ready, (priority[c], c))
         waves.append(cur)
-    assert sum(len(w) for w in waves) == n, "cycle in graph"
+    assert sum(len(w) for w in waves) == len(npar), "cycle in graph"
     return waves
+
+
+def wave_schedule(parents, priority, width):
+    """Bounded-width list scheduling: each wave takes up to ``width`` ready
+    nodes with the smallest priority.  parents[v] = list of node ids."""
+    n = len(parents)
+    cons, npar = _consumer_lists(parents, n)
+    return _waves(cons, npar, [int(x) for x in priority], width)
+
+
+def _allocate(wave_of, last, needs_slot, order, first_slot=0):
+    """Slot allocation over waves for nodes taken in ``order`` (wave by wave):
+    a value written in wave b and last read in wave d keeps its slot through
+    wave d; a slot is reused only by a value born in a later wave.  Lowest
+    free slot first."""
+    n = len(wave_of)
+    slot = np.full(n, -1, dtype=np.int64)
+    free = []
+    nxt = first_slot
+    nw = int(wave_of.max()) + 1 if n else 0
+    release_at = [[] for _ in range(max(nw, int(last.max()) + 1 if n else 0) + 2)]
+    pop, push = heapq.heappop, heapq.heappush
+    cur_w = -1
+    wl = wave_of.tolist()
+    ll = last.tolist()
+    nl = needs_slot.tolist()
+    out = [-1] * n
+    for v in order:
+        w = wl[v]
+        while cur_w < w:
+            cur_w += 1
+            for s in release_at[cur_w]:
+                push(free, s)
+        if not nl[v]:
+            continue
+        if free:
+            s = pop(free)
+        else:
+            s = nxt
+            nxt += 1
+        out[v] = s
+        release_at[ll[v] + 1].append(s)
+    slot[:] = out
+    return slot, nxt - first_slot
+
+
+def _lifetimes(parents, waves, pinned_until_end=()):
+    n = len(parents)
+    wave_of = np.zeros(n, dtype=np.int64)
+    for w, vs in enumerate(waves):
+        wave_of[np.asarray(vs, dtype=np.int64)] = w
+    last = wave_of.copy()
+    src = [p for ps in parents for p in ps]
+    if src:
+        dst = np.repeat(np.arange(n, dtype=np.int64), [len(ps) for ps in parents])
+        np.maximum.at(last, np.asarray(src, dtype=np.int64), wave_of[dst])
+    for v in pinned_until_end:
+        last[v] = len(waves)
+    return wave_of, last
 
 
 def allocate_over_waves(parents, waves, needs_slot, first_slot=0, pinned_until_end=()):
     """Slots for wave-synchronous execution: a value written in wave b and
     last read in wave d keeps its slot through wave d; a slot is reused only
     by a value born in a later wave.  Lowest free slot first."""
-    n = len(parents)
-    wave_of = np.zeros(n, dtype=np.int64)
-    for w, vs in enumerate(waves):
-        for v in vs:
-            wave_of[v] = w
-    last = wave_of.copy()
-    for v, ps in enumerate(parents):
-        for p in ps:
-            last[p] = max(last[p], wave_of[v])
-    for v in pinned_until_end:
-        last[v] = len(waves)
-    slot = np.full(n, -1, dtype=np.int64)
-    free = []
-    nxt = first_slot
-    release_at = [[] for _ in range(len(waves) + 2)]
-    for w, vs in enumerate(waves):
-        for s in release_at[w]:
-            heapq.heappush(free, s)
-        for v in vs:
-            if not needs_slot[v]:
-                continue
-            if free:
-                slot[v] = heapq.heappop(free)
-            else:
-                slot[v] = nxt
-                nxt += 1
-            release_at[last[v] + 1].append(int(slot[v]))
-    return slot, nxt - first_slot
+    wave_of, last = _lifetimes(parents, waves, pinned_until_end)
+    order = [v for vs in waves for v in vs]
+    return _allocate(wave_of, last, np.asarray(needs_slot, dtype=bool), order, first_slot)
 
 
 ILP = 2  # default nodes per lane per step (independent chains per lane)
@@ -124,189 +162,236 @@ class CoopProgram:
 PREFETCH_STEPS = 2  # no-op steps after the last wave: the executor loads ahead
 
 
-def _pack(waves, rows_of, T, nop, ilp, shape_of=None):
+def _pack(waves, rows, T, nop, ilp, shape):
     """A step is ilp * T descriptors: lane l takes descriptors ilp*l .. ilp*l +
-    ilp - 1 of the step, so a wave of n nodes spreads over the lanes first.
-    shape_of(descriptor): the nodes of a wave are independent, so they are
-    placed in order of their shape (which optional terms they evaluate):
-    the 32 lanes of a warp then mostly share one shape, and a warp issues the
-    optional FP64 instructions only when some lane needs them."""
-    ILP = ilp
-    W = ILP * T
-    steps = []
-    out = []
-    for vs in waves:
-        st = (len(vs) + W - 1) // W
-        steps.append(st)
-        block = np.tile(nop, (st * W, 1))
-        rows = [rows_of(v) for v in vs]
-        if shape_of is not None:
-            rows.sort(key=shape_of)   # stable: DSA order within a shape
-        for k, row in enumerate(rows):
-            s, r = divmod(k, W)
-            lane, j = r % T, r // T       # fill every lane's first node before second nodes
-            block[s * W + lane * ILP + j] = row
-        out.append(block)
-    out.append(np.tile(nop, (PREFETCH_STEPS * W, 1)))
-    arr = np.concatenate(out)
-    return arr.astype(np.uint32), np.array(steps, dtype=np.uint32)
+    ilp - 1 of the step, so a wave of n nodes spreads over the lanes first
+    (every lane's first node before any second node).  rows[v] is node v's
+    descriptor; shape[v] a small integer naming which optional terms it
+    evaluates.  The nodes of a wave are independent, so they are placed in
+    order of their shape (stable: DSA order within a shape): the 32 lanes of
+    a warp then mostly share one shape, and a warp issues the optional FP64
+    instructions only when some lane needs them."""
+    W = ilp * T
+    sizes = np.array([len(w) for w in waves], dtype=np.int64)
+    steps = (sizes + W - 1) // W
+    total = (int(steps.sum()) + PREFETCH_STEPS) * W
+    arr = np.tile(nop, (total, 1))
+    if len(waves):
+        idx = np.concatenate([np.asarray(w, dtype=np.int64) for w in waves])
+        wave_id = np.repeat(np.arange(len(waves)), sizes)
+        idx = idx[np.lexsort((np.arange(idx.size), shape[idx], wave_id))]
+        k = np.arange(idx.size) - np.repeat(np.cumsum(sizes) - sizes, sizes)
+        s, r = np.divmod(k, W)
+        base = np.repeat(np.cumsum(steps * W) - steps * W, sizes)
+        arr[base + s * W + (r % T) * ilp + r // T] = rows[idx]
+    return arr.astype(np.uint32), steps.astype(np.uint32)
+
+
+class _Static:
+    """The parts of a class program's cooperative form that do not depend on
+    the team shape, built once per program: Phase-1 parents and descriptor
+    templates, and the Phase-2 graph of operations and output stores with
+    its descriptor templates."""
+
+    def __init__(self, prog):
+        g = prog.g
+        nh = prog.nh
+        n = len(g)
+        self.nh = nh
+        self.n1 = n
+        # ---------------- Phase 1
+        order_pos = np.empty(n, dtype=np.int64)
+        order_pos[np.array(prog.order, dtype=np.int64)] = np.arange(n)
+        self.prio1 = order_pos.tolist()
+        par1 = [[p for _, p in ts] for ts in g.terms]
+        self.par1 = par1
+        self.cons1, self.npar1 = _consumer_lists(par1, n)
+        consumed = np.zeros(n, dtype=bool)
+        for ps in par1:
+            for p in ps:
+                consumed[p] = True
+        self.consumed = consumed
+        # descriptor template: word 0 high half (h + 1), the meta field, and
+        # the node feeding each of the five operand positions (-1: none)
+        hword = np.zeros(n, dtype=np.int64)
+        meta = np.zeros(n, dtype=np.int64)
+        src = np.full((n, 5), -1, dtype=np.int64)
+        for v, ts in enumerate(g.terms):
+            h = g.target.get(v)
+            if h is not None:
+                hword[v] = (h + 1) << 16
+            m = 0
+            if not ts:
+                m = (1 << 14) | (g.keys[v][2] << 4)
+            for (kind, val), p in ts:
+                if kind in ("PA", "QC"):
+                    side = 0 if kind == "PA" else 1
+                    src[v, 0] = p
+                    m |= (6 * side + val) | (side << 13)
+                elif kind in ("WP", "WQ"):
+                    src[v, 1] = p
+                elif kind in ("c1z", "c1e"):
+                    src[v, 2] = p
+                    m |= val << 4
+                elif kind in ("c2z", "c2e"):
+                    src[v, 3] = p
+                elif kind == "c3":
+                    src[v, 4] = p
+                    m |= val << 9
+            meta[v] = m
+        self.hword, self.meta1, self.src1 = hword, meta, src
+        # shape of a Phase-1 node: base node; c1/c2 pair present; c3 present
+        self.shape1 = (((meta >> 14) & 1) * 4 + (((meta >> 4) & 31) > 0) * 2
+                       + (((meta >> 9) & 15) > 0)).astype(np.int64)
+        # ---------------- Phase 2: graph of operations and output stores
+        p2 = prog.p2
+        ctab = {c: i for i, c in enumerate(coef_table())}
+        # node ids: 0..nh-1 = H inputs; then one node per operation chunk;
+        # then stores.  Per node after the H inputs: the node in word 0's
+        # high half (the destination, or the stored value), up to four
+        # operand nodes, and the constant bits of each word.
+        kinds = ["h"] * nh
+        parents = [[] for _ in range(nh)]
+        val_node = {i: i for i in range(nh)}   # value id -> node producing it
+        dnode, ops, const = [], [], []
+        for op in p2.ops:
+            if op[0] == "hrr":
+                _, d, hi, sym_i, lo = op
+                nid = len(kinds)
+                kinds.append("hrr")
+                a, b = val_node[hi], val_node[lo]
+                parents.append([a, b])
+                sym, i = sym_i
+                dnode.append(nid)
+                ops.append((a, b, -1, -1))
+                const.append((0, 0, i + (3 if sym == "CD" else 0), 0))
+                val_node[d] = nid
+            else:
+                # rows of more than four terms: the first descriptor sums
+                # four, each further one adds 1.0 x the running sum and up to
+                # three more
+                _, d, terms = op
+                prev = None
+                rest = list(terms)
+                while rest:
+                    take = 4 if prev is None else 3
+                    chunk, rest = rest[:take], rest[take:]
+                    nid = len(kinds)
+                    kinds.append("lin")
+                    ps = [val_node[s] for _, s in chunk]
+                    cfs = [float(cf) for cf, _ in chunk]
+                    if prev is not None:
+                        ps.append(prev)
+                        cfs.append(1.0)
+                    parents.append(list(ps))
+                    nt = len(ps)
+                    cc = [ctab[cf] for cf in cfs] + [0] * (4 - nt)
+                    dnode.append(nid)
+                    ops.append(tuple(ps) + (-1,) * (4 - nt))
+                    const.append((1 | (nt << 2), 0, 0, cc[0] | (cc[1] << 8) | (cc[2] << 16) | (cc[3] << 24)))
+                    prev = nid
+                val_node[d] = prev
+        store_first = len(kinds)
+        for k, v in enumerate(p2.outputs):
+            kinds.append("store")
+            parents.append([val_node[v]])
+            i = np.unravel_index(k, p2.out_dims)
+            dnode.append(val_node[v])
+            ops.append((-1, -1, -1, -1))
+            const.append((2, k, int(i[0]) | (int(i[1]) << 8) | (int(i[2]) << 16) | (int(i[3]) << 24), 0))
+        n2 = len(kinds)
+        self.n2w = n2 - nh                     # scheduled Phase-2 nodes (work ids v - nh)
+        prio = np.arange(n2, dtype=np.int64)
+        # stores go right after their value: priority of the producer
+        for nid in range(store_first, n2):
+            prio[nid] = parents[nid][0]
+        self.prio2 = prio[nh:].tolist()
+        # H inputs are not scheduled (they are read in place)
+        par_w = [[p - nh for p in parents[v] if p >= nh] for v in range(nh, n2)]
+        self.par2 = par_w
+        self.cons2, self.npar2 = _consumer_lists(par_w, self.n2w)
+        self.needs2 = np.array([k in ("hrr", "lin") for k in kinds[nh:]], dtype=bool)
+        self.dnode2 = np.array(dnode, dtype=np.int64).reshape(-1)
+        self.ops2 = np.array(ops, dtype=np.int64).reshape(-1, 4)
+        self.const2 = np.array(const, dtype=np.int64).reshape(-1, 4)
+        # shape of a Phase-2 node: kind (HRR, linear combination, store),
+        # then number of terms
+        self.shape2 = ((self.const2[:, 0] & 3) * 8 + ((self.const2[:, 0] >> 2) & 7)).astype(np.int64)
+
+
+def _static(prog):
+    st = getattr(prog, "_coop_static", None)
+    if st is None:
+        st = _Static(prog)
+        prog._coop_static = st
+        prog._coop_width = {}
+    return st
+
+
+def release(prog):
+    """Drop the cooperative-form caches held on a class program."""
+    for name in ("_coop_static", "_coop_width"):
+        prog.__dict__.pop(name, None)
+
+
+def _width_form(prog, width):
+    """Waves, slots and descriptor rows of both phases for waves of up to
+    ``width`` nodes (cached per program and width: shapes of equal width
+    share them)."""
+    st = _static(prog)
+    cached = prog._coop_width.get(width)
+    if cached is not None:
+        return cached
+    nh = st.nh
+    # ---------------- Phase 1
+    waves1 = _waves(st.cons1, list(st.npar1), st.prio1, width)
+    wave_of, last = _lifetimes(st.par1, waves1)
+    slot1, nslot1 = _allocate(wave_of, last, st.consumed, [v for w in waves1 for v in w])
+    src = st.src1
+    sl = np.where(src >= 0, slot1[np.maximum(src, 0)], 0)
+    rows1 = np.empty((st.n1, 4), dtype=np.int64)
+    rows1[:, 0] = np.where(st.consumed, slot1, 0xFFFF) | st.hword
+    rows1[:, 1] = sl[:, 0] | (sl[:, 1] << 16)
+    rows1[:, 2] = sl[:, 2] | (sl[:, 3] << 16)
+    rows1[:, 3] = sl[:, 4] | (st.meta1 << 16)
+    # ---------------- Phase 2
+    waves2 = _waves(st.cons2, list(st.npar2), st.prio2, width)
+    wave_of2, last2 = _lifetimes(st.par2, waves2)
+    slot2, nslot2 = _allocate(wave_of2, last2, st.needs2, [v for w in waves2 for v in w])
+    # operand id of a node: H index, or nh + its value slot
+    oid = np.concatenate([np.arange(nh, dtype=np.int64), nh + slot2])
+
+    def ids(nodes):
+        return np.where(nodes >= 0, oid[np.maximum(nodes, 0)], 0)
+
+    o = ids(st.ops2)
+    c = st.const2
+    rows2 = np.empty((st.n2w, 4), dtype=np.int64)
+    rows2[:, 0] = c[:, 0] | (ids(st.dnode2) << 16)
+    rows2[:, 1] = c[:, 1] | o[:, 0] | (o[:, 1] << 16)
+    rows2[:, 2] = c[:, 2] | o[:, 2] | (o[:, 3] << 16)
+    rows2[:, 3] = c[:, 3]
+    form = (waves1, rows1, int(nslot1), waves2, rows2, int(nslot2))
+    prog._coop_width[width] = form
+    return form
 
 
 def build(prog, T=128, ilp=ILP, wave_steps=1):
     """CoopProgram of a class program for teams of T lanes taking ilp nodes
     per step; a wave (the nodes between two team barriers) holds up to
     wave_steps steps of mutually independent nodes."""
-    g = prog.g
-    nh = prog.nh
-    # ---------------- Phase 1
-    order_pos = np.empty(len(g), dtype=np.int64)
-    order_pos[np.array(prog.order, dtype=np.int64)] = np.arange(len(g))
-    par1 = [[p for _, p in ts] for ts in g.terms]
-    waves1 = wave_schedule(par1, order_pos, ilp * T * wave_steps)
-    consumed = np.zeros(len(g), dtype=bool)
-    for ps in par1:
-        for p in ps:
-            consumed[p] = True
-    slot1, nslot1 = allocate_over_waves(par1, waves1, consumed)
-
-    def row1(v):
-        ts = g.terms[v]
-        dst = int(slot1[v]) if consumed[v] else 0xFFFF
-        h = g.target.get(v)
-        src = [0] * 5
-        meta = 0
-        if not ts:
-            meta = (1 << 14) | (g.keys[v][2] << 4)
-        for (kind, val), p in ts:
-            s_ = int(slot1[p])
-            if kind in ("PA", "QC"):
-                side = 0 if kind == "PA" else 1
-                src[0] = s_
-                meta |= (6 * side + val) | (side << 13)
-            elif kind in ("WP", "WQ"):
-                src[1] = s_
-            elif kind in ("c1z", "c1e"):
-                src[2] = s_
-                meta |= val << 4
-            elif kind in ("c2z", "c2e"):
-                src[3] = s_
-            elif kind == "c3":
-                src[4] = s_
-                meta |= val << 9
-        return np.array([dst | ((h + 1) << 16 if h is not None else 0), src[0] | (src[1] << 16),
-                         src[2] | (src[3] << 16), src[4] | (meta << 16)], dtype=np.uint32)
-
-    def shape1(row):
-        # base node; c1/c2 pair present; c3 term present
-        meta = int(row[3]) >> 16
-        return ((meta >> 14) & 1, ((meta >> 4) & 31) > 0, ((meta >> 9) & 15) > 0)
-
-    ph1, steps1 = _pack(waves1, row1, T, NOP1, ilp, shape1)
-
-    # ---------------- Phase 2: graph of operations and output stores
-    p2 = prog.p2
-    ctab = {c: i for i, c in enumerate(coef_table())}
-    # node ids: 0..nh-1 = H inputs; then one node per operation chunk; then stores
-    nodes = []      # (kind, payload)
-    parents = []
-    val_node = {i: i for i in range(nh)}   # value id -> node producing it
-    for i in range(nh):
-        nodes.append(("h", i))
-        parents.append([])
-    for op in p2.ops:
-        if op[0] == "hrr":
-            _, d, hi, sym_i, lo = op
-            nid = len(nodes)
-            nodes.append(("hrr", (hi, lo, sym_i)))
-            parents.append([val_node[hi], val_node[lo]])
-            val_node[d] = nid
-        else:
-            # rows of more than four terms: the first descriptor sums four,
-            # each further one adds 1.0 x the running sum and up to three more
-            _, d, terms = op
-            prev = None
-            rest = list(terms)
-            while rest:
-                take = 4 if prev is None else 3
-                chunk, rest = rest[:take], rest[take:]
-                nid = len(nodes)
-                nodes.append(("lin", (chunk, prev)))
-                ps = [val_node[s] for _, s in chunk]
-                if prev is not None:
-                    ps.append(prev)
-                parents.append(ps)
-                prev = nid
-            val_node[d] = prev
-    store_nodes = []
-    for k, v in enumerate(p2.outputs):
-        nid = len(nodes)
-        nodes.append(("store", (k, v)))
-        parents.append([val_node[v]])
-        store_nodes.append(nid)
-    n2 = len(nodes)
-    prio = np.arange(n2, dtype=np.int64)
-    # stores go right after their value: priority of the producer
-    for nid in store_nodes:
-        prio[nid] = parents[nid][0]
-    # H inputs are not scheduled (they are read in place)
-    work = [v for v in range(n2) if nodes[v][0] != "h"]
-    pos = {v: i for i, v in enumerate(work)}
-    par_list = [[pos[p] for p in parents[v] if nodes[p][0] != "h"] for v in work]
-    waves2 = wave_schedule(par_list, np.array([prio[v] for v in work]), ilp * T * wave_steps)
-    waves2 = [[work[i] for i in w] for w in waves2]
-    needs = np.zeros(n2, dtype=bool)
-    for v in range(n2):
-        if nodes[v][0] in ("hrr", "lin"):
-            needs[v] = True
-    # slot allocation over the waves (H inputs keep their own ids)
-    sched = [v for w in waves2 for v in w]
-    loc = {v: i for i, v in enumerate(sched)}
-    p_loc = [[loc[p] for p in parents[v] if p in loc] for v in sched]
-    w_loc = []
-    c = 0
-    for w in waves2:
-        w_loc.append(list(range(c, c + len(w))))
-        c += len(w)
-    slot_l, nslot2 = allocate_over_waves(p_loc, w_loc, np.array([needs[v] for v in sched]))
-    slot2 = {v: int(slot_l[loc[v]]) for v in sched}
-
-    def oid(node):
-        # operand id of a node's value: H index or nh + slot
-        return node if nodes[node][0] == "h" else nh + slot2[node]
-
-    def row2(v):
-        kind, pl = nodes[v]
-        if kind == "hrr":
-            hi, lo, (sym, i) = pl
-            return np.array([0 | (oid(v) << 16), oid(val_node[hi]) | (oid(val_node[lo]) << 16),
-                             i + (3 if sym == "CD" else 0), 0], dtype=np.uint32)
-        if kind == "lin":
-            chunk, prev = pl
-            terms = [(float(cf), oid(val_node[s])) for cf, s in chunk]
-            if prev is not None:
-                terms.append((1.0, oid(prev)))
-            n = len(terms)
-            ss = [x for _, x in terms] + [0] * (4 - n)
-            cc = [ctab[cf] for cf, _ in terms] + [0] * (4 - n)
-            return np.array([1 | (n << 2) | (oid(v) << 16), ss[0] | (ss[1] << 16), ss[2] | (ss[3] << 16),
-                             cc[0] | (cc[1] << 8) | (cc[2] << 16) | (cc[3] << 24)], dtype=np.uint32)
-        k, val = pl
-        i = np.unravel_index(k, p2.out_dims)
-        return np.array([2 | (oid(val_node[val]) << 16), k,
-                         int(i[0]) | (int(i[1]) << 8) | (int(i[2]) << 16) | (int(i[3]) << 24), 0], dtype=np.uint32)
-
-    def shape2(row):
-        # kind (HRR, linear combination, store) and number of terms
-        return (int(row[0]) & 3, (int(row[0]) >> 2) & 7)
-
-    ph2, steps2 = _pack(waves2, row2, T, NOP2, ilp, shape2)
-    nslot = max(int(nslot1), int(nslot2))
+    st = _static(prog)
+    waves1, rows1, nslot1, waves2, rows2, nslot2 = _width_form(prog, ilp * T * wave_steps)
+    ph1, steps1 = _pack(waves1, rows1, T, NOP1, ilp, st.shape1)
+    ph2, steps2 = _pack(waves2, rows2, T, NOP2, ilp, st.shape2)
+    nh = st.nh
+    nslot = max(nslot1, nslot2)
     if nslot >= 0xFFFF or nh + nslot > MAX_ID:
         raise ValueError("class {} needs {} ids".format(prog.ls, nh + nslot))
-    eff1 = len(g) / max(1, int(steps1.sum()) * T * ilp)
-    eff2 = len(sched) / max(1, int(steps2.sum()) * T * ilp)
+    eff1 = st.n1 / max(1, int(steps1.sum()) * T * ilp)
+    eff2 = st.n2w / max(1, int(steps2.sum()) * T * ilp)
     assert ph1.shape[0] == (int(steps1.sum()) + PREFETCH_STEPS) * T * ilp
-    return CoopProgram(T, ilp, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(p2.out_dims), eff1, eff2)
+    return CoopProgram(T, ilp, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(prog.p2.out_dims), eff1, eff2)
 
 
 ROW_BYTES = 56 * 8           # one primitive quartet's coefficient row (executor constant)
@@ -398,6 +483,7 @@ def choose_both(prog, shapes=SHAPES):
     for rows in (DEEP_ROWS, SHALLOW_ROWS):
         scored = [(sc, k) for k, cp in enumerate(built) for sc in [_score(cp, rows)] if sc is not None]
         out.append(_wide_waves(prog, built[max(scored)[1]], rows) if scored else None)
+    release(prog)
     return tuple(out)
 
 

@@ -176,37 +176,40 @@ def dsa_scores(g, window: int = 8192) -> np.ndarray:
         if cons[v]:
             depth[v] = 1 + max(depth[c] for c in cons[v])
     maxc = max((len(c) for c in cons), default=0)
-    cmat = np.full((n, max(maxc, 1)), n, dtype=np.int64)  # n = dummy zero row
+    cmat = np.full((n, max(maxc, 1)), n, dtype=np.int64)  # n = no consumer
     for v, c in enumerate(cons):
         cmat[v, :len(c)] = c
     levels = [np.nonzero(depth == k)[0] for k in range(int(depth.max()) + 1 if n else 0)]
     score = np.zeros(n, dtype=np.int64)
-    dvals = np.unique(d)
     for w0 in range(0, n, window):
         w1 = min(n, w0 + window)
-        words = (w1 - w0 + 63) // 64
-        bits = np.zeros((n + 1, words), dtype=np.uint64)
+        # bit position of each node of the window: grouped by d(w), every
+        # group starting on a word, so that one popcount per word weighted
+        # by its group's d gives the sum
+        dw = d[w0:w1]
+        order = np.argsort(dw, kind="stable")
+        vals, counts = np.unique(dw, return_counts=True)
+        gwords = (counts + 63) // 64
+        start = np.repeat((np.cumsum(gwords) - gwords) * 64, counts)
+        pos = np.empty(w1 - w0, dtype=np.int64)
+        pos[order] = start + np.arange(w1 - w0) - np.repeat(np.cumsum(counts) - counts, counts)
+        words = int(gwords.sum())
+        # rows 0..w1-1, and row w1 (zero) for consumers at or beyond w1:
+        # a node at or beyond w1 reaches only later nodes, none in the window
+        bits = np.zeros((w1 + 1, words), dtype=np.uint64)
         own = np.arange(w0, w1)
-        bits[own, (own - w0) // 64] |= (np.uint64(1) << ((own - w0) % 64).astype(np.uint64))
+        bits[own, pos // 64] |= np.uint64(1) << (pos % 64).astype(np.uint64)
         for lev in levels:
+            lev = lev[: np.searchsorted(lev, w1)]
             if lev.size == 0:
                 continue
-            ch = cmat[lev]
-            acc = bits[lev].copy()
+            ch = np.minimum(cmat[lev], w1)
+            acc = bits[lev]
             for k in range(ch.shape[1]):
                 acc |= bits[ch[:, k]]
             bits[lev] = acc
-        # weighted popcount: one mask per distinct d value
-        for dv in dvals:
-            if dv == 0:
-                continue
-            sel = np.nonzero(d[w0:w1] == dv)[0]
-            if sel.size == 0:
-                continue
-            mask = np.zeros(words, dtype=np.uint64)
-            np.bitwise_or.at(mask, sel // 64, (np.uint64(1) << (sel % 64).astype(np.uint64)))
-            cnt = np.bitwise_count(bits[:n] & mask[None, :]).sum(axis=1).astype(np.int64)
-            score += dv * cnt
+        weight = np.repeat(vals, gwords)
+        score[:w1] += np.bitwise_count(bits[:w1]).astype(np.int64) @ weight
     return score
 
 
