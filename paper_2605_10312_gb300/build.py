@@ -8,6 +8,8 @@ Steps (FusionRCG Sec. IV, stages 8-9):
      the registry that lists them;
   3. nvcc -gencode arch=compute_103a,code=sm_103a for every unit, in
      parallel, then one shared library liberi.so.
+Every program is checked for in-bounds indexes (gen.verify) before it is
+written.
 Everything lands in paper_2605_10312_gb300/_build/.  Units whose source did
 not change are not recompiled.
 """
@@ -74,9 +76,12 @@ def _class_job(args):
     ls, opts, want_reg = args[:3]
     force_coop = len(args) > 3 and args[3]
     sys.setrecursionlimit(100000)
-    from paper_2605_10312_gb300.gen import emit_cuda, encode, program
+    from paper_2605_10312_gb300.gen import emit_cuda, encode, program, verify
     prog = program.make(*ls, *opts)
     enc = encode.encode(prog)
+    ncoef = len(encode.coef_table())
+    # every index a program-driven kernel takes from a descriptor is in bounds
+    verify.check(ls, verify.verify_encoded(enc, ncoef))
     c = prog.counts()
     rec = dict(ls=ls, opts=opts, nh=enc.nh, nslot=enc.nslot, L=enc.L, n1=int(enc.ph1.shape[0]),
                n2=int(enc.ph2.shape[0]), kmax=enc.kmax, dims=enc.out_dims, flops_prim=float(c["per_prim_flops"]),
@@ -99,6 +104,9 @@ def _class_job(args):
                         nw2=int(cp.steps2.shape[0]), ph1=cp.ph1.tobytes(), ph2=cp.ph2.tobytes(),
                         n1=int(cp.ph1.shape[0]), n2=int(cp.ph2.shape[0]), eff1=cp.eff1, eff2=cp.eff2)
         deep, shallow = coop.choose_both(prog)
+        for cp in (deep, shallow):
+            if cp is not None:
+                verify.check(ls, verify.verify_coop(cp, prog.L, ncoef))
         rec["coop"] = pack(deep)
         # a second shape for shallow contractions, when it differs
         if shallow is not None and (shallow.T, shallow.ilp) != (deep.T, deep.ilp):

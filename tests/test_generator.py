@@ -244,3 +244,52 @@ def test_coop_shallow_shape_prefers_narrow_teams():
     assert shallow.T < deep.T
     assert coop._score(shallow, coop.SHALLOW_ROWS) >= coop._score(deep, coop.SHALLOW_ROWS)
     assert coop._score(deep, coop.DEEP_ROWS) >= coop._score(shallow, coop.DEEP_ROWS)
+
+
+@pytest.mark.parametrize("ls", [(1, 1, 1, 1), (2, 2, 1, 1), (3, 1, 2, 0), (2, 2, 2, 2), (4, 0, 2, 1)])
+def test_generated_programs_are_in_bounds(ls):
+    """Every index a program-driven kernel takes from a descriptor (slots,
+    accumulators, coefficient-row entries, transform-table entries, output
+    elements) lies in the region the kernel addresses with it."""
+    from paper_2605_10312_gb300.gen import verify
+    prog = program.make(*ls)
+    ncoef = len(encode.coef_table())
+    assert verify.verify_encoded(encode.encode(prog), ncoef) == []
+    for T, ilp, k in ((32, 2, 1), (128, 4, 1), (64, 2, 2), (512, 2, 2)):
+        assert verify.verify_coop(coop.build(prog, T, ilp, k), prog.L, ncoef) == []
+
+
+def test_bounds_verifier_catches_planted_errors():
+    """Out-of-range indexes planted in copies of a valid program (on the
+    host) are each reported."""
+    import copy
+    from paper_2605_10312_gb300.gen import verify
+    prog = program.make(2, 2, 1, 1)
+    ncoef = len(encode.coef_table())
+    cp = coop.build(prog, 32, 2)
+    live1 = np.flatnonzero(((cp.ph1[:, 3] >> 16) & 0xC000) == 0)   # nodes with operands
+    stores = np.flatnonzero((cp.ph2[:, 0] & 3) == 2)
+    lins = np.flatnonzero((cp.ph2[:, 0] & 3) == 1)
+
+    def planted(fn):
+        c = copy.deepcopy(cp)
+        fn(c)
+        return verify.verify_coop(c, prog.L, ncoef)
+
+    def operand(c):
+        c.ph1[live1[0], 1] = (c.ph1[live1[0], 1] & 0xFFFF0000) | c.nslot
+    def accumulator(c):
+        c.ph1[live1[0], 0] = (c.ph1[live1[0], 0] & 0xFFFF) | ((c.nh + 1) << 16)
+    def element(c):
+        c.ph2[stores[0], 1] = np.prod(c.out_dims)
+    def coefficient(c):
+        c.ph2[lins[0], 3] = (c.ph2[lins[0], 3] & 0xFFFFFF00) | ncoef
+    def prefetch(c):
+        c.ph1[-1] = c.ph1[live1[0]]
+    for fn in (operand, accumulator, element, coefficient, prefetch):
+        assert planted(fn), fn.__name__
+    enc = encode.encode(prog)
+    term = int(np.flatnonzero(((enc.ph1[:, 3] >> 16) & 3) != 2)[0])   # first node with operands
+    bad = copy.deepcopy(enc)
+    bad.ph1[term, 1] = enc.nslot
+    assert verify.verify_encoded(bad, ncoef)
