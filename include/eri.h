@@ -5,8 +5,9 @@
  * (ab|cd) (FusionRCG paper, Sec. II-A, Eq. 1) by the Head-Gordon-Pople
  * scheme: Boys function and Obara-Saika vertical recurrence per primitive
  * quartet (Eq. 2), contraction, horizontal recurrence (Eq. 3) with the
- * Cartesian-to-spherical transform fused stepwise (Eqs. 8, 16).  All
- * arithmetic is FP64 and runs in CUDA kernels for sm_103a.
+ * Cartesian-to-spherical transform fused stepwise (Eqs. 8, 16).  The
+ * arithmetic is FP64 (eri_plan_mixed: FP32 recurrences for quartets whose
+ * bound is below a threshold) and runs in CUDA kernels for sm_103a.
  *
  * Conventions (bohr, Hartree atomic units):
  *  - a primitive x^i y^j z^k exp(-a r^2) of shell angular momentum l carries
