@@ -144,6 +144,37 @@ def oracle_rates(parts, budget_s=15.0, nthreads=None):
     return rates, samples, nthreads
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, else the Arm
+    implementer and part codes), else the machine type."""
+    import platform
+    info = {}
+    try:
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                info.setdefault(k.strip().lower(), v.strip())
+    except OSError:
+        pass
+    if "model name" in info:
+        return info["model name"]
+    if "cpu part" in info:
+        return "{} (CPU implementer {}, part {})".format(platform.machine(), info.get("cpu implementer", "?"),
+                                                       info["cpu part"])
+    return platform.machine()
+
+
+def single_core_baseline(parts, budget_s=4.0):
+    """The oracle on one host core: per-class rates on a bounded sample and
+    the rate of the step's class mix."""
+    r, samples, _ = oracle_rates(parts, budget_s=budget_s, nthreads=1)
+    return {"value": mix_rate(r), "unit": UNIT, "cores": 1,
+            "per_class": {"".join("spdfg"[x] for x in ls): r[ls] for ls in r},
+            "sample": "prefix of each class's quartets: " + ", ".join(
+                "{} {}".format("".join("spdfg"[x] for x in ls), samples[ls]) for ls in samples) +
+            " ({:.0f} s of CPU work)".format(budget_s)}
+
+
 def sweep():
     return [(ls, max(1, int(n * SCALE))) for ls, n in SWEEP
             if not ONLY or "".join("spdfg"[x] for x in ls) in ONLY]
@@ -181,7 +212,8 @@ def run_reference(args):
                       for ls in r},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "per step, a bounded prefix of each class's quartets ({} s of CPU work)".format(
-                             round(per_step, 1))},
+                             round(per_step, 1)),
+                         "cpu_model": cpu_model(), "single_core": single_core_baseline(parts)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -317,7 +349,8 @@ def run_ours(args):
                "sample": "prefix of each class's quartets: " + ", ".join(
                    "{} {}".format("".join("spdfg"[x] for x in ls), samples[ls]) for ls in samples) +
                " ({:.0f} s of CPU work)".format(args.cpu_seconds),
-               "per_class": {"".join("spdfg"[x] for x in ls): rates[ls] for ls in rates}}
+               "per_class": {"".join("spdfg"[x] for x in ls): rates[ls] for ls in rates},
+               "cpu_model": cpu_model(), "single_core": single_core_baseline(parts)}
     if rank != 0:
         return 0
     line = {
