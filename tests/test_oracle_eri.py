@@ -2,7 +2,8 @@
 Eqs. 2, 3, 8, 17), each independent of the oracle's own arithmetic:
 
 * (ss|ss) against the electrostatic energy of two Gaussian charge clouds;
-* brute-force quadrature of Eq. 1 for every s/p class and spot d classes;
+* brute-force quadrature of Eq. 1 for every s/p class and spot d, f and g
+  classes through (gg|gg);
 * 8-fold permutational symmetry (each permutation runs different recurrences);
 * rotational invariance through Wigner matrices built from scipy harmonics;
 * translational invariance, the Schwarz inequality, sph == cart for l <= 1;
@@ -52,9 +53,13 @@ def test_ssss_gaussian_charges(oracle_mod):
 
 SP_CLASSES = [c for c in itertools.product((0, 1), repeat=4)]
 D_CLASSES = [(2, 0, 0, 0), (0, 2, 0, 0), (2, 2, 0, 0), (2, 0, 1, 0), (1, 1, 2, 0), (0, 0, 0, 2), (2, 1, 1, 2)]
+# f and g shells: Obara-Saika terms with k = 2, 3 (and cross terms of k3 up
+# to 4) first appear here; the Gauss-Hermite rule stays exact through l = 4
+FG_CLASSES = [(3, 0, 0, 0), (0, 3, 0, 0), (4, 0, 0, 0), (0, 0, 0, 4), (3, 1, 0, 0), (3, 0, 2, 0), (4, 0, 1, 0),
+              (3, 3, 0, 0), (4, 1, 3, 0), (4, 4, 4, 0), (3, 3, 3, 3), (4, 4, 4, 4)]
 
 
-@pytest.mark.parametrize("ls", SP_CLASSES + D_CLASSES)
+@pytest.mark.parametrize("ls", SP_CLASSES + D_CLASSES + FG_CLASSES)
 def test_quadrature(oracle_mod, ls):
     K = 2 if sum(ls) <= 4 else 1
     basis, q = _basis_for(ls, K, seed=500 + 7 * sum(l * 5 ** i for i, l in enumerate(ls)))
