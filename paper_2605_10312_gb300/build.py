@@ -102,7 +102,8 @@ def _class_job(args):
             return dict(T=cp.T, ilp=cp.ilp, nh=cp.nh, nslot=cp.nslot, L=cp.L, dims=cp.out_dims,
                         steps1=cp.steps1.tobytes(), steps2=cp.steps2.tobytes(), nw1=int(cp.steps1.shape[0]),
                         nw2=int(cp.steps2.shape[0]), ph1=cp.ph1.tobytes(), ph2=cp.ph2.tobytes(),
-                        n1=int(cp.ph1.shape[0]), n2=int(cp.ph2.shape[0]), eff1=cp.eff1, eff2=cp.eff2)
+                        n1=int(cp.ph1.shape[0]), n2=int(cp.ph2.shape[0]), eff1=cp.eff1, eff2=cp.eff2,
+                        issue=coop.fp64_issue(cp))
         deep, shallow = coop.choose_both(prog)
         for cp in (deep, shallow):
             if cp is not None:
@@ -234,7 +235,8 @@ def build(force=False, jobs=None, log=print):
         # class table for the docs and the benchmark: per-class counts
         with open(os.path.join(BUILD, "classes.tsv"), "w") as f:
             f.write("la\tlb\tlc\tld\ttier\tvrr_nodes\tpeak_live\tnslot\tnh\tnout\tper_prim_flops\tp2_flops"
-                    "\tcoop_T\tcoop_ilp\tcoop_nslot\tcoop_eff1\tcoop_eff2\tshallow_T\tshallow_ilp\n")
+                    "\tcoop_T\tcoop_ilp\tcoop_nslot\tcoop_eff1\tcoop_eff2\tshallow_T\tshallow_ilp"
+                    "\tcoop_fp64_ceil1\tcoop_fp64_ceil2\n")
             for r in sorted(recs, key=lambda r: r["ls"]):
                 c = r["counts"]
                 cp = r.get("coop")
@@ -246,7 +248,12 @@ def build(force=False, jobs=None, log=print):
                                                    round(cp["eff1"], 3) if cp else "",
                                                    round(cp["eff2"], 3) if cp else "",
                                                    r["coop_shallow"]["T"] if "coop_shallow" in r else "",
-                                                   r["coop_shallow"]["ilp"] if "coop_shallow" in r else "")) + "\n")
+                                                   r["coop_shallow"]["ilp"] if "coop_shallow" in r else "",
+                                                   # FP64 issue ceilings of the deep shape: algorithmic
+                                                   # flops / (64 x FP64 warp-instructions)
+                                                   round(c["vrr_flops"] / (64 * max(1, cp["issue"][0])), 3) if cp else "",
+                                                   round(c["p2_flops"] / (64 * max(1, cp["issue"][1])), 3)
+                                                   if cp else "")) + "\n")
         open(stamp, "w").write(gen_key)
     units = [os.path.join(CSRC, "eri_runtime.cu"), os.path.join(CSRC, "eri_exec.cu"),
              os.path.join(CSRC, "eri_coop.cu"), os.path.join(CSRC, "eri_digest.cu"),

@@ -394,6 +394,42 @@ def build(prog, T=128, ilp=ILP, wave_steps=1):
     return CoopProgram(T, ilp, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(prog.p2.out_dims), eff1, eff2)
 
 
+def fp64_issue(cp):
+    """FP64 warp-instructions the cooperative executor issues for a program:
+    (Phase 1 per primitive quartet, Phase 2 per shell quartet).  A warp
+    issues an instruction whenever one of its 32 lanes needs it (a
+    predicated-off lane still takes the issue slot): per descriptor slot, a
+    Phase-1 node costs a multiply and an FMA, two more FMAs when it has the
+    second Obara-Saika term and one more for the cross term; an HRR step one
+    FMA; a linear combination of n terms a multiply and n - 1 FMAs.  H
+    updates (atomic reductions in global memory) and stores of a quartet's
+    first part issue none.  With a class's algorithmic flops this gives the
+    fraction of the FP64 FMA rate the program could reach if the pipe never
+    waited."""
+    W = cp.T * cp.ilp
+    warps = cp.T // 32
+
+    def slots(ph, steps):
+        n = int(np.sum(steps))
+        return ph[: n * W].astype(np.int64).reshape(n, warps, 32, cp.ilp, 4)
+
+    def any_lane(m):
+        return m.any(axis=2).astype(np.int64)
+
+    d = slots(cp.ph1, cp.steps1)
+    meta = d[..., 3] >> 16
+    term = (meta & 0xC000) == 0
+    i1 = (2 * any_lane(term) + 2 * any_lane(term & (((meta >> 4) & 31) > 0))
+          + any_lane(term & (((meta >> 9) & 15) > 0)))
+    d = slots(cp.ph2, cp.steps2)
+    kind = d[..., 0] & 3
+    nt = (d[..., 0] >> 2) & 7
+    lin = kind == 1
+    i2 = (any_lane(kind == 0) + any_lane(lin) + any_lane(lin & (nt > 1)) + any_lane(lin & (nt > 2))
+          + any_lane(lin & (nt > 3)))
+    return int(i1.sum()), int(i2.sum())
+
+
 ROW_BYTES = 56 * 8           # one primitive quartet's coefficient row (executor constant)
 DEEP_ROWS = 32               # rows per team for deep contractions (one per lane of a warp)
 SHALLOW_ROWS = 12            # rows per team for contractions of at most 12 primitive quartets

@@ -293,3 +293,19 @@ def test_bounds_verifier_catches_planted_errors():
     bad = copy.deepcopy(enc)
     bad.ph1[term, 1] = enc.nslot
     assert verify.verify_encoded(bad, ncoef)
+
+
+def test_fp64_issue_count_bounds():
+    """The FP64 warp-instruction count of a cooperative program lies between
+    the lane instructions packed 32 to a warp and one full warp-instruction
+    set per occupied descriptor slot; the ceiling it gives is below 1."""
+    prog = program.make(2, 2, 2, 1)
+    c = prog.counts()
+    cp = coop.build(prog, 64, 2)
+    i1, i2 = coop.fp64_issue(cp)
+    g = prog.g
+    lane1 = sum(len(ts) for ts in g.terms)        # one instruction per term
+    assert lane1 / 32 <= i1 <= 5 * int(cp.steps1.sum()) * (cp.T // 32) * cp.ilp
+    ins2, _ = hrr.op_counts(prog.p2)
+    assert ins2 / 32 <= i2
+    assert c["vrr_flops"] / (64 * i1) < 1 and c["p2_flops"] / (64 * i2) < 1
