@@ -1,5 +1,11 @@
-"""Serving loop host logic without a GPU: the request stream generator and
-the run summary."""
+"""Serving loop host logic without a GPU: the request stream generator, the
+run summary, and the request loop (admission by device-memory footprint,
+slots, rejection, bounded waits and timeouts) against fakes of the device
+calls."""
+import contextlib
+import sys
+import time
+
 import numpy as np
 
 from paper_2605_10312_gb300 import serve
@@ -34,3 +40,137 @@ def test_summary():
     assert abs(s["p50_ms"] - 12.5) < 1e-9
     assert abs(s["served_quartets_per_s"] - 400 / 0.5) < 1e-6
     assert abs(s["offered_requests_per_s"] - 3 / 0.02) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# the request loop against fakes of the device calls (no GPU): streams and
+# events that complete after a set time, and a plan whose compute occupies
+# its stream for a set duration
+# ---------------------------------------------------------------------------
+class _FakeStream:
+    def __init__(self):
+        self.busy_until = 0.0
+
+
+class _FakeEvent:
+    def __init__(self):
+        self.t = None
+
+    def record(self, stream):
+        self.t = stream.busy_until
+
+    def query(self):
+        return time.perf_counter() >= self.t
+
+
+class _FakeCuda:
+    Stream = _FakeStream
+    Event = _FakeEvent
+
+    @contextlib.contextmanager
+    def stream(self, st):
+        yield
+
+
+class _FakeTorch:
+    float64 = "float64"
+    cuda = _FakeCuda()
+
+    @staticmethod
+    def empty(n, dtype=None, device=None):
+        return np.empty(n)
+
+
+class _Tracker:
+    """In-flight plans (computed, not closed), checked against the budget
+    and the slot count at every launch."""
+
+    def __init__(self, budget, slots, mol, duration):
+        self.budget, self.slots, self.mol, self.duration = budget, slots, mol, duration
+        self.live = set()
+        self.max_live = 0
+        self.launch_order = []
+
+    def plan_class(self):
+        tr = self
+
+        class FakePlan:
+            def __init__(self, basis, quartets, mol=None, stream=None, qbound=None, fp32_below=None, **kw):
+                self.q = np.asarray(quartets)
+                self.output_count = int(self.q.shape[0])
+
+            def compute(self, out, st):
+                st.busy_until = max(st.busy_until, time.perf_counter()) + tr.duration(self.q)
+                tr.live.add(self)
+                tr.launch_order.append(int(self.q[0, 0]))
+                tr.max_live = max(tr.max_live, len(tr.live))
+                used = sum(serve.Server.footprint(tr.mol, p.q) for p in tr.live)
+                assert used <= tr.budget, "admitted beyond the memory budget"
+                assert len(tr.live) <= tr.slots, "more requests in flight than slots"
+
+            def stats(self):
+                return {"fp32_parts": 0}
+
+            def close(self):
+                tr.live.discard(self)
+        return FakePlan
+
+
+class _FakeMol:
+    def close(self):
+        pass
+
+
+def _server(monkeypatch, budget, slots, timeout_s, duration):
+    monkeypatch.setitem(sys.modules, "torch", _FakeTorch())
+    mol = serve.Molecule("m", None, np.zeros((10, 2), dtype=np.int32), np.ones(10), None, mol=_FakeMol(),
+                         nsph=np.ones(64, dtype=np.int64))
+    tr = _Tracker(budget, slots, mol, duration)
+    monkeypatch.setattr(serve.eri, "Plan", tr.plan_class())
+    srv = serve.Server(budget_bytes=budget, slots=slots, planners=2, fp32_below=None, timeout_s=timeout_s,
+                       poll_s=1e-4)
+    srv.molecules["m"] = mol
+    return srv, tr, mol
+
+
+def _requests(sizes, arrivals):
+    # the first shell index of a request's quartets is its id (launch order)
+    return [serve.Request(i, "m", np.full((n, 4), i, dtype=np.int32), t) for i, (n, t) in
+            enumerate(zip(sizes, arrivals))]
+
+
+def test_admission_holds_the_memory_budget_and_the_slots(monkeypatch):
+    """Twelve requests at once, memory for two: never more than two in
+    flight, all served, admitted and launched in arrival order."""
+    one = serve.Server.footprint(serve.Molecule("m", None, np.zeros((10, 2)), np.ones(10), None,
+                                                nsph=np.ones(64, dtype=np.int64)), np.zeros((1000, 4), dtype=np.int32))
+    srv, tr, _ = _server(monkeypatch, budget=2 * one + 100, slots=4, timeout_s=5.0, duration=lambda q: 0.05)
+    res = srv.serve(_requests([1000] * 12, [0.0] * 12))
+    srv.close()
+    assert [r.status for r in res] == ["ok"] * 12
+    assert tr.max_live == 2
+    assert tr.launch_order == sorted(tr.launch_order)
+    assert all(r.admitted <= r.launched <= r.finished for r in res)
+
+
+def test_oversize_request_is_rejected_others_served(monkeypatch):
+    srv, tr, mol = _server(monkeypatch, budget=300_000, slots=2, timeout_s=5.0, duration=lambda q: 0.005)
+    res = srv.serve(_requests([100, 100_000, 100], [0.0, 0.001, 0.002]))
+    srv.close()
+    assert serve.Server.footprint(mol, np.zeros((100_000, 4), dtype=np.int32)) > 300_000
+    assert [r.status for r in res] == ["ok", "rejected", "ok"]
+
+
+def test_timeout_is_reported_and_the_slot_held_until_the_work_ends(monkeypatch):
+    """A request whose work outlasts the timeout is reported as "timeout" at
+    the deadline; its slot and memory return only when the device finishes,
+    so the next request (one slot, arriving shortly before) launches after
+    that and, its latency counted from its arrival, within its timeout."""
+    work = {0: 0.30, 1: 0.01}
+    srv, tr, _ = _server(monkeypatch, budget=1 << 30, slots=1, timeout_s=0.05,
+                         duration=lambda q: work[int(q[0, 0])])
+    res = srv.serve(_requests([10, 10], [0.0, 0.27]))
+    srv.close()
+    assert res[0].status == "timeout" and res[1].status == "ok"
+    assert res[0].finished - res[0].arrival < 0.25          # reported at the deadline, not at the end
+    assert res[1].launched >= 0.29                          # the slot was held until the work ended
