@@ -76,3 +76,34 @@ def test_count_screened(thr):
     q = 10.0 ** rng.uniform(-8, 0.3, pairs.shape[0])
     q[:4] = 0.0
     assert synth.count_screened(q, thr) == synth.screened_quartets(q, pairs, thr).shape[0]
+
+
+def test_water_cluster_geometry_and_basis():
+    """The recipe of the water-cluster workloads: rigid waters (O-H 0.96 A,
+    H-O-H 104.5 deg), O-O >= 2.8 A, one basis per element shared by all its
+    atoms, exponents in [0.05, 500] sorted tight to diffuse within a shell,
+    coefficients in [0.1, 1]."""
+    b = synth.water_cluster(20, seed=3, layout="dz")
+    xyz = b.centers / synth.ANGSTROM_TO_BOHR
+    assert xyz.shape == (60, 3)
+    O, H1, H2 = xyz[0::3], xyz[1::3], xyz[2::3]
+    assert np.allclose(np.linalg.norm(H1 - O, axis=1), 0.96, atol=1e-12)
+    assert np.allclose(np.linalg.norm(H2 - O, axis=1), 0.96, atol=1e-12)
+    cosang = np.sum((H1 - O) * (H2 - O), axis=1) / 0.96 ** 2
+    assert np.allclose(np.degrees(np.arccos(cosang)), 104.5, atol=1e-9)
+    d = np.linalg.norm(O[:, None] - O[None], axis=2) + np.eye(20) * 1e9
+    assert d.min() >= 2.8
+    # per atom: O 3s 2p 1d (K = 6, 3, 1, 3, 1, 1), H 2s 1p (K = 3, 1, 1)
+    per_atom = {0: [(0, 6), (0, 3), (0, 1), (1, 3), (1, 1), (2, 1)], 1: [(0, 3), (0, 1), (1, 1)]}
+    shells = {}
+    for s in range(b.nshell):
+        shells.setdefault(int(b.shell_center[s]), []).append(s)
+    for atom, ss in shells.items():
+        want = per_atom[0 if atom % 3 == 0 else 1]
+        assert [(int(b.shell_l[s]), int(b.shell_nprim[s])) for s in ss] == want
+        ref = shells[0 if atom % 3 == 0 else 1]   # the first atom of the same element
+        for s, r in zip(ss, ref):
+            e = b.exps[b.shell_prim[s]:b.shell_prim[s] + b.shell_nprim[s]]
+            assert np.array_equal(e, b.exps[b.shell_prim[r]:b.shell_prim[r] + b.shell_nprim[r]])
+            assert np.all(np.diff(e) < 0) and e.min() >= 0.05 and e.max() <= 500.0
+    assert b.coefs.min() >= 0.1 and b.coefs.max() <= 1.0
