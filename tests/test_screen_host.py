@@ -107,3 +107,27 @@ def test_water_cluster_geometry_and_basis():
             assert np.array_equal(e, b.exps[b.shell_prim[r]:b.shell_prim[r] + b.shell_nprim[r]])
             assert np.all(np.diff(e) < 0) and e.min() >= 0.05 and e.max() <= 500.0
     assert b.coefs.min() >= 0.1 and b.coefs.max() <= 1.0
+
+
+def test_tiny_set_and_class_sweep_recipes():
+    """The tiny set: 3 atoms in a 3 A cube, each with s, s, p shells of 3
+    primitives (exponents in [0.1, 100], coefficients in [0.1, 1]), and all
+    45 * 46 / 2 = 1035 unique quartets.  The per-class sweep: independent
+    quartets of one class, four fresh centres each in a 10 A cube, K per
+    shell drawn from the given set, exponents in [0.05, 500]."""
+    b, q = synth.tiny_set(seed=1)
+    assert b.nshell == 9 and q.shape == (1035, 4)
+    assert list(b.shell_l) == [0, 0, 1] * 3 and set(b.shell_nprim.tolist()) == {3}
+    xyz = b.centers / synth.ANGSTROM_TO_BOHR
+    assert xyz.shape == (3, 3) and xyz.min() >= 0.0 and xyz.max() <= 3.0
+    assert b.exps.min() >= 0.1 and b.exps.max() <= 100.0 and b.coefs.min() >= 0.1 and b.coefs.max() <= 1.0
+    # unique under the 8-fold permutational symmetry
+    canon = {tuple(sorted([tuple(sorted(x[:2])), tuple(sorted(x[2:]))])) for x in q.tolist()}
+    assert len(canon) == 1035
+    b, q = synth.class_sweep((2, 1, 3, 0), 500, kset=(1, 3, 6), seed=9)
+    assert q.shape == (500, 4) and np.array_equal(q.ravel(), np.arange(2000))
+    assert list(b.shell_l[:4]) == [2, 1, 3, 0]
+    assert set(b.shell_nprim.tolist()) == {1, 3, 6} and np.array_equal(b.shell_center, np.arange(2000))
+    xyz = b.centers / synth.ANGSTROM_TO_BOHR
+    assert xyz.min() >= 0.0 and xyz.max() <= 10.0
+    assert b.exps.min() >= 0.05 and b.exps.max() <= 500.0
