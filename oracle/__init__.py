@@ -15,7 +15,8 @@ Parity status of each function (what pins it; the pins live in ``tests/``):
   cart2sph   -- pinned: textbook l <= 2 solid harmonics, orthonormality under
                 the Cartesian overlap metric, scipy spherical harmonics.
   eri        -- pinned: (ss|ss) closed form, brute-force quadrature of Eq. 1
-                for l <= 1 (and spot d cases), 8-fold permutation symmetry,
+                for every s/p class and spot d, f and g classes through
+                (gg|gg), 8-fold permutation symmetry,
                 rotational and translational invariance, Schwarz inequality,
                 long-double adjudication.
   full_tensor, jk
