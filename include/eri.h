@@ -92,7 +92,8 @@ typedef struct eri_mol_s eri_mol_t;
  * order, host memory).  Validates every input, canonicalises each quartet to
  * its class and orientation, uploads basis, pair list and quartet records to
  * the current CUDA device and sizes the scratch.  Host inputs are copied;
- * the plan owns its device memory.  nq may be 0.  Synchronous. */
+ * the plan owns its device memory.  nq may be 0, and is at most 2^31 - 1
+ * (ERI_EINVAL above).  Synchronous. */
 int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
              int64_t nq, const eri_opts* opts, eri_plan_t** plan_out);
 

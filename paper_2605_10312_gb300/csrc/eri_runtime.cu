@@ -717,7 +717,8 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   }
   if (nq < 0 || nshell < 0 || (nq > 0 && (!shells || !basis || !quartets)))
     return fail(ERI_EINVAL, "NULL or negative argument");
-  if (nq > (int64_t)1 << 31) return fail(ERI_EINVAL, "too many quartets for one plan");
+  // launches take their quartet count as int32
+  if (nq > ((int64_t)1 << 31) - 1) return fail(ERI_EINVAL, "too many quartets for one plan (at most 2^31 - 1)");
   const bool cart = opts.sph_mode == 2;
   // ---- validation
   if (nshell > 0) {

@@ -62,6 +62,14 @@ def test_argument_errors_without_gpu():
     with pytest.raises(eri.EriError) as e:
         eri.Plan(neg, q[:4])
     assert e.value.code == -1
+    # launches take their quartet count as int32: 2^31 quartets are refused
+    # before the quartet array is read
+    lib = eri.library()
+    sh, ns, b, keep = eri._marshal_basis(basis)
+    qq = np.ascontiguousarray(q[:1])
+    h = ctypes.c_void_p()
+    assert lib.eri_plan(sh, ns, ctypes.byref(b), qq.ctypes.data, 1 << 31, None, ctypes.byref(h)) == -1
+    assert b"too many quartets" in lib.eri_last_error()
     # an empty quartet list is a valid plan with no output
     p = eri.Plan(basis, np.zeros((0, 4), dtype=np.int32))
     assert p.output_count == 0
