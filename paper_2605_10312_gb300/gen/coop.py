@@ -117,6 +117,8 @@ def _allocate(wave_of, last, needs_slot, order, first_slot=0):
 
 
 def _lifetimes(parents, waves, pinned_until_end=()):
+    """Wave of every node and the last wave that reads it (its own wave if
+    nothing does; pinned nodes: past the last wave)."""
     n = len(parents)
     wave_of = np.zeros(n, dtype=np.int64)
     for w, vs in enumerate(waves):
