@@ -309,3 +309,18 @@ def test_fp64_issue_count_bounds():
     ins2, _ = hrr.op_counts(prog.p2)
     assert ins2 / 32 <= i2
     assert c["vrr_flops"] / (64 * i1) < 1 and c["p2_flops"] / (64 * i2) < 1
+
+
+def test_gggg_production_program_matches_oracle():
+    """The (gg|gg) cooperative program the build ships (512-lane teams,
+    waves of up to two steps), walked wave by wave on the CPU, reproduces the
+    oracle on compact quartets with O(1e-2) integrals."""
+    prog = program.make(4, 4, 4, 4)
+    deep, _ = coop.choose_both(prog)
+    assert (deep.T, deep.ilp) == coop.WIDEST_SHAPE and int(deep.steps1.max()) == 2
+    basis, q = synth.class_sweep((4, 4, 4, 4), 2, kset=(1, 2), seed=24, box_angstrom=0.5, exp_range=(0.3, 3.0))
+    ref, _ = blocks(basis, q)
+    ref = ref.reshape(q.shape[0], -1)
+    assert np.abs(ref).max() > 1e-2
+    got = run_coop(deep, prog, basis, q)
+    assert within(got, ref).all()
