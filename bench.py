@@ -122,26 +122,42 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (also the --impl reference arm)
 # ---------------------------------------------------------------------------
-def oracle_rates(parts, budget_s=15.0, nthreads=None):
+def oracle_rates(parts, budget_s=15.0, nthreads=None, sizes=None):
     """Oracle quartets/s per class on a bounded sample of each class's
-    quartets (same geometry and contraction mix), all host cores."""
+    quartets (a prefix: same geometry and contraction mix), all host cores.
+
+    The oracle's thread pool hands out one quartet per task, so a batch ends
+    with threads idle while the slowest quartets finish; a rate taken from
+    batches of a few quartets per thread understates the oracle.  Each class
+    therefore gets a short calibration (batches growing from 16 quartets, a
+    fifth of its budget) and then one batch sized to fill the rest of its
+    budget with at least eight quartets per thread; the rate is that batch's.
+    ``sizes`` (the second return value of an earlier call) skips the
+    calibration.  Returns (rates, sizes, threads)."""
     import oracle
     oracle.build()
     nthreads = nthreads or os.cpu_count() or 1
-    rates, samples = {}, {}
+    rates, out_sizes = {}, {}
     per_class = budget_s / len(parts)
     for ls, basis, q in parts:
-        n, done, t_used = 16, 0, 0.0
-        while t_used < per_class and done < q.shape[0]:
-            sel = q[done:done + n]
-            t0 = time.perf_counter()
-            oracle.eri(basis, sel, nthreads=nthreads)
-            t_used += time.perf_counter() - t0
-            done += sel.shape[0]
-            n = max(16, int(n * 2))
-        rates[ls] = done / t_used
-        samples[ls] = done
-    return rates, samples, nthreads
+        if sizes is None:
+            n, done, t_used = 16, 0, 0.0
+            while t_used < 0.2 * per_class and done < q.shape[0]:
+                sel = q[done:done + n]
+                t0 = time.perf_counter()
+                oracle.eri(basis, sel, nthreads=nthreads)
+                t_used += time.perf_counter() - t0
+                done += sel.shape[0]
+                n *= 2
+            size = int(max(8 * nthreads, done / t_used * 0.8 * per_class))
+        else:
+            size = sizes[ls]
+        sel = q[:min(size, q.shape[0])]
+        t0 = time.perf_counter()
+        oracle.eri(basis, sel, nthreads=nthreads)
+        rates[ls] = sel.shape[0] / (time.perf_counter() - t0)
+        out_sizes[ls] = sel.shape[0]
+    return rates, out_sizes, nthreads
 
 
 def cpu_model():
@@ -193,10 +209,14 @@ def run_reference(args):
         return 0
     parts = workload()
     times = []
-    per_step = max(2.0, 30.0 / max(1, args.steps + args.warmup))
+    # one calibration sizes each class's sample for about 6 s of CPU work per
+    # step (the same measurement as the cpu_baseline leg, on a smaller
+    # budget); every step then evaluates those samples
+    per_step = 6.0
+    _, sizes, _ = oracle_rates(parts, budget_s=per_step)
     rates = None
     for s in range(args.warmup + args.steps):
-        r, samples, cores = oracle_rates(parts, budget_s=per_step)
+        r, samples, cores = oracle_rates(parts, budget_s=per_step, sizes=sizes)
         if s >= args.warmup:
             times.append(mix_rate(r))
             rates = (r, samples, cores)
@@ -211,8 +231,9 @@ def run_reference(args):
         "per_class": {"".join("spdfg"[x] for x in ls): {"quartets_per_s": r[ls], "sample": samples[ls]}
                       for ls in r},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "per step, a bounded prefix of each class's quartets ({} s of CPU work)".format(
-                             round(per_step, 1)),
+                         "sample": "per step, a prefix of each class's quartets: " + ", ".join(
+                             "{} {}".format("".join("spdfg"[x] for x in ls), samples[ls]) for ls in samples) +
+                         " (about {:.0f} s of CPU work, sized by one calibration run)".format(per_step),
                          "cpu_model": cpu_model(), "single_core": single_core_baseline(parts)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -247,7 +268,7 @@ def run_ours(args):
     parts = workload(rank)
     plans, outs = [], []
     for ls, basis, q in parts:
-        p = eri.Plan(basis, q)
+        p = eri.Plan(basis, q, votes=args.votes, persistent=args.persistent)
         p.set_timing(True)
         plans.append((ls, p))
         outs.append(torch.empty(p.output_count, dtype=torch.float64, device=dev))
@@ -514,7 +535,7 @@ def run_water(args):
         if args.autotune:
             tuned = tune.autotune(basis, quartets, sample=1024)
         t1 = time.perf_counter()
-        plan = eri.Plan(basis, quartets, digest=args.jk)
+        plan = eri.Plan(basis, quartets, digest=args.jk, persistent=args.persistent)
         t_plan = time.perf_counter() - t1
         out = torch.empty(max(1, plan.output_count), dtype=torch.float64, device="cuda")
         plan.set_timing(True)
@@ -550,7 +571,7 @@ def run_water(args):
             "value": quartets.shape[0] / (ms * 1e-3), "unit": "quartets/s",
             "fp64_tflops": st["flops"] / (ms * 1e-3) / 1e12,
             "fp64_frac_of_peak": st["flops"] / (ms * 1e-3) / 1e12 / fp64_peak_tflops(),
-            "launches_per_step": st["launches"] + 1, "graph": True, "jk": jk,
+            "launches_per_step": st["launches"] + 1, "graph": True, "persistent": bool(args.persistent), "jk": jk,
             "autotuned": None if tuned is None else {"".join(map(str, c)): v["tier"] for c, v in tuned.items()},
             "per_class": {k: {"parts": v["quartet_parts"], "ms": v["ms"], "tier": v["tier"],
                               "fp64_frac": v["flops"] / max(1e-9, v["ms"] * 1e-3) / 1e12 / fp64_peak_tflops()}
@@ -572,15 +593,24 @@ def run_water_jk(args, basis, plan, out, stream):
     J = torch.zeros_like(D)
     K = torch.zeros_like(D)
     step_ms, dig_ms = [], []
+    fused = bool(getattr(args, "persistent", False))
     with torch.cuda.stream(stream):
         for it in range(args.warmup + args.steps):
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
-            plan.replay(stream)
-            J.zero_()
-            K.zero_()
-            e1.record(stream)
-            plan.digest_jk(out, D, J, K, stream)
+            if fused:
+                # persistent plan: the digestion runs inside the evaluation
+                # launch (eri_compute_jk), no separate pass
+                J.zero_()
+                K.zero_()
+                e1.record(stream)
+                plan.compute_jk(D, J, K, stream)
+            else:
+                plan.replay(stream)
+                J.zero_()
+                K.zero_()
+                e1.record(stream)
+                plan.digest_jk(out, D, J, K, stream)
             e2.record(stream)
             e2.synchronize()
             if it >= args.warmup:
@@ -590,6 +620,10 @@ def run_water_jk(args, basis, plan, out, stream):
     nbytes = 8.0 * plan.output_count + 24.0 * nq
     dig = statistics.mean(dig_ms)
     peak = hbm_peak_gbs()
+    if fused:
+        return {"nbf": nbf, "ms_per_step": statistics.mean(step_ms), "fused": True,
+                "value": nq / (statistics.mean(step_ms) * 1e-3), "unit": "quartets/s (ERI + J/K digestion)",
+                "energies": {"coulomb": float(torch.sum(D * J).item()), "exchange": float(torch.sum(D * K).item())}}
     return {"nbf": nbf, "ms_per_step": statistics.mean(step_ms), "digest_ms": dig,
             "value": nq / (statistics.mean(step_ms) * 1e-3), "unit": "quartets/s (ERI + J/K digestion)",
             "digest_roofline": {"bound": "hbm", "achieved": nbytes / (dig * 1e-3) / 1e9, "peak": peak,
@@ -714,7 +748,7 @@ def run_per_k(args):
         for K in (1, 3, 6):
             n = max(1, int(counts[ls[0]][K] * SCALE))
             basis, q = synth.class_sweep(ls, n, kset=(K,), seed=SEED + 10 * ls[0] + K)
-            p = eri.Plan(basis, q)
+            p = eri.Plan(basis, q, votes=args.votes, persistent=args.persistent)
             out = torch.empty(p.output_count, dtype=torch.float64, device="cuda")
             ms = []
             for it in range(args.warmup + args.steps):
@@ -805,6 +839,10 @@ def main():
     ap.add_argument("--layout", default="dz", choices=["dz", "tz"])
     ap.add_argument("--threshold", type=float, default=1e-10)
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--votes", default="auto", choices=["auto", "off", "on"],
+                    help="team-cooperative programs: warp votes around optional FP64 terms")
+    ap.add_argument("--persistent", action="store_true",
+                    help="persistent plans: every class in one launch per precision over a device work list")
     ap.add_argument("--jk", action="store_true", help="water workload: also digest into J and K")
     ap.add_argument("--fp32-below", type=float, default=None,
                     help="water workload in mixed precision: FP32 recurrences below this Schwarz bound")

@@ -41,7 +41,7 @@ enum {
   ERI_ENOMEM = -3,        /* device or host allocation failed */
   ERI_ECUDA = -4,         /* a CUDA call failed (message in eri_last_error) */
   ERI_EBUSY = -5,         /* reserved: plan in use */
-  ERI_ETIMEOUT = -6,      /* reserved: bounded device wait expired */
+  ERI_ETIMEOUT = -6,      /* a bounded wait expired (serving waits) */
   ERI_ESTATE = -7         /* library files missing or inconsistent */
 };
 
@@ -82,14 +82,28 @@ typedef struct {
                            0 auto (4 for plans holding several classes, else 1), 1 serial, at most 8 */
   int32_t digest;       /* 1: also keep on the device what eri_digest_jk / eri_compute_jk need (the quartet list,
                            16 B per quartet); 0: no */
-  int32_t reserved[1];
+  int32_t votes;        /* team-cooperative tier: 0 auto (the class table of eri_set_class_votes, else on for
+                           teams of 128 lanes or more), 1 each lane predicates its optional FP64 terms, 2 each
+                           optional term sits behind a warp vote */
+  int32_t persistent;   /* 1: every class without a compiled register-tier kernel (with tier 4: every class) in
+                           one persistent launch per precision and vote form over a device work list (one
+                           512-thread block per SM takes items -- runs of one class's quartets -- from a
+                           counter); the parts of a quartet reduce into its zeroed block in any order; tier
+                           must be 0 or 4.  0: one launch per class bucket */
 } eri_opts;
 
 typedef struct eri_plan_s eri_plan_t;
 typedef struct eri_mol_s eri_mol_t;
 
 /* Build a plan for nq shell quartets (quartets = [nq][4] shell indices, any
- * order, host memory).  Validates every input, canonicalises each quartet to
+ * order, host memory).  What the plan evaluates is the contracted integral
+ * (ab|cd) of Sec. II-A, Eq. 1, by the steps of Algorithm 2: per primitive
+ * pair the Gaussian-product data (zeta, P, K_AB), per primitive quartet the
+ * Boys function and the vertical recurrence of Eq. 2 (and its ket mirror) in
+ * the axis order of Algorithm 1 and the DSA order of Eq. 7, contraction into
+ * the accumulator bank, then per shell quartet the horizontal recurrence of
+ * Eq. 3 with the spherical transform fused stepwise (Sec. III-B, Eq. 16).
+ * Validates every input, canonicalises each quartet to
  * its class and orientation, uploads basis, pair list and quartet records to
  * the current CUDA device and sizes the scratch.  Host inputs are copied;
  * the plan owns its device memory.  nq may be 0, and is at most 2^31 - 1
@@ -159,7 +173,10 @@ int64_t eri_output_count(const eri_plan_t* plan);
 int eri_output_offsets(const eri_plan_t* plan, int64_t* offsets);
 
 /* Evaluate every quartet of the plan into out (device memory, at least
- * eri_output_count doubles, 8-byte aligned), asynchronously on stream
+ * eri_output_count doubles, 8-byte aligned): the blocks (ab|cd) of Eq. 1 as
+ * Algorithm 2 computes them, minus its J/K scatter (see eri_digest_jk), with
+ * the final transform of Eq. 16 (or Eq. 17 / Cartesian per opts.sph_mode).
+ * Asynchronous on stream
  * (a cudaStream_t; NULL = the legacy default stream).  Kernel launch errors
  * are returned; the caller synchronises the stream to observe completion. */
 int eri_compute(eri_plan_t* plan, double* out, void* stream);
@@ -215,7 +232,11 @@ int eri_digest_jk(eri_plan_t* plan, const double* blocks, const double* density,
                   double* K, void* stream);
 
 /* eri_compute into a plan-owned device buffer followed by eri_digest_jk on
- * the same stream: J and K of a density without handing the blocks out. */
+ * the same stream: J and K of a density without handing the blocks out.  For
+ * a persistent plan (opts.persistent = 1 and opts.digest = 1) the digestion
+ * is fused into the evaluation launch: the team that completes a quartet's
+ * last part digests its block while it is in L2 (the block is still written
+ * to the plan's buffer). */
 int eri_compute_jk(eri_plan_t* plan, const double* density, int32_t nbf, double* J, double* K, void* stream);
 
 /* Evaluate like eri_compute without allocating: for callers that may not
@@ -237,7 +258,8 @@ int eri_compute_jk(eri_plan_t* plan, const double* density, int32_t nbf, double*
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture.
  *  - Every call shares the one array and the kernels reinitialise what they
- *    read (accumulators are zeroed per quartet), so nothing is carried
+ *    read (accumulators are zeroed per quartet; a plan whose parts add into
+ *    their blocks has out zeroed first, by a memset), so nothing is carried
  *    between calls; calls that overlap on the GPU (other streams, other
  *    host threads) race on the array and must be serialised by the caller.
  * Returns ERI_EUNSUPPORTED for a plan with non-global tiers. */
@@ -256,6 +278,12 @@ int eri_schwarz(const eri_plan_t* plan, const double* blocks, double* bounds, vo
  * Applies to plans built afterwards, process-wide. */
 int eri_set_class_tier(int la, int lb, int lc, int ld, int tier);
 
+/* Preferred form of the team-cooperative program for a class (la lb | lc ld)
+ * where a plan leaves eri_opts.votes at 0 (auto): 1 optional FP64 terms
+ * predicated per lane, 2 skipped by warp vote; 0 clears the entry (written by
+ * the autotuner).  Applies to plans built afterwards, process-wide. */
+int eri_set_class_votes(int la, int lb, int lc, int ld, int votes);
+
 /* Capture eri_compute(plan, out, stream) into a CUDA graph held by the plan
  * (stream must not be the legacy default stream; launch timing is off in the
  * graph), and replay it with eri_plan_graph_launch: all of the plan's class
@@ -267,6 +295,15 @@ int eri_plan_graph_launch(eri_plan_t* plan, void* stream);
  * frees its memory stream-ordered on its stream and returns at once; any
  * other plan synchronises the device first. */
 int eri_plan_destroy(eri_plan_t* plan);
+
+/* Diagnostic: the device Boys function on its own.  F_m(T) = int_0^1
+ * t^(2m) exp(-T t^2) dt (Sec. II-A, the base of Eq. 2) for m = 0..L, for each
+ * of n arguments T[i] >= 0 (device memory), into F (device, [n][L + 1]),
+ * asynchronously on stream.  form selects the routine of one tier: 0 the
+ * compiled register-tier kernels' (compile-time order), 1 the
+ * team-cooperative executor's, 2 the thread-per-quartet executor's.
+ * Errors: ERI_EINVAL for L outside 0..16, a bad form or NULL pointers. */
+int eri_boys_eval(const double* T, int64_t n, int32_t L, int32_t form, double* F, void* stream);
 
 /* Message for the calling thread's last error ("" if none). */
 const char* eri_last_error(void);

@@ -19,6 +19,7 @@ import hashlib
 import math
 import multiprocessing as mp
 import os
+import re
 import shutil
 import struct
 import subprocess
@@ -93,9 +94,10 @@ def _class_job(args):
         # the reduced-precision form (FP32 recurrences) of the same schedule
         rec["cuda_f32"] = emit_cuda.emit_class(prog, "reg", real="float")
         rec["kname_f32"] = emit_cuda.kernel_name(ls, "reg", real="float")
-    if (want_reg and rec["size"] > REG_TIER_MAX) or force_coop:
-        # team-cooperative form: one warp per primitive quartet while four
-        # teams' live sets fit in shared memory, else four warps
+    if want_reg or force_coop:
+        # team-cooperative form of every class (the tier of the classes too
+        # large for straight-line code; for the others an alternative the
+        # autotuner and the persistent launch can take)
         from paper_2605_10312_gb300.gen import coop
 
         def pack(cp):
@@ -103,7 +105,7 @@ def _class_job(args):
                         steps1=cp.steps1.tobytes(), steps2=cp.steps2.tobytes(), nw1=int(cp.steps1.shape[0]),
                         nw2=int(cp.steps2.shape[0]), ph1=cp.ph1.tobytes(), ph2=cp.ph2.tobytes(),
                         n1=int(cp.ph1.shape[0]), n2=int(cp.ph2.shape[0]), eff1=cp.eff1, eff2=cp.eff2,
-                        issue=coop.fp64_issue(cp))
+                        issue=coop.fp64_issue(cp), lag=cp.lag)
         deep, shallow = coop.choose_both(prog)
         for cp in (deep, shallow):
             if cp is not None:
@@ -130,7 +132,7 @@ def generate(classes, opts=("prose", "dsa", "stepwise"), want_reg=True, jobs=Non
 
 def write_blob(path, recs, boys, c2s):
     with open(path + ".tmp", "wb") as f:
-        f.write(b"ERIPRG01")
+        f.write(b"ERIPRG02")
         f.write(struct.pack("<I", boys.size))
         f.write(np.ascontiguousarray(boys, dtype="<f8").tobytes())
         f.write(struct.pack("<I", len(c2s)))
@@ -155,8 +157,8 @@ def _write_coops(f, coops, key):
     for r in coops:
         o, c = r["opts"], r[key]
         f.write(struct.pack("<8b", *r["ls"], AXIS[o[0]], SCHED[o[1]], SPH[o[2]], c["ilp"]))
-        f.write(struct.pack("<12i", c["T"], c["nh"], c["nslot"], c["L"], c["nw1"], c["nw2"], c["n1"], c["n2"],
-                            *c["dims"]))
+        f.write(struct.pack("<13i", c["T"], c["nh"], c["nslot"], c["L"], c["nw1"], c["nw2"], c["n1"], c["n2"],
+                            *c["dims"], c["lag"]))
         f.write(struct.pack("<2d", r["flops_prim"], r["flops_p2"]))
         f.write(c["steps1"])
         f.write(c["steps2"])
@@ -187,7 +189,13 @@ def _write_if_changed(path, text):
 
 def _compile(src, obj, extra=()):
     key = hashlib.sha256()
-    for p in [src, os.path.join(CSRC, "eri_common.cuh"), os.path.join(ROOT, "include", "eri.h")]:
+    heads = [os.path.join(CSRC, "eri_common.cuh"), os.path.join(ROOT, "include", "eri.h")]
+    # project headers the unit includes by name
+    for name in re.findall(r'^#include "([^"]+)"', open(src).read(), flags=re.M):
+        h = os.path.join(CSRC, name)
+        if os.path.exists(h) and h not in heads:
+            heads.append(h)
+    for p in [src] + heads:
         key.update(open(p, "rb").read())
     key.update(" ".join(NVCC_ARCH + NVCC_FLAGS + list(extra)).encode())
     stamp = obj + ".key"

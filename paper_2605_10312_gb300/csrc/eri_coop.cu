@@ -15,25 +15,11 @@
 // team-private global region (L2-resident).  Operand ids: id < nh is H[id],
 // id >= nh is value slot id - nh; slots beyond the shared-memory part spill to
 // a team-private global region.
-#include "eri_common.cuh"
+#include <algorithm>
 
-struct EriCoopArgs {
-  const uint4* __restrict__ ph1;      // Phase-1 descriptors, waves of steps x T
-  const uint32_t* __restrict__ steps1;
-  const uint4* __restrict__ ph2;      // Phase-2 descriptors
-  const uint32_t* __restrict__ steps2;
-  const double* __restrict__ c2s;     // transform coefficient table
-  double* __restrict__ gvals;         // unused: every value slot is in shared memory
-  double* __restrict__ gH;            // [team][nh] when H is not in shared memory
-  int32_t nw1, nw2;
-  int32_t nh, nslot, L;
-  int32_t smem_slots;                 // value slots held in shared memory
-  int32_t h_in_smem;
-  int32_t nteams;                     // teams in the grid
-  int32_t batch;                      // coefficient rows per team (1..ERI_COOP_BATCH)
-  int32_t single;                     // every quartet has one primitive quartet: the rows of
-                                      // `batch` consecutive quartets of a team are computed together
-};
+#include "eri_common.cuh"
+#include "eri_coop.cuh"
+
 
 __device__ __forceinline__ double eri_coop_pick8(int k, const double (&t)[8]) {
   double r = t[0];
@@ -62,18 +48,6 @@ __device__ __forceinline__ void eri_coop_boys(int L, double T, double* F, const 
     F[0] = 0.88622692545275801365 * rt;
     const double h = 0.5 * rt * rt;
     for (int m = 0; m < L; ++m) F[m + 1] = fma((double)(2 * m + 1), F[m], -ex) * h;
-  }
-}
-
-template <int T>
-__device__ __forceinline__ void eri_team_sync() {
-  if (T == 32) {
-    __syncwarp();
-  } else if (T >= 128) {
-    __syncthreads();  // one team per block
-  } else {
-    // two teams of 64 lanes per 128-thread block: named barriers 1 and 2
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / T)), "r"(T) : "memory");
   }
 }
 
@@ -137,16 +111,42 @@ __device__ __forceinline__ void eri_coop_load1(const uint4& d, const R* V, EriCo
   if (meta & (15u << 9)) v.e = V[d.w & 0xFFFF];
 }
 
-template <typename R>
+// Every lane of the warp calls this (no-op lanes included).  A warp issues
+// an FP64 instruction when any of its lanes executes it.  VOTE: each
+// optional part of the node sits behind a warp vote, so a warp none of whose
+// lanes needs it skips it (lanes are packed by node shape, so most warps
+// agree); else the parts are predicated per lane and the compiler decides.
+template <bool VOTE, typename R>
 __device__ __forceinline__ R eri_coop_eval1(const uint4& d, const R* row, const EriCoopOps<R>& v) {
   const unsigned meta = d.w >> 16;
   const unsigned k = (meta >> 4) & 31;
-  if (meta & 0x4000u) return row[k];  // base node: pref * F_m
-  const unsigned cgo = meta & 15, k3 = (meta >> 9) & 15, side = (meta >> 13) & 1;
-  R x = row[17 + cgo] * v.a;
-  x = eri_fma(row[20 + cgo], v.b, x);
-  if (k) x = eri_fma(row[28 + 8 * side + k], eri_fma(row[53 + side], v.d, v.c), x);
-  if (k3) x = eri_fma(row[44 + k3], v.e, x);
+  if (!VOTE) {
+    if (meta & 0x4000u) return row[k];  // base node: pref * F_m
+    const unsigned cgo = meta & 15, k3 = (meta >> 9) & 15, side = (meta >> 13) & 1;
+    R x = row[17 + cgo] * v.a;
+    x = eri_fma(row[20 + cgo], v.b, x);
+    if (k) x = eri_fma(row[28 + 8 * side + k], eri_fma(row[53 + side], v.d, v.c), x);
+    if (k3) x = eri_fma(row[44 + k3], v.e, x);
+    return x;
+  }
+  const bool term = (meta & 0xC000u) == 0;
+  const bool t2 = term && k != 0, t3 = term && (meta & (15u << 9)) != 0;
+  R x = (meta & 0x4000u) ? row[k] : (R)0;  // base node: pref * F_m
+  if (__any_sync(0xffffffffu, term)) {
+    const unsigned cgo = meta & 15;
+    if (term) {
+      x = row[17 + cgo] * v.a;
+      x = eri_fma(row[20 + cgo], v.b, x);
+    }
+  }
+  if (__any_sync(0xffffffffu, t2)) {
+    const unsigned side = (meta >> 13) & 1;
+    if (t2) x = eri_fma(row[28 + 8 * side + k], eri_fma(row[53 + side], v.d, v.c), x);
+  }
+  if (__any_sync(0xffffffffu, t3)) {
+    const unsigned k3 = (meta >> 9) & 15;
+    if (t3) x = eri_fma(row[44 + k3], v.e, x);
+  }
   return x;
 }
 
@@ -184,25 +184,33 @@ __device__ __forceinline__ void eri_coop_load2(const uint4& d, const Ptr& ptr, R
   }
 }
 
-template <typename R, typename Ptr>
+template <bool VOTE, typename R, typename Ptr>
 __device__ __forceinline__ void eri_coop_exec2(const uint4& d, const R (&v)[4], const EriPairRec& bra,
                                                const EriPairRec& ket, const EriQuartetRec& qr, double* o, bool acc,
                                                bool red, const double* __restrict__ c2s, const Ptr& ptr) {
+  // every lane of the warp calls this; with VOTE the FP64 parts sit behind
+  // warp votes (see eri_coop_eval1)
   const int kind = d.x & 3;
   const unsigned dst = d.x >> 16;
-  if (kind == 0) {
-    const int ax = d.z;
-    const R X = (R)(ax < 3 ? eri_coop_pick3(ax, bra.AB[0], bra.AB[1], bra.AB[2])
-                           : eri_coop_pick3(ax - 3, ket.AB[0], ket.AB[1], ket.AB[2]));
-    *ptr(dst) = eri_fma(X, v[1], v[0]);
-  } else if (kind == 1) {
-    const int nt = (d.x >> 2) & 7;
-    R x = (R)__ldg(c2s + (d.w & 255)) * v[0];
-    if (nt > 1) x = eri_fma((R)__ldg(c2s + ((d.w >> 8) & 255)), v[1], x);
-    if (nt > 2) x = eri_fma((R)__ldg(c2s + ((d.w >> 16) & 255)), v[2], x);
-    if (nt > 3) x = eri_fma((R)__ldg(c2s + (d.w >> 24)), v[3], x);
-    *ptr(dst) = x;
-  } else if (kind == 2) {
+  const int nt = kind == 1 ? (d.x >> 2) & 7 : 0;
+  if (!VOTE || __any_sync(0xffffffffu, kind == 0)) {
+    if (kind == 0) {
+      const int ax = d.z;
+      const R X = (R)(ax < 3 ? eri_coop_pick3(ax, bra.AB[0], bra.AB[1], bra.AB[2])
+                             : eri_coop_pick3(ax - 3, ket.AB[0], ket.AB[1], ket.AB[2]));
+      *ptr(dst) = eri_fma(X, v[1], v[0]);
+    }
+  }
+  if (!VOTE || __any_sync(0xffffffffu, nt > 0)) {
+    if (nt > 0) {
+      R x = (R)__ldg(c2s + (d.w & 255)) * v[0];
+      if (nt > 1) x = eri_fma((R)__ldg(c2s + ((d.w >> 8) & 255)), v[1], x);
+      if (nt > 2) x = eri_fma((R)__ldg(c2s + ((d.w >> 16) & 255)), v[2], x);
+      if (nt > 3) x = eri_fma((R)__ldg(c2s + (d.w >> 24)), v[3], x);
+      *ptr(dst) = x;
+    }
+  }
+  if (kind == 2) {
     // the block store (and any accumulation into the output) is FP64
     const int64_t off = (int64_t)(d.z & 255) * qr.st[0] + (int64_t)((d.z >> 8) & 255) * qr.st[1] +
                         (int64_t)((d.z >> 16) & 255) * qr.st[2] + (int64_t)(d.z >> 24) * qr.st[3];
@@ -210,28 +218,44 @@ __device__ __forceinline__ void eri_coop_exec2(const uint4& d, const R (&v)[4], 
   }
 }
 
-// HSM: the accumulators H share the team's shared-memory region with the
-// value slots ([H | slots], operand id = offset); otherwise H is a
-// team-private global region and slots follow at id - nh.
+// Team barrier for a team size known at compile time (TC > 0) or only at
+// run time (TC == 0, the persistent launch): __syncwarp for one warp, the
+// block barrier for a team that is the whole block (TC >= 128), else the
+// named barrier 1 + team with the team's thread count.
+template <int TC>
+struct EriTeamBarrier {
+  int T, tb;
+  __device__ __forceinline__ void operator()() const {
+    if (TC == 32 || (TC == 0 && T == 32)) {
+      __syncwarp();
+    } else if (TC >= 128) {
+      __syncthreads();  // one team per block
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + tb), "r"(T) : "memory");
+    }
+  }
+};
+
+// One team's quartets: q = q0, q0 + stride, ... < a.nq, each through its
+// primitive quartets (Phase 1, wave by wave) and Phase 2 with the stores.
+// rows: the team's shared-memory region [coefficient rows | H when hsm |
+// value slots]; Hg: the team's private global H otherwise.  TC / HSMC fix
+// the team size and the H placement at compile time (HSMC = -1: at run
+// time).
 // R: value type of the recurrences, the contraction sums H, HRR and the
 // transform -- double, or float for the reduced-precision form (coefficient
 // rows and the Boys function are still formed in FP64; stores are FP64).
-// Blocks are 128 threads (teams of up to 128 lanes) or one team of 256 or
-// 512 lanes; every shape keeps the 128 registers per thread that two nodes
-// per lane need (four nodes per lane: 255, at most 256 threads per SM).
-template <typename R, int T, bool HSM, int ILP>
-__global__ void __launch_bounds__(T > 128 ? T : 128,
-                                  T > 256 ? 1 : T > 128 ? (ILP == 4 ? 1 : 2) : (ILP == 4 ? 2 : 4))
-    eri_coop_kernel(const EriLaunchArgs a, const EriCoopArgs p) {
-  extern __shared__ double eri_coop_smem[];
-  const int tb = threadIdx.x / T;           // team within the block
-  const int l = threadIdx.x - tb * T;       // lane within the team
-  const int team = blockIdx.x * (blockDim.x / T) + tb;
-  const int per_team = p.batch * ERI_COOP_NC + (HSM ? p.nh : 0) + p.nslot;
-  R* const rows = reinterpret_cast<R*>(eri_coop_smem) + (size_t)tb * per_team;
+template <typename R, int ILP, bool VOTE, int TC, int HSMC, typename Bar>
+__device__ __forceinline__ void eri_coop_team(const EriLaunchArgs& a, const EriCoopArgs& p, const int T_rt,
+                                              const bool hsm_rt, const int q0, const int stride, const int l,
+                                              R* const rows, R* const Hg, const Bar& team_sync,
+                                              const EriFuse* fuse = nullptr, int64_t rec0 = 0,
+                                              int* team_word = nullptr) {
+  const int T = TC ? TC : T_rt;
+  const bool HSM = HSMC >= 0 ? HSMC != 0 : hsm_rt;
   R* const Hsm = rows + p.batch * ERI_COOP_NC;                        // H when HSM
   R* const V = Hsm + (HSM ? p.nh : 0);                              // value slots (shared)
-  R* const Hs = HSM ? Hsm : reinterpret_cast<R*>(p.gH) + (size_t)team * p.nh;
+  R* const Hs = HSM ? Hsm : Hg;
   const unsigned nh = (unsigned)p.nh;
   // Phase-2 operand id -> address: H below nh, value slots above
   auto ptr = [&](unsigned id) -> R* { return id < nh ? Hs + id : V + (id - nh); };
@@ -240,14 +264,14 @@ __global__ void __launch_bounds__(T > 128 ? T : 128,
   // (one lane each) rather than one row per quartet on one lane
   const bool single = p.single != 0;
   int gi = 0;  // single: position of quartet q in its group of rows
-  for (int q = team; q < a.nq; q += p.nteams) {
+  for (int q = q0; q < a.nq; q += stride) {
     const EriQuartetRec qr = a.quartets[q];
     const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];
     const bool acc = ERI_ACCUMULATE(qr.bra);
     const bool red = ERI_REDUCE(qr.bra);
     const EriPairRec ket = a.pairs[qr.ket];
     if (single && gi == 0) {
-      const int qi = q + l * p.nteams;
+      const int qi = q + l * stride;
       if (l < p.batch && qi < a.nq) {
         const EriQuartetRec r = a.quartets[qi];
         eri_coop_row(a.pprims[a.pairs[ERI_PAIR_INDEX(r.bra)].prim_off], a.pprims[a.pairs[r.ket].prim_off], p.L,
@@ -265,7 +289,7 @@ __global__ void __launch_bounds__(T > 128 ? T : 128,
         eri_coop_row(a.pprims[bra.prim_off + i], a.pprims[ket.prim_off + j], p.L, a.boys_tab,
                      rows + l * ERI_COOP_NC);
       }
-      eri_team_sync<T>();
+      team_sync();
       for (int pi = 0; pi < nb; ++pi) {
         const R* const row = rows + (single ? gi : pi) * ERI_COOP_NC;
         // a step gives each lane ILP descriptors (independent nodes of the
@@ -290,7 +314,7 @@ __global__ void __launch_bounds__(T > 128 ? T : 128,
             for (int u = 0; u < ILP; ++u) eri_coop_load1(d[u], V, v[u]);
             R x[ILP];
 #pragma unroll
-            for (int u = 0; u < ILP; ++u) x[u] = eri_coop_eval1(d[u], row, v[u]);
+            for (int u = 0; u < ILP; ++u) x[u] = eri_coop_eval1<VOTE>(d[u], row, v[u]);
 #pragma unroll
             for (int u = 0; u < ILP; ++u) {
               if (HSM)
@@ -304,7 +328,7 @@ __global__ void __launch_bounds__(T > 128 ? T : 128,
               dn[u] = dnn[u];
             }
           }
-          eri_team_sync<T>();
+          team_sync();
         }
       }
     }
@@ -328,44 +352,195 @@ __global__ void __launch_bounds__(T > 128 ? T : 128,
 #pragma unroll
         for (int u = 0; u < ILP; ++u) eri_coop_load2(d[u], ptr, v[u]);
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) eri_coop_exec2(d[u], v[u], bra, ket, qr, o, acc, red, p.c2s, ptr);
+        for (int u = 0; u < ILP; ++u) eri_coop_exec2<VOTE>(d[u], v[u], bra, ket, qr, o, acc, red, p.c2s, ptr);
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
           d[u] = dn[u];
           dn[u] = dnn[u];
         }
       }
-      eri_team_sync<T>();
+      team_sync();
+    }
+    if (fuse != nullptr) {
+      // J/K of the block once its last part is in: a quartet of several
+      // parts (orientations, chunks) is digested by the team that brings its
+      // count of finished parts to the total; every lane's stores and
+      // reductions reach L2 before the count (fence, then the team barrier
+      // that the Phase-2 loop ended with), and the block is read from L2
+      const int32_t qu = fuse->rec_q[rec0 + q];
+      const int32_t np = fuse->nparts[qu];
+      bool last = true;
+      if (np > 1) {
+        __threadfence();
+        team_sync();
+        if (l == 0) *team_word = atomicAdd(fuse->done + qu, 1) == np - 1 ? 1 : 0;
+        team_sync();
+        last = *team_word != 0;
+      }
+      if (last) {
+        __threadfence();
+        eri_digest_quartet(fuse->jk, qu, l, T, fuse->jk.blocks + fuse->jk.offsets[qu],
+                           [](const double* p) { return __ldcg(p); });
+      }
+      team_sync();  // team_word is rewritten for the next quartet
     }
     if (single && ++gi == p.batch) gi = 0;
   }
 }
 
-#define ERI_COOP_FNS_T(R, I)                                                                      \
-  (const void*)eri_coop_kernel<R, 32, true, I>, (const void*)eri_coop_kernel<R, 32, false, I>,     \
-      (const void*)eri_coop_kernel<R, 64, true, I>, (const void*)eri_coop_kernel<R, 64, false, I>, \
-      (const void*)eri_coop_kernel<R, 128, true, I>, (const void*)eri_coop_kernel<R, 128, false, I>, \
-      (const void*)eri_coop_kernel<R, 256, true, I>, (const void*)eri_coop_kernel<R, 256, false, I>
+// One launch per class bucket.  HSM: the accumulators H share the team's
+// shared-memory region with the value slots ([H | slots], operand id =
+// offset); otherwise H is a team-private global region and slots follow at
+// id - nh.  Blocks are 128 threads (teams of up to 128 lanes) or one team of
+// 256 or 512 lanes; every shape keeps the 128 registers per thread that two
+// nodes per lane need (four nodes per lane: 255, at most 256 threads per SM).
+template <typename R, int T, bool HSM, int ILP, bool VOTE>
+__global__ void __launch_bounds__(T > 128 ? T : 128,
+                                  T > 256 ? 1 : T > 128 ? (ILP == 4 ? 1 : 2) : (ILP == 4 ? 2 : 4))
+    eri_coop_kernel(const EriLaunchArgs a, const EriCoopArgs p) {
+  extern __shared__ double eri_coop_smem[];
+  const int tb = threadIdx.x / T;           // team within the block
+  const int l = threadIdx.x - tb * T;       // lane within the team
+  const int team = blockIdx.x * (blockDim.x / T) + tb;
+  const int per_team = p.batch * ERI_COOP_NC + (HSM ? p.nh : 0) + p.nslot;
+  R* const rows = reinterpret_cast<R*>(eri_coop_smem) + (size_t)tb * per_team;
+  R* const Hg = HSM ? nullptr : reinterpret_cast<R*>(p.gH) + (size_t)team * p.nh;
+  eri_coop_team<R, ILP, VOTE, T, HSM ? 1 : 0>(a, p, T, HSM, team, p.nteams, l, rows, Hg, EriTeamBarrier<T>{T, tb});
+}
+
+// Persistent launch over a device work list (one block of 512 threads per
+// SM).  Each item is a run of quartet records of one class program with its
+// team shape: the block takes the next item from a global counter, forms
+// item.teams teams of item.T lanes (threads beyond them wait for the next
+// item), and its teams stride over the item's quartets.  Every cooperative
+// class of a plan -- any team size, H placement and vote form -- goes
+// through one launch of this kernel per precision.
+template <typename R, bool VOTE>
+__global__ void __launch_bounds__(512, 1) eri_coop_persist_kernel(const EriLaunchArgs a0, const EriPersistArgs pa) {
+  extern __shared__ double eri_coop_smem[];
+  // the current item's arguments, read by the teams from shared memory (not
+  // held in registers across the item's loops)
+  __shared__ EriCoopArgs ps;
+  __shared__ EriLaunchArgs as;
+  __shared__ EriWorkItem ws;
+  __shared__ int item_s;
+  __shared__ int team_words[16];  // one per team (fused digestion)
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(pa.next, 1);
+      item_s = it;
+      if (it < pa.nitems) {
+        const EriWorkItem w = pa.items[it];
+        const EriCoopProgDesc g = pa.progs[w.prog];
+        ws = w;
+        ps.ph1 = g.ph1;
+        ps.steps1 = g.steps1;
+        ps.ph2 = g.ph2;
+        ps.steps2 = g.steps2;
+        ps.c2s = pa.c2s;
+        ps.gvals = nullptr;
+        ps.gH = pa.gH;
+        ps.nw1 = g.nw1;
+        ps.nw2 = g.nw2;
+        ps.nh = g.nh;
+        ps.nslot = g.nslot;
+        ps.L = g.L;
+        ps.smem_slots = g.nslot;
+        ps.h_in_smem = w.hsm;
+        ps.nteams = w.teams;
+        ps.batch = w.batch;
+        ps.single = w.single;
+        as = a0;
+        as.quartets = a0.quartets + w.first;
+        as.nq = w.count;
+      }
+    }
+    __syncthreads();
+    if (item_s >= pa.nitems) break;
+    const int T = ws.T, teams = ws.teams;
+    const bool hsm = ws.hsm != 0;
+    const int tb = threadIdx.x / T, l = threadIdx.x - tb * T;
+    if (tb < teams) {
+      const int per_team = ps.batch * ERI_COOP_NC + (hsm ? ps.nh : 0) + ps.nslot;
+      R* const rows = reinterpret_cast<R*>(eri_coop_smem) + (size_t)tb * per_team;
+      R* const Hg = reinterpret_cast<R*>(pa.gH) + (size_t)blockIdx.x * pa.gh_per_block + (size_t)tb * ps.nh;
+      const EriTeamBarrier<0> bar{T, tb};
+      eri_coop_team<R, 2, VOTE, 0, -1>(as, ps, T, hsm, tb, teams, l, rows, Hg, bar, pa.fuse.on ? &pa.fuse : nullptr,
+                                       (int64_t)ws.first, team_words + tb);
+    }
+    __syncthreads();  // the item's shared memory is free, the item may be rewritten
+  }
+}
+
+static const void* const eri_coop_persist_fns[] = {
+    (const void*)eri_coop_persist_kernel<double, false>, (const void*)eri_coop_persist_kernel<double, true>,
+    (const void*)eri_coop_persist_kernel<float, false>, (const void*)eri_coop_persist_kernel<float, true>};
+
+extern "C" cudaError_t eri_coop_persist_launch(int fp32, int vote, const EriLaunchArgs* a, const EriPersistArgs* pa,
+                                               int grid, size_t smem, cudaStream_t stream) {
+  EriLaunchArgs aa = *a;
+  EriPersistArgs pp = *pa;
+  void* args[] = {&aa, &pp};
+  return cudaLaunchKernel(eri_coop_persist_fns[2 * (fp32 ? 1 : 0) + (vote ? 1 : 0)], dim3(grid), dim3(512), args,
+                          smem, stream);
+}
+
+// dynamic shared memory a persistent launch may take: the opt-in limit less
+// the static shared memory of its kernels (the current item)
+extern "C" size_t eri_coop_persist_smem_max(size_t optin) {
+  size_t s = 0;
+  for (const void* f : eri_coop_persist_fns) {
+    cudaFuncAttributes at;
+    if (cudaFuncGetAttributes(&at, f) != cudaSuccess) return 0;
+    s = std::max(s, at.sharedSizeBytes);
+  }
+  return optin - s;
+}
+
+#define ERI_COOP_FNS_T(R, I, V)                                                                               \
+  (const void*)eri_coop_kernel<R, 32, true, I, V>, (const void*)eri_coop_kernel<R, 32, false, I, V>,           \
+      (const void*)eri_coop_kernel<R, 64, true, I, V>, (const void*)eri_coop_kernel<R, 64, false, I, V>,       \
+      (const void*)eri_coop_kernel<R, 128, true, I, V>, (const void*)eri_coop_kernel<R, 128, false, I, V>,     \
+      (const void*)eri_coop_kernel<R, 256, true, I, V>, (const void*)eri_coop_kernel<R, 256, false, I, V>
 // 512-lane teams exist with two nodes per lane only (four would need more
 // registers than a 512-thread block can hold)
-#define ERI_COOP_FNS(R)                                                                                     \
-  ERI_COOP_FNS_T(R, 2), (const void*)eri_coop_kernel<R, 512, true, 2>, (const void*)eri_coop_kernel<R, 512, false, 2>, \
-      ERI_COOP_FNS_T(R, 4), nullptr, nullptr
+#define ERI_COOP_FNS_V(R, V)                                                                                   \
+  ERI_COOP_FNS_T(R, 2, V), (const void*)eri_coop_kernel<R, 512, true, 2, V>,                                    \
+      (const void*)eri_coop_kernel<R, 512, false, 2, V>, ERI_COOP_FNS_T(R, 4, V), nullptr, nullptr
 
-// every instantiation, indexed [fp32][ilp 4][T 32/64/128/256/512][H not in shared memory]
-static const void* const eri_coop_fns[] = {ERI_COOP_FNS(double), ERI_COOP_FNS(float)};
+// every instantiation, indexed [vote][fp32][ilp 4][T 32/64/128/256/512][H not in shared memory]
+static const void* const eri_coop_fns[] = {ERI_COOP_FNS_V(double, false), ERI_COOP_FNS_V(float, false),
+                                           ERI_COOP_FNS_V(double, true), ERI_COOP_FNS_V(float, true)};
 
-extern "C" cudaError_t eri_coop_launch(int T, int ilp, int fp32, const EriLaunchArgs* a, const EriCoopArgs* p,
-                                       int grid, int block, size_t smem, cudaStream_t stream) {
+extern "C" cudaError_t eri_coop_launch(int T, int ilp, int fp32, int vote, const EriLaunchArgs* a,
+                                       const EriCoopArgs* p, int grid, int block, size_t smem, cudaStream_t stream) {
   const int ti = T == 32 ? 0 : T == 64 ? 1 : T == 128 ? 2 : T == 256 ? 3 : T == 512 ? 4 : -1;
   if (ti < 0 || (ilp != 2 && ilp != 4)) return cudaErrorInvalidValue;
   if (block != (T > 128 ? T : 128) && !(T <= 128 && block % T == 0 && block <= 128)) return cudaErrorInvalidValue;
-  const int idx = (fp32 ? 20 : 0) + (ilp == 4 ? 10 : 0) + 2 * ti + (p->h_in_smem ? 0 : 1);
+  const int idx = (vote ? 40 : 0) + (fp32 ? 20 : 0) + (ilp == 4 ? 10 : 0) + 2 * ti + (p->h_in_smem ? 0 : 1);
   if (eri_coop_fns[idx] == nullptr) return cudaErrorInvalidValue;
   EriLaunchArgs aa = *a;
   EriCoopArgs pp = *p;
   void* args[] = {&aa, &pp};
   return cudaLaunchKernel(eri_coop_fns[idx], dim3(grid), dim3(block), args, smem, stream);
+}
+
+// Diagnostic: F_0..F_L(T[i]) by this tier's Boys routine, one thread per
+// argument (F is [n][L + 1]).
+__global__ void eri_coop_boys_kernel(const double* __restrict__ T, int64_t n, int L, const double* __restrict__ tab,
+                                     double* __restrict__ F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double f[ERI_BOYS_LMAX + 1];
+  eri_coop_boys(L, T[i], f, tab);
+  for (int m = 0; m <= L; ++m) F[i * (L + 1) + m] = f[m];
+}
+
+extern "C" cudaError_t eri_coop_boys_launch(const double* T, int64_t n, int L, const double* tab, double* F,
+                                            cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  eri_coop_boys_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(T, n, L, tab, F);
+  return cudaGetLastError();
 }
 
 // shared memory of one coefficient row, in elements, and the largest batch
@@ -376,6 +551,14 @@ extern "C" cudaError_t eri_coop_set_smem(size_t bytes) {
   for (const void* f : eri_coop_fns) {
     if (f == nullptr) continue;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
+  // the persistent kernels hold their current item in static shared memory
+  for (const void* f : eri_coop_persist_fns) {
+    cudaFuncAttributes at;
+    cudaError_t e = cudaFuncGetAttributes(&at, f);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes - at.sharedSizeBytes));
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

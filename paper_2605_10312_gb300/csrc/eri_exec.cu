@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(128) eri_exec_kernel(const EriLaunchArgs a, co
     const EriQuartetRec qr = a.quartets[q];
     const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];
     const bool acc = ERI_ACCUMULATE(qr.bra);
+    const bool red = ERI_REDUCE(qr.bra);
     const EriPairRec ket = a.pairs[qr.ket];
     for (int h = 0; h < p.nh; ++h) VAL(h) = 0.0;
     const int kk = ket.nprim;
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(128) eri_exec_kernel(const EriLaunchArgs a, co
         } else {
           const int64_t off = (int64_t)(d.z & 255) * qr.st[0] + (int64_t)((d.z >> 8) & 255) * qr.st[1] +
                               (int64_t)((d.z >> 16) & 255) * qr.st[2] + (int64_t)(d.z >> 24) * qr.st[3];
-          eri_st(o + off, VAL(dst), acc);
+          eri_st(o + off, VAL(dst), acc, red);
         }
       }
     }
@@ -162,6 +163,24 @@ __global__ void __launch_bounds__(128) eri_exec_kernel(const EriLaunchArgs a, co
     if (G > 1) __syncwarp(gmask);
   }
 #undef VAL
+}
+
+// Diagnostic: F_0..F_L(T[i]) by this tier's Boys routine, one thread per
+// argument (F is [n][L + 1]).
+__global__ void eri_exec_boys_kernel(const double* __restrict__ T, int64_t n, int L, const double* __restrict__ tab,
+                                     double* __restrict__ F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double f[ERI_BOYS_LMAX + 1];
+  eri_boys_rt(L, T[i], f, tab);
+  for (int m = 0; m <= L; ++m) F[i * (L + 1) + m] = f[m];
+}
+
+extern "C" cudaError_t eri_exec_boys_launch(const double* T, int64_t n, int L, const double* tab, double* F,
+                                            cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  eri_exec_boys_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(T, n, L, tab, F);
+  return cudaGetLastError();
 }
 
 extern "C" cudaError_t eri_exec_launch(int shared, const EriLaunchArgs* a, const EriProgArgs* p, int grid,

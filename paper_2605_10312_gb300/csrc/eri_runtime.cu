@@ -24,6 +24,8 @@
 
 #include "eri.h"
 #include "eri_common.cuh"
+#include "eri_coop.cuh"
+#include "eri_digest.cuh"
 
 // ---------------------------------------------------------------------------
 // executor and registry (other translation units)
@@ -31,43 +33,21 @@
 extern "C" cudaError_t eri_exec_launch(int shared, const EriLaunchArgs* a, const EriProgArgs* p, int grid,
                                        int block, size_t smem, cudaStream_t stream);
 extern "C" cudaError_t eri_exec_set_smem(size_t bytes);
+extern "C" cudaError_t eri_exec_boys_launch(const double* T, int64_t n, int L, const double* tab, double* F,
+                                            cudaStream_t stream);
+extern "C" cudaError_t eri_coop_boys_launch(const double* T, int64_t n, int L, const double* tab, double* F,
+                                            cudaStream_t stream);
 
-struct EriDigestArgs {
-  const int64_t* list;
-  int64_t nlist;
-  const int32_t* quartets;
-  const int64_t* offsets;
-  const int32_t* shell_bf;
-  const double* blocks;
-  const double* D;
-  double* J;
-  double* K;
-  int64_t nq;
-  int32_t nbf;
-};
 extern "C" cudaError_t eri_digest_launch(const EriDigestArgs* g, int small, cudaStream_t stream);
 // blocks of up to this many elements are digested by one thread each
 static const int64_t kSmallBlock = 128;
 
-struct EriCoopArgs {
-  const uint4* ph1;
-  const uint32_t* steps1;
-  const uint4* ph2;
-  const uint32_t* steps2;
-  const double* c2s;
-  double* gvals;
-  double* gH;
-  int32_t nw1, nw2;
-  int32_t nh, nslot, L;
-  int32_t smem_slots;
-  int32_t h_in_smem;
-  int32_t nteams;
-  int32_t batch;
-  int32_t single;
-};
-extern "C" cudaError_t eri_coop_launch(int T, int ilp, int fp32, const EriLaunchArgs* a, const EriCoopArgs* p,
-                                       int grid, int block, size_t smem, cudaStream_t stream);
+extern "C" cudaError_t eri_coop_launch(int T, int ilp, int fp32, int vote, const EriLaunchArgs* a,
+                                       const EriCoopArgs* p, int grid, int block, size_t smem, cudaStream_t stream);
 extern "C" cudaError_t eri_coop_set_smem(size_t bytes);
+extern "C" cudaError_t eri_coop_persist_launch(int fp32, int vote, const EriLaunchArgs* a, const EriPersistArgs* pa,
+                                               int grid, size_t smem, cudaStream_t stream);
+extern "C" size_t eri_coop_persist_smem_max(size_t optin);
 extern "C" size_t eri_coop_row_elems(void);
 extern "C" int eri_coop_max_batch(void);
 // contractions of at most this many primitive quartets per part use the
@@ -175,7 +155,7 @@ bool load_blob(Library& L, const std::string& path, bool tables) {
   if (!f) return false;
   char magic[8];
   uint32_t nb = 0, nc = 0, ncls = 0;
-  bool ok = rd(f, magic, 8) && memcmp(magic, "ERIPRG01", 8) == 0 && rd(f, &nb);
+  bool ok = rd(f, magic, 8) && memcmp(magic, "ERIPRG02", 8) == 0 && rd(f, &nb);
   std::vector<double> boys(nb);
   ok = ok && rd(f, boys.data(), nb) && rd(f, &nc);
   std::vector<double> c2s(nc);
@@ -214,13 +194,14 @@ bool load_blob(Library& L, const std::string& path, bool tables) {
     for (uint32_t c = 0; ok && c < ncoop; ++c) {
       auto p = std::make_unique<CoopProg>();
       int8_t hdr[8];
-      int32_t iv[12];
+      int32_t iv[13];
       double fv[2];
-      ok = rd(f, hdr, 8) && rd(f, iv, 12) && rd(f, fv, 2);
+      ok = rd(f, hdr, 8) && rd(f, iv, 13) && rd(f, fv, 2);
       if (!ok) break;
       for (int k = 0; k < 4; ++k) p->ls[k] = hdr[k];
       for (int k = 0; k < 3; ++k) p->opts[k] = hdr[4 + k];
       p->ilp = hdr[7] ? hdr[7] : 2;
+      if (iv[12] != 1) ok = false;  // full-barrier programs only
       p->T = iv[0];
       p->nh = iv[1];
       p->nslot = iv[2];
@@ -542,7 +523,7 @@ __global__ void eri_pair_setup_kernel(const DevPairIn* __restrict__ pin, int npa
 // plan
 // ---------------------------------------------------------------------------
 namespace {
-enum Tier { TIER_REG = 1, TIER_SHARED = 2, TIER_GLOBAL = 3, TIER_COOP = 4 };
+enum Tier { TIER_REG = 1, TIER_SHARED = 2, TIER_GLOBAL = 3, TIER_COOP = 4, TIER_PERSIST = 5 };
 
 struct Bucket {
   int ls[4];
@@ -558,10 +539,13 @@ struct Bucket {
   int smem_slots = 0, h_in_smem = 0, nteams = 0;
   int batch = 0;                 // cooperative tier: coefficient rows per team
   int single = 0;                // cooperative tier: every part has one primitive quartet
+  int vote = 0;                  // cooperative tier: optional FP64 terms behind warp votes
   int fp32 = 0;                  // recurrences in FP32 (quartets with a small Schwarz bound)
   int round = 0;                 // part round: buckets of a round are independent
   int lane = 0;                  // stream of its round (0 = the caller's stream)
   bool shared_scratch = false;   // uses the plan's global scratch (runs on lane 0)
+  // persistent plans: launch `pgroup` runs items [item0, item0 + nitems)
+  int pgroup = -1, item0 = 0, nitems = 0;
 };
 
 // Plans built by eri_plan_on_stream allocate stream-ordered on that stream
@@ -665,6 +649,15 @@ struct eri_plan_s {
   DevBuf<double> scratch;
   DevBuf<double> outbuf;
   DevBuf<double> coop_vals, coop_h;  // team-private spill regions of the cooperative tier
+  // persistent plans (eri_opts.persistent): work items, class programs, one
+  // item counter per launch, the team-private H pool
+  bool persistent = false;
+  DevBuf<EriWorkItem> items;
+  DevBuf<EriCoopProgDesc> progs;
+  DevBuf<int32_t> counters;
+  DevBuf<double> persist_h;
+  int64_t persist_h_per_block = 0;
+  DevBuf<int32_t> rec_q, nparts_q, done_q;  // fused digestion: record -> quartet, parts, finished parts
   int64_t scratch_stride = 0;
   double h2d_bytes = 0;
   bool zero_out = false;  // chunks reduce into their block: eri_compute zeroes the output first
@@ -673,6 +666,7 @@ struct eri_plan_s {
   DevBuf<int32_t> d_uq;              // digest plans: the caller's quartet list
   DevBuf<int32_t> d_shell_bf;        // digest plans: first basis function of each shell, and the total
   DevBuf<int64_t> d_small, d_large;  // digest plans: quartets with small / large blocks
+  DevBuf<int64_t> d_rsmall, d_rlarge;  // fused digestion: the same lists for quartets with no persistent part
   int32_t nbf = 0;
   bool digest = false;
   DevBuf<int32_t> d_nab;
@@ -696,6 +690,7 @@ struct eri_plan_s {
 
 static int nfun(int l, bool cart) { return cart ? (l + 1) * (l + 2) / 2 : 2 * l + 1; }
 int preferred_tier(const int ls[4]);
+int preferred_votes(const int ls[4]);
 
 static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
                      int64_t nq, const double* qbound, double fp32_below, const eri_opts* opts_in,
@@ -707,7 +702,8 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   if (opts_in) opts = *opts_in;
   if (opts.axis_rule < 0 || opts.axis_rule > 2 || opts.schedule < 0 || opts.schedule > 1 || opts.sph_mode < 0 ||
       opts.sph_mode > 2 || opts.tier < 0 || opts.tier > 4 || opts.orientation < 0 || opts.orientation > 2 ||
-      opts.streams < 0 || opts.streams > 8 || opts.digest < 0 || opts.digest > 1)
+      opts.streams < 0 || opts.streams > 8 || opts.digest < 0 || opts.digest > 1 || opts.votes < 0 ||
+      opts.votes > 2 || opts.persistent < 0 || opts.persistent > 1)
     return fail(ERI_EINVAL, "option out of range");
   if (mol) {
     shells = mol->shells.data();
@@ -720,6 +716,10 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   // launches take their quartet count as int32
   if (nq > ((int64_t)1 << 31) - 1) return fail(ERI_EINVAL, "too many quartets for one plan (at most 2^31 - 1)");
   const bool cart = opts.sph_mode == 2;
+  // persistent plans run every class on the team-cooperative programs
+  if (opts.persistent && opts.tier != 0 && opts.tier != TIER_COOP)
+    return fail(ERI_EINVAL, "a persistent plan takes tier 0 or 4");
+  const bool persistent = opts.persistent == 1;
   // ---- validation
   if (nshell > 0) {
     if (!basis->centers || !basis->exponents || !basis->coefs || basis->ncenter < 0 || basis->nprim_total < 0)
@@ -776,16 +776,43 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   // chunks of about kCoopChunk primitive quartets (sub-ranges of the bra
   // pair's primitive pairs) that different teams run concurrently.
   const int kCoopChunk = 32;
-  const bool default_opts0 = opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0;
-  // class code ((la * 5 + lb) * 5 + lc) * 5 + ld; per-code answers cached
-  std::vector<int8_t> coop_of(625, -1);
-  auto is_coop = [&](int la, int lb, int lc, int ld) {
-    int8_t& c = coop_of[((la * 5 + lb) * 5 + lc) * 5 + ld];
+  const bool default_opts = opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0;
+  // Tier of a class at a precision: the caller's forced tier; FP32 forms on
+  // the compiled register kernel, else the cooperative program; otherwise the
+  // autotuner's choice when it is feasible, else the static rule (register,
+  // cooperative, shared, global).  0 when no tier can hold the class (the
+  // bucket loop reports why).  Chunking of deep contractions asks the same
+  // question, so only buckets that run on the cooperative tier -- the one
+  // that reduces chunks into their blocks -- are ever chunked.
+  auto route_tier = [&](const int ls[4], int prec) -> int {
+    const std::vector<int> pkey = {ls[0], ls[1], ls[2], ls[3], opts.axis_rule, opts.schedule, opts.sph_mode};
+    auto pit = L.progs.find(pkey);
+    const ClassProg* prog = pit == L.progs.end() ? nullptr : pit->second.get();
+    const bool cp = L.coops.find(pkey) != L.coops.end();
+    const auto& regmap = prec ? L.reg_f32 : L.reg;
+    const bool regfn = default_opts && regmap.find({ls[0], ls[1], ls[2], ls[3]}) != regmap.end();
+    const size_t smem_need = prog ? (size_t)prog->nslot * 128 * sizeof(double) : 0;
+    // persistent plans: the compiled register-tier kernels keep their
+    // classes (launches of their own, before the persistent launch); every
+    // other class goes on the work list (tier 4 forces all of them there)
+    if (persistent) return (opts.tier == 0 && regfn) ? TIER_REG : TIER_COOP;
+    if (opts.tier != 0) return opts.tier;
+    if (prec) return regfn ? TIER_REG : TIER_COOP;
+    const int pt = preferred_tier(ls);
+    const bool ok = (pt == TIER_REG && regfn) || (pt == TIER_COOP && cp) ||
+                    (pt == TIER_SHARED && prog && smem_need <= L.smem_optin) || (pt == TIER_GLOBAL && prog);
+    if (ok) return pt;
+    return regfn ? TIER_REG : cp ? TIER_COOP : (prog && smem_need <= L.smem_optin ? TIER_SHARED : TIER_GLOBAL);
+  };
+  // class code ((la * 5 + lb) * 5 + lc) * 5 + ld, x2 for the precision;
+  // per-code answers cached
+  std::vector<int8_t> coop_of(2 * 625, -1);
+  auto is_coop = [&](int la, int lb, int lc, int ld, int prec) {
+    int8_t& c = coop_of[2 * (((la * 5 + lb) * 5 + lc) * 5 + ld) + prec];
     if (c < 0) {
-      std::vector<int> key = {la, lb, lc, ld, opts.axis_rule, opts.schedule, opts.sph_mode};
-      bool v = L.coops.find(key) != L.coops.end();
-      if (v && opts.tier != TIER_COOP) v = opts.tier == 0 && !(default_opts0 && L.reg.count({la, lb, lc, ld}));
-      c = v ? 1 : 0;
+      const int ls[4] = {la, lb, lc, ld};
+      const std::vector<int> key = {la, lb, lc, ld, opts.axis_rule, opts.schedule, opts.sph_mode};
+      c = (route_tier(ls, prec) == TIER_COOP && L.coops.find(key) != L.coops.end()) ? 1 : 0;
     }
     return c == 1;
   };
@@ -845,8 +872,12 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     int round;  // part number within its quartet: 0 writes the block, later parts add
     int kb, kk;
     int prec;   // 1: FP32 recurrences
+    int32_t uq; // the caller's quartet
     EriQuartetRec rec;
   };
+  // fused digestion (persistent digest plans): parts of every quartet
+  const bool fuse = persistent && opts.digest == 1;
+  std::vector<int32_t> nparts_q(fuse ? nq : 0, 0);
   // reduced precision is offered for the default generator options, where
   // every class has an FP32 form (register or team-cooperative tier)
   const bool mixed = qbound != nullptr && opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0 &&
@@ -887,7 +918,7 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
           cls_keys.push_back({lb0, lb1, lk0, lk1});
         }
         int cb = B.nprim, nchunk = 1;
-        if ((int64_t)B.nprim * K.nprim > kCoopChunk && is_coop(lb0, lb1, lk0, lk1)) {
+        if ((int64_t)B.nprim * K.nprim > kCoopChunk && is_coop(lb0, lb1, lk0, lk1, prec)) {
           cb = std::max(1, kCoopChunk / K.nprim);
           nchunk = (B.nprim + cb - 1) / cb;
         }
@@ -895,18 +926,28 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
           const int start = c * cb, cnt = std::min(cb, B.nprim - start);
           QInfo x;
           const int bpair = nchunk > 1 ? get_alias(B.pair, start, cnt) : B.pair;
-          x.rec.bra = bpair | (round > 0 ? (int32_t)0x80000000 : 0) | (nchunk > 1 ? 0x40000000 : 0);
+          if (persistent) {
+            // one launch: every part of a quartet with several reduces into
+            // its zeroed block, in any order
+            x.rec.bra = bpair | ((nb * nk > 1 || nchunk > 1) ? 0x40000000 : 0);
+          } else {
+            x.rec.bra = bpair | (round > 0 ? (int32_t)0x80000000 : 0) | (nchunk > 1 ? 0x40000000 : 0);
+          }
           x.rec.ket = K.pair;
           x.rec.out_off = plan->offsets[q];
           for (int k = 0; k < 4; ++k) x.rec.st[k] = ustride[pos[k]];
           x.cls = cidx;
-          x.round = round;
+          x.round = persistent ? 0 : round;
           x.kb = cnt;
           x.kk = K.nprim;
           x.prec = prec;
+          x.uq = (int32_t)q;
+          // fused digestion counts the parts the persistent launch runs; a
+          // quartet whose every part is register-tier is digested after it
+          if (fuse && is_coop(lb0, lb1, lk0, lk1, prec)) ++nparts_q[q];
           qi.push_back(x);
         }
-        if (nchunk > 1) any_reduce = true;
+        if (nchunk > 1 || (persistent && nb * nk > 1)) any_reduce = true;
       }
   }
   const int64_t nparts = (int64_t)qi.size();
@@ -937,6 +978,7 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   };
   std::vector<PartKey> pk(nparts);
   std::vector<EriQuartetRec> recs(nparts);
+  std::vector<int32_t> rec_q(fuse ? nparts : 0);
   {
     // dense ids: used (round, class, precision) groups and (K4, kb) signatures
     std::vector<int32_t> gdense(4 * ncls * 2, -1);
@@ -974,6 +1016,7 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       const QInfo& x = qi[q];
       const int64_t p = start[key[q]]++;
       recs[p] = x.rec;
+      if (fuse) rec_q[p] = x.uq;
       pk[p] = {x.cls, x.round, x.prec, x.kb, x.kk};
     }
   }
@@ -1007,7 +1050,6 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   size_t max_scratch_slots = 0;
   int max_grid_global = 0;
   size_t max_coop_vals = 0, max_coop_h = 0;
-  const bool default_opts = opts.axis_rule == 0 && opts.schedule == 0 && opts.sph_mode == 0;
   for (int64_t i = 0; i < nparts;) {
     const int c = pk[i].cls;
     const int round = pk[i].round;
@@ -1024,18 +1066,7 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     auto rit = regmap.find({b.ls[0], b.ls[1], b.ls[2], b.ls[3]});
     const void* regfn = (rit != regmap.end() && default_opts) ? rit->second : nullptr;
     const size_t smem_need = prog ? (size_t)prog->nslot * 128 * sizeof(double) : 0;
-    int tier = opts.tier;
-    if (prec && tier == 0) {
-      // FP32 forms: the compiled register kernel, else the cooperative program
-      tier = regfn ? TIER_REG : TIER_COOP;
-    } else if (tier == 0) {
-      // the autotuner's choice when it is feasible, else the static rule
-      const int pt = preferred_tier(b.ls);
-      const bool ok = (pt == TIER_REG && regfn) || (pt == TIER_COOP && cp) ||
-                      (pt == TIER_SHARED && prog && smem_need <= L.smem_optin) || (pt == TIER_GLOBAL && prog);
-      tier = ok ? pt
-                : regfn ? TIER_REG : cp ? TIER_COOP : (prog && smem_need <= L.smem_optin ? TIER_SHARED : TIER_GLOBAL);
-    }
+    const int tier = route_tier(b.ls, prec);
     if (tier == TIER_REG && !regfn)
       return fail(ERI_EUNSUPPORTED, "no register-tier kernel for this class/options");
     if (tier == TIER_COOP && !cp)
@@ -1086,6 +1117,16 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       if (shallow) {
         auto sit = L.coops_shallow.find(pkey);
         if (sit != L.coops_shallow.end()) cp = sit->second.get();
+      }
+      // warp votes around the optional FP64 terms: on request, else the
+      // class table's preference (autotuner), else the static rule, measured
+      // on the sweep classes with K per shell from {1, 3, 6}: votes pay for
+      // teams of 128 lanes or more ((ff|ff) 0.610 -> 0.690 of the FP64 rate,
+      // (gg|gg) 0.620 -> 0.632) and cost 64-lane teams ((dd|dd) 0.602 -> 0.582)
+      {
+        const int pv = preferred_votes(b.ls);
+        const int want_v = opts.votes ? opts.votes : pv ? pv : (cp->T >= 128 ? 2 : 1);
+        b.vote = want_v == 2 ? 1 : 0;
       }
       b.coop = cp;
       // single-primitive parts: a team computes the rows of kShallowK4
@@ -1145,6 +1186,108 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     plan->buckets.push_back(b);
     i = j;
   }
+  // ---- persistent plans: the cooperative buckets become work items of one
+  // launch per (precision, vote form); a block of 512 threads per SM takes
+  // items from a counter.  Per bucket: the team shape of its program, the
+  // teams per block that fit the launch's shared memory (H in shared memory
+  // when that keeps as many teams), and items of `teams` x r quartets, r
+  // chosen for about eight items per SM per bucket.  Items go heaviest
+  // bucket first so that the dynamic queue ends evenly.
+  if (persistent) {
+    std::vector<Bucket> groups;
+    std::vector<EriWorkItem> items;
+    std::vector<EriCoopProgDesc> progs;
+    std::map<const CoopProg*, int> prog_id;
+    const size_t smax = eri_coop_persist_smem_max(L.smem_optin);
+    size_t smem_need = 0;
+    int64_t gh_need = 0;
+    for (int prec = 0; prec < 2; ++prec) {
+      for (int vote = 0; vote < 2; ++vote) {
+        std::vector<const Bucket*> bs;
+        for (const Bucket& b : plan->buckets)
+          if (b.tier == TIER_COOP && b.fp32 == prec && b.vote == vote) bs.push_back(&b);
+        if (bs.empty()) continue;
+        std::stable_sort(bs.begin(), bs.end(), [](const Bucket* x, const Bucket* y) {
+          return x->flops / std::max<int64_t>(1, x->count) > y->flops / std::max<int64_t>(1, y->count);
+        });
+        Bucket g;
+        g.tier = TIER_PERSIST;
+        for (int k = 0; k < 4; ++k) g.ls[k] = -1;
+        g.fp32 = prec;
+        g.vote = vote;
+        g.pgroup = (int)groups.size();
+        g.item0 = (int)items.size();
+        g.block = 512;
+        g.grid = L.nsm;
+        const size_t elem = prec ? sizeof(float) : sizeof(double);
+        for (const Bucket* b : bs) {
+          const CoopProg* cp = b->coop;
+          auto pit = prog_id.find(cp);
+          if (pit == prog_id.end()) {
+            EriCoopProgDesc d;
+            d.ph1 = cp->d_ph1;
+            d.steps1 = cp->d_steps1;
+            d.ph2 = cp->d_ph2;
+            d.steps2 = cp->d_steps2;
+            d.nw1 = cp->nw1;
+            d.nw2 = cp->nw2;
+            d.nh = cp->nh;
+            d.nslot = cp->nslot;
+            d.L = cp->L;
+            d.pad = 0;
+            pit = prog_id.emplace(cp, (int)progs.size()).first;
+            progs.push_back(d);
+          }
+          const size_t rows = eri_coop_row_elems() * (size_t)b->batch;
+          int best = 0, hsm = 0;
+          for (int h_in = 1; h_in >= 0; --h_in) {
+            const size_t per_team = (rows + cp->nslot + (h_in ? (size_t)cp->nh : 0)) * elem;
+            const int t = (int)std::min<size_t>(512 / cp->T, smax / per_team);
+            if (t > best) best = t, hsm = h_in;
+          }
+          if (best < 1) return fail(ERI_EUNSUPPORTED, "class does not fit the persistent launch's shared memory");
+          const size_t per_team = rows + cp->nslot + (hsm ? (size_t)cp->nh : 0);
+          smem_need = std::max(smem_need, (per_team * best * elem + 15) / 16 * 16);
+          if (!hsm) gh_need = std::max<int64_t>(gh_need, (int64_t)best * cp->nh);
+          const int64_t r = std::max<int64_t>(1, (b->count + (int64_t)best * 8 * L.nsm - 1) /
+                                                     ((int64_t)best * 8 * L.nsm));
+          const int64_t per_item = r * best;
+          for (int64_t f = 0; f < b->count; f += per_item) {
+            EriWorkItem w;
+            w.prog = pit->second;
+            w.first = (int32_t)(b->first + f);
+            w.count = (int32_t)std::min<int64_t>(per_item, b->count - f);
+            w.T = (int16_t)cp->T;
+            w.teams = (int16_t)best;
+            w.hsm = (int8_t)hsm;
+            w.vote = (int8_t)vote;
+            w.single = (int8_t)b->single;
+            w.pad = 0;
+            w.batch = b->batch;
+            items.push_back(w);
+          }
+          g.count += b->count;
+          g.flops += b->flops;
+        }
+        g.nitems = (int)items.size() - g.item0;
+        groups.push_back(g);
+      }
+    }
+    if (items.size() > (size_t)INT32_MAX) return fail(ERI_EUNSUPPORTED, "too many work items");
+    for (Bucket& g : groups) g.smem = smem_need;
+    // the register-tier buckets first, then the persistent launches
+    std::vector<Bucket> all;
+    for (const Bucket& b : plan->buckets)
+      if (b.tier != TIER_COOP) all.push_back(b);
+    all.insert(all.end(), groups.begin(), groups.end());
+    plan->buckets = all;
+    plan->persistent = true;
+    plan->persist_h_per_block = gh_need;
+    if ((rc = plan->items.upload(items, "work items")) || (rc = plan->progs.upload(progs, "program table")) ||
+        (rc = plan->counters.alloc(std::max<size_t>(1, groups.size()), "item counters")) ||
+        (rc = plan->persist_h.alloc((size_t)gh_need * L.nsm, "persistent accumulators")))
+      return rc;
+  }
   // ---- concurrency: the launches of one part round write distinct blocks,
   // so they may overlap on several streams (fork/join per round); launches
   // on the plan's global scratch stay on the caller's stream.  Greedy
@@ -1153,7 +1296,8 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   {
     std::set<std::vector<int>> classes;
     for (const Bucket& b : plan->buckets) classes.insert({b.ls[0], b.ls[1], b.ls[2], b.ls[3]});
-    const int want = opts.streams > 0 ? opts.streams : (classes.size() > 1 ? 4 : 1);
+    // a persistent plan's launches each fill the GPU: one stream
+    const int want = persistent ? 1 : opts.streams > 0 ? opts.streams : (classes.size() > 1 ? 4 : 1);
     int used = 1;
     for (size_t i = 0; i < plan->buckets.size();) {
       size_t j = i;
@@ -1249,15 +1393,24 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       if ((rc = plan->d_nab.upload(nab, "pair sizes"))) return rc;
     }
   }
+  if (fuse) {
+    if ((rc = plan->rec_q.upload(rec_q, "record quartets")) || (rc = plan->nparts_q.upload(nparts_q, "part counts")) ||
+        (rc = plan->done_q.alloc((size_t)nq, "part counters")))
+      return rc;
+  }
   if (opts.digest) {
     std::vector<int32_t> uq(quartets, quartets + 4 * nq);
     std::vector<int32_t> bf(nshell + 1, 0);
     for (int s = 0; s < nshell; ++s) bf[s + 1] = bf[s] + nfun(shells[s].l, cart);
-    std::vector<int64_t> small, large;
-    for (int64_t q = 0; q < nq; ++q)
-      (plan->offsets[q + 1] - plan->offsets[q] <= kSmallBlock ? small : large).push_back(q);
+    std::vector<int64_t> small, large, rsmall, rlarge;
+    for (int64_t q = 0; q < nq; ++q) {
+      const bool sm = plan->offsets[q + 1] - plan->offsets[q] <= kSmallBlock;
+      (sm ? small : large).push_back(q);
+      if (fuse && nparts_q[q] == 0) (sm ? rsmall : rlarge).push_back(q);
+    }
     if ((rc = plan->d_uq.upload(uq, "quartet list")) || (rc = plan->d_shell_bf.upload(bf, "shell offsets")) ||
-        (rc = plan->d_small.upload(small, "digest list")) || (rc = plan->d_large.upload(large, "digest list")))
+        (rc = plan->d_small.upload(small, "digest list")) || (rc = plan->d_large.upload(large, "digest list")) ||
+        (rc = plan->d_rsmall.upload(rsmall, "digest list")) || (rc = plan->d_rlarge.upload(rlarge, "digest list")))
       return rc;
     plan->nbf = bf[nshell];
     plan->digest = true;
@@ -1417,7 +1570,21 @@ extern "C" int eri_output_offsets(const eri_plan_t* plan, int64_t* offsets) {
   return ERI_OK;
 }
 
+// Digestion fused into a persistent plan's launch (eri_compute_jk).
+struct FuseIn {
+  const double* D;
+  double* J;
+  double* K;
+  int32_t nbf;
+};
+
+static int compute_impl(eri_plan_t* plan, double* out, void* stream_, const FuseIn* fz);
+
 extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
+  return compute_impl(plan, out, stream_, nullptr);
+}
+
+static int compute_impl(eri_plan_t* plan, double* out, void* stream_, const FuseIn* fz) {
   if (!plan) return fail(ERI_EINVAL, "NULL plan");
   if (plan->nq == 0) return ERI_OK;
   if (!out) return fail(ERI_EINVAL, "NULL output");
@@ -1451,6 +1618,8 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
   int cur_round = -1;
   if (plan->zero_out)
     CUDA_OR(cudaMemsetAsync(out, 0, (size_t)plan->offsets.back() * sizeof(double), stream), "zero output");
+  if (fz)
+    CUDA_OR(cudaMemsetAsync(plan->done_q.p, 0, plan->done_q.n * sizeof(int32_t), stream), "zero part counters");
   {
     CUDA_OR(mark(0), "cudaEventRecord");
     // molecule plans have their primitive pairs already (npair = 0)
@@ -1494,6 +1663,35 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
     if (b.tier == TIER_REG) {
       void* args[] = {&a};
       CUDA_OR(cudaLaunchKernel(b.reg_fn, dim3(b.grid), dim3(b.block), args, 0, cur), "class kernel launch");
+    } else if (b.tier == TIER_PERSIST) {
+      EriPersistArgs pa;
+      pa.items = plan->items.p + b.item0;
+      pa.progs = plan->progs.p;
+      pa.next = plan->counters.p + b.pgroup;
+      pa.nitems = b.nitems;
+      pa.pad = 0;
+      pa.gH = plan->persist_h.p;
+      pa.gh_per_block = plan->persist_h_per_block;
+      pa.c2s = L.d_c2s;
+      memset(&pa.fuse, 0, sizeof pa.fuse);
+      if (fz) {
+        pa.fuse.on = 1;
+        pa.fuse.jk.quartets = plan->d_uq.p;
+        pa.fuse.jk.offsets = plan->d_offsets.p;
+        pa.fuse.jk.shell_bf = plan->d_shell_bf.p;
+        pa.fuse.jk.blocks = out;
+        pa.fuse.jk.D = fz->D;
+        pa.fuse.jk.J = fz->J;
+        pa.fuse.jk.K = fz->K;
+        pa.fuse.jk.nq = plan->nq;
+        pa.fuse.jk.nbf = fz->nbf;
+        pa.fuse.rec_q = plan->rec_q.p;
+        pa.fuse.nparts = plan->nparts_q.p;
+        pa.fuse.done = plan->done_q.p;
+      }
+      a.quartets = plan->quartets.p;  // items index the whole record array
+      CUDA_OR(cudaMemsetAsync(pa.next, 0, sizeof(int32_t), cur), "zero item counter");
+      CUDA_OR(eri_coop_persist_launch(b.fp32, b.vote, &a, &pa, b.grid, b.smem, cur), "persistent launch");
     } else if (b.tier == TIER_COOP) {
       const CoopProg* cp = b.coop;
       EriCoopArgs p;
@@ -1514,7 +1712,7 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
       p.nteams = b.nteams;
       p.batch = b.batch;
       p.single = b.single;
-      CUDA_OR(eri_coop_launch(cp->T, cp->ilp, b.fp32, &a, &p, b.grid, b.block, b.smem, cur),
+      CUDA_OR(eri_coop_launch(cp->T, cp->ilp, b.fp32, b.vote, &a, &p, b.grid, b.block, b.smem, cur),
               "cooperative launch");
     } else {
       EriProgArgs p;
@@ -1533,14 +1731,10 @@ extern "C" int eri_compute(eri_plan_t* plan, double* out, void* stream_) {
   return join_round();
 }
 
-extern "C" int eri_digest_jk(eri_plan_t* plan, const double* blocks, const double* density, int32_t nbf, double* J,
-                             double* K, void* stream) {
-  if (!plan) return fail(ERI_EINVAL, "NULL plan");
-  if (plan->nq == 0) return ERI_OK;
-  if (!plan->digest) return fail(ERI_ESTATE, "plan built without opts.digest = 1");
-  if (!blocks || !density) return fail(ERI_EINVAL, "NULL blocks or density");
-  if (nbf != plan->nbf) return fail(ERI_EINVAL, "nbf does not match the plan's basis functions");
-  if (!J && !K) return ERI_OK;
+// The separate digestion kernels over the plan's quartet lists: every quartet
+// (rest = false), or the quartets a persistent launch does not digest.
+static int digest_lists(eri_plan_t* plan, const double* blocks, const double* density, int32_t nbf, double* J,
+                        double* K, void* stream, bool rest) {
   EriDigestArgs g;
   g.quartets = plan->d_uq.p;
   g.offsets = plan->d_offsets.p;
@@ -1551,13 +1745,30 @@ extern "C" int eri_digest_jk(eri_plan_t* plan, const double* blocks, const doubl
   g.K = K;
   g.nq = plan->nq;
   g.nbf = nbf;
-  g.list = plan->d_small.p;
-  g.nlist = (int64_t)plan->d_small.n;
-  CUDA_OR(eri_digest_launch(&g, 1, (cudaStream_t)stream), "digest launch");
-  g.list = plan->d_large.p;
-  g.nlist = (int64_t)plan->d_large.n;
-  CUDA_OR(eri_digest_launch(&g, 0, (cudaStream_t)stream), "digest launch");
+  const DevBuf<int64_t>& sm = rest ? plan->d_rsmall : plan->d_small;
+  const DevBuf<int64_t>& lg = rest ? plan->d_rlarge : plan->d_large;
+  if (sm.n > 0) {
+    g.list = sm.p;
+    g.nlist = (int64_t)sm.n;
+    CUDA_OR(eri_digest_launch(&g, 1, (cudaStream_t)stream), "digest launch");
+  }
+  if (lg.n > 0) {
+    g.list = lg.p;
+    g.nlist = (int64_t)lg.n;
+    CUDA_OR(eri_digest_launch(&g, 0, (cudaStream_t)stream), "digest launch");
+  }
   return ERI_OK;
+}
+
+extern "C" int eri_digest_jk(eri_plan_t* plan, const double* blocks, const double* density, int32_t nbf, double* J,
+                             double* K, void* stream) {
+  if (!plan) return fail(ERI_EINVAL, "NULL plan");
+  if (plan->nq == 0) return ERI_OK;
+  if (!plan->digest) return fail(ERI_ESTATE, "plan built without opts.digest = 1");
+  if (!blocks || !density) return fail(ERI_EINVAL, "NULL blocks or density");
+  if (nbf != plan->nbf) return fail(ERI_EINVAL, "nbf does not match the plan's basis functions");
+  if (!J && !K) return ERI_OK;
+  return digest_lists(plan, blocks, density, nbf, J, K, stream, false);
 }
 
 extern "C" int eri_compute_jk(eri_plan_t* plan, const double* density, int32_t nbf, double* J, double* K,
@@ -1569,6 +1780,16 @@ extern "C" int eri_compute_jk(eri_plan_t* plan, const double* density, int32_t n
   if (plan->outbuf.n < n) {
     plan->outbuf.reset();
     if (int rc = plan->outbuf.alloc(n, "output buffer")) return rc;
+  }
+  if (plan->persistent) {
+    // the digestion runs in the evaluation launch itself
+    if (!density) return fail(ERI_EINVAL, "NULL density");
+    if (nbf != plan->nbf) return fail(ERI_EINVAL, "nbf does not match the plan's basis functions");
+    if (!J && !K) return eri_compute(plan, plan->outbuf.p, stream);
+    const FuseIn fz = {density, J, K, nbf};
+    if (int rc = compute_impl(plan, plan->outbuf.p, stream, &fz)) return rc;
+    // quartets whose parts all ran on the register tier
+    return digest_lists(plan, plan->outbuf.p, density, nbf, J, K, stream, true);
   }
   if (int rc = eri_compute(plan, plan->outbuf.p, stream)) return rc;
   return eri_digest_jk(plan, plan->outbuf.p, density, nbf, J, K, stream);
@@ -1714,6 +1935,10 @@ extern "C" int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* st
   if (rc) return rc;
   cudaStream_t stream = (cudaStream_t)stream_;
   Library& L = lib();
+  // parts that add into their block need it zeroed first (a memset
+  // allocates nothing)
+  if (plan->zero_out)
+    CUDA_OR(cudaMemsetAsync(out, 0, (size_t)plan->offsets.back() * sizeof(double), stream), "zero output");
   {
     // molecule plans have their primitive pairs already (npair = 0)
     const int threads = 128;
@@ -1750,6 +1975,44 @@ extern "C" int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* st
     p.L = b.prog->L;
     CUDA_OR(eri_exec_launch(0, &a, &p, grid, 128, 0, stream), "executor launch (fixed scratch)");
   }
+  return ERI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostic: the device Boys function on its own
+// ---------------------------------------------------------------------------
+// The compiled register-tier kernels inline eri_boys<L> with a compile-time
+// order; one instantiation per order.
+template <int L>
+__global__ void eri_boys_reg_kernel(const double* __restrict__ T, int64_t n, const double* __restrict__ tab,
+                                    double* __restrict__ F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double f[L + 1];
+  eri_boys<L>(T[i], f, tab);
+#pragma unroll
+  for (int m = 0; m <= L; ++m) F[i * (L + 1) + m] = f[m];
+}
+
+template <int L>
+static cudaError_t boys_reg_launch(const double* T, int64_t n, int l, const double* tab, double* F, cudaStream_t st) {
+  if (l != L) return boys_reg_launch<(L < ERI_BOYS_LMAX ? L + 1 : L)>(T, n, l, tab, F, st);
+  eri_boys_reg_kernel<L><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(T, n, tab, F);
+  return cudaGetLastError();
+}
+
+extern "C" int eri_boys_eval(const double* T, int64_t n, int32_t L, int32_t form, double* F, void* stream_) {
+  if (n < 0 || L < 0 || L > ERI_BOYS_LMAX || form < 0 || form > 2) return fail(ERI_EINVAL, "bad n, L or form");
+  if (n == 0) return ERI_OK;
+  if (!T || !F) return fail(ERI_EINVAL, "NULL argument");
+  int rc = ensure_library();
+  if (rc) return rc;
+  const double* tab = lib().d_boys;
+  cudaStream_t st = (cudaStream_t)stream_;
+  cudaError_t e = form == 0   ? boys_reg_launch<0>(T, n, L, tab, F, st)
+                  : form == 1 ? eri_coop_boys_launch(T, n, L, tab, F, st)
+                              : eri_exec_boys_launch(T, n, L, tab, F, st);
+  CUDA_OR(e, "Boys launch");
   return ERI_OK;
 }
 
@@ -1804,6 +2067,28 @@ int preferred_tier(const int ls[4]) {
   std::lock_guard<std::mutex> g(g_tier_mu);
   auto it = g_tier_table.find({ls[0], ls[1], ls[2], ls[3]});
   return it == g_tier_table.end() ? 0 : it->second;
+}
+
+namespace {
+std::map<std::vector<int>, int> g_vote_table;  // class -> preferred vote form (autotuner)
+}  // namespace
+
+extern "C" int eri_set_class_votes(int la, int lb, int lc, int ld, int votes) {
+  if (la < 0 || lb < 0 || lc < 0 || ld < 0 || la > ERI_MAX_L || lb > ERI_MAX_L || lc > ERI_MAX_L ||
+      ld > ERI_MAX_L || votes < 0 || votes > 2)
+    return fail(ERI_EINVAL, "bad class or vote form");
+  std::lock_guard<std::mutex> g(g_tier_mu);
+  if (votes == 0)
+    g_vote_table.erase({la, lb, lc, ld});
+  else
+    g_vote_table[{la, lb, lc, ld}] = votes;
+  return ERI_OK;
+}
+
+int preferred_votes(const int ls[4]) {
+  std::lock_guard<std::mutex> g(g_tier_mu);
+  auto it = g_vote_table.find({ls[0], ls[1], ls[2], ls[3]});
+  return it == g_vote_table.end() ? 0 : it->second;
 }
 
 extern "C" int eri_plan_graph_capture(eri_plan_t* plan, double* out, void* stream_) {

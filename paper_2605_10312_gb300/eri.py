@@ -19,8 +19,9 @@ AXIS_RULES = {"prose": 0, "literal": 1, "common": 2}
 SCHEDULES = {"dsa": 0, "level": 1}
 SPH_MODES = {"stepwise": 0, "materialize": 1, "cart": 2}
 TIERS = {"auto": 0, "reg": 1, "shared": 2, "global": 3, "coop": 4}
-TIERS_INV = {0: "setup", 1: "reg", 2: "shared", 3: "global", 4: "coop"}
+TIERS_INV = {0: "setup", 1: "reg", 2: "shared", 3: "global", 4: "coop", 5: "persistent"}
 ORIENTATIONS = {"split": 0, "l": 1, "tight": 2}
+VOTES = {"auto": 0, "off": 1, "on": 2}
 
 
 class EriError(RuntimeError):
@@ -42,7 +43,7 @@ class _Basis(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("axis_rule", ctypes.c_int32), ("schedule", ctypes.c_int32), ("sph_mode", ctypes.c_int32),
                 ("tier", ctypes.c_int32), ("orientation", ctypes.c_int32), ("streams", ctypes.c_int32),
-                ("digest", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("digest", ctypes.c_int32), ("votes", ctypes.c_int32), ("persistent", ctypes.c_int32)]
 
 
 _lib = None
@@ -106,10 +107,15 @@ def library(path: str = LIB):
         lib.eri_schwarz.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.eri_set_class_tier.restype = ctypes.c_int
         lib.eri_set_class_tier.argtypes = [ctypes.c_int] * 5
+        lib.eri_set_class_votes.restype = ctypes.c_int
+        lib.eri_set_class_votes.argtypes = [ctypes.c_int] * 5
         lib.eri_plan_graph_capture.restype = ctypes.c_int
         lib.eri_plan_graph_capture.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.eri_plan_graph_launch.restype = ctypes.c_int
         lib.eri_plan_graph_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_boys_eval.restype = ctypes.c_int
+        lib.eri_boys_eval.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_void_p]
         lib.eri_plan_destroy.restype = ctypes.c_int
         lib.eri_plan_destroy.argtypes = [ctypes.c_void_p]
         lib.eri_last_error.restype = ctypes.c_char_p
@@ -175,7 +181,7 @@ class Plan:
 
     def __init__(self, basis, quartets, axis_rule="prose", schedule="dsa", sph_mode="stepwise", tier="auto",
                  orientation="split", qbound=None, fp32_below=None, streams=0, stream=None, digest=False,
-                 mol=None):
+                 mol=None, votes="auto", persistent=False):
         """qbound/fp32_below: mixed precision (eri_plan_mixed) -- quartets whose
         bound is below fp32_below run their recurrences in FP32.  stream: a
         stream-ordered plan (eri_plan_on_stream) whose device memory lives and
@@ -189,7 +195,8 @@ class Plan:
             sh, ns, b, keep = _marshal_basis(basis)
             self._keep = keep + [q]
         o = _Opts(AXIS_RULES[axis_rule], SCHEDULES[schedule], SPH_MODES[sph_mode], TIERS[tier],
-                  ORIENTATIONS[orientation], int(streams), 1 if digest else 0)
+                  ORIENTATIONS[orientation], int(streams), 1 if digest else 0, VOTES[votes],
+                  1 if persistent else 0)
         h = ctypes.c_void_p()
         qb = None
         if qbound is not None:
@@ -340,6 +347,29 @@ def set_class_tier(ls, tier):
     autotuner); tier name or 0 to clear."""
     t = TIERS[tier] if isinstance(tier, str) else int(tier)
     _check(library().eri_set_class_tier(*[int(x) for x in ls], t))
+
+
+BOYS_FORMS = {"reg": 0, "coop": 1, "exec": 2}
+
+
+def boys(T, L, form="coop", stream=None):
+    """Device Boys values F_0..F_L at the arguments of the CUDA float64 tensor
+    ``T`` (eri_boys_eval), as a tensor of shape (n, L + 1)."""
+    import torch
+    if not (isinstance(T, torch.Tensor) and T.is_cuda and T.dtype == torch.float64 and T.is_contiguous()):
+        raise TypeError("T must be a contiguous CUDA float64 tensor")
+    F = torch.empty((T.numel(), int(L) + 1), dtype=torch.float64, device=T.device)
+    _check(library().eri_boys_eval(T.data_ptr(), T.numel(), int(L), BOYS_FORMS[form], F.data_ptr(),
+                                   _stream_handle(stream)))
+    return F
+
+
+def set_class_votes(ls, votes):
+    """Process-wide preferred cooperative form for class ls (autotuner):
+    "off" (optional FP64 terms predicated per lane), "on" (skipped by warp
+    vote), or "auto" / 0 to clear."""
+    v = VOTES[votes] if isinstance(votes, str) else int(votes)
+    _check(library().eri_set_class_votes(*[int(x) for x in ls], v))
 
 
 def eri(basis, quartets, device="cuda", **opts):

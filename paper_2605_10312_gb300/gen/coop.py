@@ -52,45 +52,59 @@ def _consumer_lists(parents, n):
     return cons, npar
 
 
-def _waves(cons, npar, priority, width):
+def _waves(cons, npar, priority, width, lag=1):
     """Bounded-width list scheduling over consumer lists (npar is consumed):
     each wave takes up to ``width`` ready nodes, smallest (priority, node)
-    first, in that order."""
+    first, in that order.  A node whose last parent is placed in wave w
+    becomes ready in wave w + lag: lag 1 for waves separated by a full team
+    barrier, lag 2 for split barriers (a lane may start wave w + 1 while
+    others still run wave w, so wave w + 1 reads nothing wave w writes)."""
     ready = [(priority[v], v) for v in range(len(npar)) if npar[v] == 0]
     heapq.heapify(ready)
     pop, push = heapq.heappop, heapq.heappush
+    pending = [[] for _ in range(lag)]   # pending[j]: ready j + 1 waves from now
     waves = []
-    while ready:
+    placed, n = 0, len(npar)
+    while placed < n:
+        for v in pending.pop(0):
+            push(ready, (priority[v], v))
+        pending.append([])
+        if not ready:
+            assert any(pending), "cycle in graph"
+            waves.append([])
+            continue
         cur = [pop(ready)[1] for _ in range(min(width, len(ready)))]
         for v in cur:
             for c in cons[v]:
                 npar[c] -= 1
                 if npar[c] == 0:
-                    push(ready, (priority[c], c))
+                    pending[lag - 1].append(c)
         waves.append(cur)
-    assert sum(len(w) for w in waves) == len(npar), "cycle in graph"
+        placed += len(cur)
     return waves
 
 
-def wave_schedule(parents, priority, width):
+def wave_schedule(parents, priority, width, lag=1):
     """Bounded-width list scheduling: each wave takes up to ``width`` ready
-    nodes with the smallest priority.  parents[v] = list of node ids."""
+    nodes with the smallest priority; a node's parents lie at least ``lag``
+    waves before it.  parents[v] = list of node ids."""
     n = len(parents)
     cons, npar = _consumer_lists(parents, n)
-    return _waves(cons, npar, [int(x) for x in priority], width)
+    return _waves(cons, npar, [int(x) for x in priority], width, lag)
 
 
-def _allocate(wave_of, last, needs_slot, order, first_slot=0):
+def _allocate(wave_of, last, needs_slot, order, first_slot=0, lag=1):
     """Slot allocation over waves for nodes taken in ``order`` (wave by wave):
     a value written in wave b and last read in wave d keeps its slot through
-    wave d; a slot is reused only by a value born in a later wave.  Lowest
-    free slot first."""
+    wave d + lag - 1; a slot is reused only by a value born in wave d + lag
+    or later (lag 2: a lane may still be reading it in wave d while another
+    writes wave d + 1).  Lowest free slot first."""
     n = len(wave_of)
     slot = np.full(n, -1, dtype=np.int64)
     free = []
     nxt = first_slot
     nw = int(wave_of.max()) + 1 if n else 0
-    release_at = [[] for _ in range(max(nw, int(last.max()) + 1 if n else 0) + 2)]
+    release_at = [[] for _ in range(max(nw, int(last.max()) + 1 if n else 0) + 1 + lag)]
     pop, push = heapq.heappop, heapq.heappush
     cur_w = -1
     wl = wave_of.tolist()
@@ -111,7 +125,7 @@ def _allocate(wave_of, last, needs_slot, order, first_slot=0):
             s = nxt
             nxt += 1
         out[v] = s
-        release_at[ll[v] + 1].append(s)
+        release_at[ll[v] + lag].append(s)
     slot[:] = out
     return slot, nxt - first_slot
 
@@ -133,13 +147,14 @@ def _lifetimes(parents, waves, pinned_until_end=()):
     return wave_of, last
 
 
-def allocate_over_waves(parents, waves, needs_slot, first_slot=0, pinned_until_end=()):
+def allocate_over_waves(parents, waves, needs_slot, first_slot=0, pinned_until_end=(), lag=1):
     """Slots for wave-synchronous execution: a value written in wave b and
-    last read in wave d keeps its slot through wave d; a slot is reused only
-    by a value born in a later wave.  Lowest free slot first."""
+    last read in wave d keeps its slot through wave d + lag - 1; a slot is
+    reused only by a value born in wave d + lag or later.  Lowest free slot
+    first."""
     wave_of, last = _lifetimes(parents, waves, pinned_until_end)
     order = [v for vs in waves for v in vs]
-    return _allocate(wave_of, last, np.asarray(needs_slot, dtype=bool), order, first_slot)
+    return _allocate(wave_of, last, np.asarray(needs_slot, dtype=bool), order, first_slot, lag)
 
 
 ILP = 2  # default nodes per lane per step (independent chains per lane)
@@ -159,6 +174,8 @@ class CoopProgram:
     out_dims: tuple
     eff1: float            # busy lanes / lane slots, Phase 1
     eff2: float
+    lag: int = 1           # 1: a full team barrier after every wave; 2: split
+                           # barriers (wave w waits for wave w - 2 only)
 
 
 PREFETCH_STEPS = 2  # no-op steps after the last wave: the executor loads ahead
@@ -336,19 +353,19 @@ def release(prog):
         prog.__dict__.pop(name, None)
 
 
-def _width_form(prog, width):
+def _width_form(prog, width, lag=1):
     """Waves, slots and descriptor rows of both phases for waves of up to
-    ``width`` nodes (cached per program and width: shapes of equal width
-    share them)."""
+    ``width`` nodes and parents at least ``lag`` waves back (cached per
+    program, width and lag: shapes of equal width share them)."""
     st = _static(prog)
-    cached = prog._coop_width.get(width)
+    cached = prog._coop_width.get((width, lag))
     if cached is not None:
         return cached
     nh = st.nh
     # ---------------- Phase 1
-    waves1 = _waves(st.cons1, list(st.npar1), st.prio1, width)
+    waves1 = _waves(st.cons1, list(st.npar1), st.prio1, width, lag)
     wave_of, last = _lifetimes(st.par1, waves1)
-    slot1, nslot1 = _allocate(wave_of, last, st.consumed, [v for w in waves1 for v in w])
+    slot1, nslot1 = _allocate(wave_of, last, st.consumed, [v for w in waves1 for v in w], lag=lag)
     src = st.src1
     sl = np.where(src >= 0, slot1[np.maximum(src, 0)], 0)
     rows1 = np.empty((st.n1, 4), dtype=np.int64)
@@ -357,9 +374,9 @@ def _width_form(prog, width):
     rows1[:, 2] = sl[:, 2] | (sl[:, 3] << 16)
     rows1[:, 3] = sl[:, 4] | (st.meta1 << 16)
     # ---------------- Phase 2
-    waves2 = _waves(st.cons2, list(st.npar2), st.prio2, width)
+    waves2 = _waves(st.cons2, list(st.npar2), st.prio2, width, lag)
     wave_of2, last2 = _lifetimes(st.par2, waves2)
-    slot2, nslot2 = _allocate(wave_of2, last2, st.needs2, [v for w in waves2 for v in w])
+    slot2, nslot2 = _allocate(wave_of2, last2, st.needs2, [v for w in waves2 for v in w], lag=lag)
     # operand id of a node: H index, or nh + its value slot
     oid = np.concatenate([np.arange(nh, dtype=np.int64), nh + slot2])
 
@@ -374,16 +391,19 @@ def _width_form(prog, width):
     rows2[:, 2] = c[:, 2] | o[:, 2] | (o[:, 3] << 16)
     rows2[:, 3] = c[:, 3]
     form = (waves1, rows1, int(nslot1), waves2, rows2, int(nslot2))
-    prog._coop_width[width] = form
+    prog._coop_width[(width, lag)] = form
     return form
 
 
-def build(prog, T=128, ilp=ILP, wave_steps=1):
+def build(prog, T=128, ilp=ILP, wave_steps=1, lag=1):
     """CoopProgram of a class program for teams of T lanes taking ilp nodes
     per step; a wave (the nodes between two team barriers) holds up to
-    wave_steps steps of mutually independent nodes."""
+    wave_steps steps of mutually independent nodes.  lag 2: split barriers
+    (teams of 64 lanes or more), parents at least two waves back."""
+    if lag == 2 and T < 64:
+        raise ValueError("split barriers need teams of 64 lanes or more")
     st = _static(prog)
-    waves1, rows1, nslot1, waves2, rows2, nslot2 = _width_form(prog, ilp * T * wave_steps)
+    waves1, rows1, nslot1, waves2, rows2, nslot2 = _width_form(prog, ilp * T * wave_steps, lag)
     ph1, steps1 = _pack(waves1, rows1, T, NOP1, ilp, st.shape1)
     ph2, steps2 = _pack(waves2, rows2, T, NOP2, ilp, st.shape2)
     nh = st.nh
@@ -393,7 +413,8 @@ def build(prog, T=128, ilp=ILP, wave_steps=1):
     eff1 = st.n1 / max(1, int(steps1.sum()) * T * ilp)
     eff2 = st.n2w / max(1, int(steps2.sum()) * T * ilp)
     assert ph1.shape[0] == (int(steps1.sum()) + PREFETCH_STEPS) * T * ilp
-    return CoopProgram(T, ilp, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(prog.p2.out_dims), eff1, eff2)
+    return CoopProgram(T, ilp, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(prog.p2.out_dims), eff1, eff2,
+                       lag)
 
 
 def fp64_issue(cp):
@@ -462,6 +483,12 @@ def _score(cp, rows):
     return warps * eff * min(1.0, chains / 4.0)
 
 
+# Split-barrier forms (waves scheduled with parents two waves back, so a lane
+# may start a wave while others finish the previous one) were measured on
+# GB300 against full barriers and lost 2-5% on (dd|dd), (ff|ff) and (gg|gg):
+# their extra steps cost more than the barrier drains they save.  The build
+# takes full-barrier forms; the schedule stays available (split=True).
+SPLIT_BARRIERS = False
 WIDE_SHAPES = ((256, 2), (256, 4))
 # sixteen warps on one live set: 512 lanes, two nodes per lane (the register
 # file holds 128 registers for each of 512 threads)
@@ -497,7 +524,28 @@ def _wide_waves(prog, cp, rows):
     return cp
 
 
-def choose_both(prog, shapes=SHAPES):
+# split barriers cost no drain at a wave's end but put a node's parents at
+# least two waves back, which can stretch a narrow graph: they are taken when
+# the steps they need stay within this factor of the full-barrier form's
+SPLIT_STEP_RATIO = 1.15
+
+
+def _split_barriers(prog, cp, rows):
+    """The same team shape with split barriers (one step per wave, parents at
+    least two waves back, slots released a wave later), when it keeps the
+    teams per SM and its steps stay within SPLIT_STEP_RATIO of the
+    full-barrier form's, else None.  Teams of one warp keep full barriers
+    (a warp-synchronous point costs no drain)."""
+    if cp is None or cp.T < 64:
+        return None
+    ck = build(prog, cp.T, cp.ilp, 1, lag=2)
+    if _score(ck, rows) is None or _teams_per_sm(ck, rows) < _teams_per_sm(cp, rows):
+        return None
+    steps = lambda c: int(c.steps1.sum()) + int(c.steps2.sum()) / 8.0
+    return ck if steps(ck) <= SPLIT_STEP_RATIO * steps(cp) else None
+
+
+def choose_both(prog, shapes=SHAPES, split=None):
     """(deep, shallow): the best (team size, nodes per lane) shape when a
     team holds DEEP_ROWS coefficient rows, and when it holds SHALLOW_ROWS
     (shallow contractions: fewer rows leave shared memory for more teams).
@@ -520,7 +568,10 @@ def choose_both(prog, shapes=SHAPES):
     out = []
     for rows in (DEEP_ROWS, SHALLOW_ROWS):
         scored = [(sc, k) for k, cp in enumerate(built) for sc in [_score(cp, rows)] if sc is not None]
-        out.append(_wide_waves(prog, built[max(scored)[1]], rows) if scored else None)
+        cp = _wide_waves(prog, built[max(scored)[1]], rows) if scored else None
+        if SPLIT_BARRIERS if split is None else split:
+            cp = _split_barriers(prog, cp, rows) or cp
+        out.append(cp)
     release(prog)
     return tuple(out)
 

@@ -131,6 +131,7 @@ def emit_class(prog, tier="reg", threads=128, real="double"):
     w("  const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];")
     w("  const EriPairRec ket = a.pairs[qr.ket];")
     w("  const bool acc = ERI_ACCUMULATE(qr.bra);")
+    w("  const bool red = ERI_REDUCE(qr.bra);")
     if tier == "smem":
         w("  double* const S = eri_smem + threadIdx.x;")
         w("#define SV(i) S[(i) * {}]".format(threads))
@@ -281,7 +282,7 @@ def emit_class(prog, tier="reg", threads=128, real="double"):
             if ii:
                 terms.append("{}*qr.st[{}]".format(int(ii), axis))
         off = " + ".join(terms) if terms else "0"
-        w("  eri_st(o + {}, {}{}, acc);".format(off, "(double)" if real == "float" else "", pv(vid)))
+        w("  eri_st(o + {}, {}{}, acc, red);".format(off, "(double)" if real == "float" else "", pv(vid)))
     if tier in ("smem", "global"):
         w("#undef SV")
     if tier == "global":

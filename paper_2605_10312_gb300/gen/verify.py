@@ -17,7 +17,14 @@ kernel addresses with it:
       indexes < the transform table, stores of element k < prod(dims) at
       component indexes that ravel to k;
     layout: descriptor count = (steps + PREFETCH_STEPS) x T x ilp, every
-      wave at least one step, the trailing prefetch steps no-ops;
+      wave at least one step (a split-barrier program may have empty waves:
+      pure synchronisation points), the trailing prefetch steps no-ops;
+    hazards: within a wave no slot is both read and written, or written
+      twice; with split barriers (lag 2, a lane may run wave w + 1 while
+      others still run wave w) neither does any slot between two adjacent
+      waves -- nothing wave w + 1 reads or writes is written or read in
+      wave w -- so any interleaving of two adjacent waves gives the
+      wave-by-wave result; each accumulator has one Phase-1 owner;
   encoded programs (thread-per-quartet executor): the same rules on its
     descriptor form, with one slot space of nslot ids (accumulators first).
 
@@ -93,7 +100,7 @@ def verify_coop(cp, L, ncoef):
             out.append("{}: {} descriptors for {} steps of {} lanes x {}".format(
                 name, ph.shape[0], int(np.sum(steps)), cp.T, cp.ilp))
             return out
-        if np.any(np.asarray(steps) < 1):
+        if np.any(np.asarray(steps) < (1 if getattr(cp, "lag", 1) == 1 else 0)):
             out.append("{}: empty wave".format(name))
         nop = NOP1 if name == "phase 1" else NOP2
         if np.any(ph[ph.shape[0] - PREFETCH_STEPS * W:] != nop[None, :]):
@@ -122,9 +129,63 @@ def verify_coop(cp, L, ncoef):
     _bad(term & (k3 > 0) & (s4 >= nslot), "phase 1: cross-term operand out of range", out)
     # largest coefficient-row entry a node reads: 28 + 8 side + k <= 44, 44 + k3 <= 52
     assert 28 + 8 + MAX_K < ROW_ENTRIES and 44 + MAX_K < ROW_ENTRIES
+    hs = h[live & (h > 0)]
+    _bad(np.bincount(hs, minlength=1)[hs] > 1, "phase 1: accumulator with more than one owner", out)
     # ---- Phase 2
     _phase2(cp.ph2, nh + nslot, ncoef, cp.out_dims, out, nop=NOP2)
+    # ---- hazards between and within waves
+    lag = getattr(cp, "lag", 1)
+    for name, reads, writes in (("phase 1",) + _phase1_access(cp), ("phase 2",) + _phase2_access(cp)):
+        prev_r = prev_w = None
+        for wv, (r, wr) in enumerate(zip(reads, writes)):
+            if np.intersect1d(r, wr).size or np.unique(wr).size != wr.size:
+                out.append("{}: wave {} reads a slot it writes, or writes one twice".format(name, wv))
+            if lag == 2 and prev_r is not None and (np.intersect1d(r, prev_w).size or
+                                                    np.intersect1d(wr, prev_r).size or
+                                                    np.intersect1d(wr, prev_w).size):
+                out.append("{}: waves {} and {} share a slot under split barriers".format(name, wv - 1, wv))
+            prev_r, prev_w = r, wr
     return out
+
+
+def _waves_of(ph, steps, W):
+    i = 0
+    for st in np.asarray(steps).tolist():
+        yield ph[i:i + int(st) * W].astype(np.int64)
+        i += int(st) * W
+
+
+def _phase1_access(cp):
+    """Per wave: value slots read (operands of the terms each node
+    evaluates) and written (kept results)."""
+    reads, writes = [], []
+    for w in _waves_of(cp.ph1, cp.steps1, cp.T * cp.ilp):
+        meta = w[:, 3] >> 16
+        term = (meta & 0xC000) == 0
+        k, k3 = (meta >> 4) & 31, (meta >> 9) & 15
+        r = [w[term, 1] & 0xFFFF, w[term, 1] >> 16, w[term & (k > 0), 2] & 0xFFFF, w[term & (k > 0), 2] >> 16,
+             w[term & (k3 > 0), 3] & 0xFFFF]
+        dst = w[:, 0] & 0xFFFF
+        reads.append(np.unique(np.concatenate(r)))
+        writes.append(dst[((meta & 0x8000) == 0) & (dst != 0xFFFF)])
+    return reads, writes
+
+
+def _phase2_access(cp):
+    """Per wave: operand ids read (accumulators and value slots) and value
+    ids written (results of HRR steps and linear combinations)."""
+    reads, writes = [], []
+    for w in _waves_of(cp.ph2, cp.steps2, cp.T * cp.ilp):
+        kind = w[:, 0] & 3
+        nt = (w[:, 0] >> 2) & 7
+        ops = np.stack([w[:, 1] & 0xFFFF, w[:, 1] >> 16, w[:, 2] & 0xFFFF, w[:, 2] >> 16], axis=1)
+        used = np.zeros(ops.shape, dtype=bool)
+        used[kind == 0, :2] = True
+        used[kind == 1] = np.arange(4)[None, :] < nt[kind == 1, None]
+        r = [ops[used], (w[kind == 2, 0] >> 16)]
+        reads.append(np.unique(np.concatenate(r)))
+        writes.append(w[(kind == 0) | (kind == 1), 0] >> 16)
+    return reads, writes
 
 
 def verify_encoded(enc, ncoef):

@@ -185,7 +185,7 @@ def test_widest_team_only_where_a_256_lane_team_is_alone(monkeypatch):
     fit, the wider team would only lose lane efficiency."""
     built = []
 
-    def fake_build(prog, T, ilp, k=1):
+    def fake_build(prog, T, ilp, k=1, lag=1):
         built.append((T, ilp, k))
         width = T * ilp * k
         nslot = prog.slots + width
@@ -315,12 +315,87 @@ def test_gggg_production_program_matches_oracle():
     """The (gg|gg) cooperative program the build ships (512-lane teams,
     waves of up to two steps), walked wave by wave on the CPU, reproduces the
     oracle on compact quartets with O(1e-2) integrals."""
+    from paper_2605_10312_gb300.gen import verify
     prog = program.make(4, 4, 4, 4)
     deep, _ = coop.choose_both(prog)
-    assert (deep.T, deep.ilp) == coop.WIDEST_SHAPE and int(deep.steps1.max()) == 2
+    assert (deep.T, deep.ilp, deep.lag) == coop.WIDEST_SHAPE + (1,) and int(deep.steps1.max()) == 2
+    assert verify.verify_coop(deep, prog.L, len(encode.coef_table())) == []
     basis, q = synth.class_sweep((4, 4, 4, 4), 2, kset=(1, 2), seed=24, box_angstrom=0.5, exp_range=(0.3, 3.0))
     ref, _ = blocks(basis, q)
     ref = ref.reshape(q.shape[0], -1)
     assert np.abs(ref).max() > 1e-2
     got = run_coop(deep, prog, basis, q)
     assert within(got, ref).all()
+
+
+def test_split_barrier_schedule_keeps_adjacent_waves_apart():
+    """With split barriers a node's parents lie at least two waves back and a
+    slot is reused two waves after its last read, so nothing one wave writes
+    is read or written by the next (a lane may run wave w + 1 while another
+    still runs wave w)."""
+    g = vrr.build(2, 2, 2, 1)
+    order = vrr.schedule(g)
+    pos = np.empty(len(g), dtype=np.int64)
+    pos[np.array(order)] = np.arange(len(g))
+    par = [[p for _, p in ts] for ts in g.terms]
+    waves = coop.wave_schedule(par, pos, 32, lag=2)
+    wave_of = {v: w for w, vs in enumerate(waves) for v in vs}
+    assert len(wave_of) == len(g)
+    for v, ps in enumerate(par):
+        for p in ps:
+            assert wave_of[p] <= wave_of[v] - 2
+    slot, n = coop.allocate_over_waves(par, waves, np.ones(len(g), dtype=bool), lag=2)
+    last = {v: max([wave_of[c] for c, ps in enumerate(par) if v in ps], default=wave_of[v]) for v in range(len(g))}
+    owners = {}
+    for v in sorted(range(len(g)), key=lambda v: wave_of[v]):
+        s = int(slot[v])
+        if s in owners:
+            assert last[owners[s]] + 2 <= wave_of[v]
+        owners[s] = v
+
+
+@pytest.mark.parametrize("T,ilp", [(64, 2), (128, 2), (128, 4), (256, 2)])
+@pytest.mark.parametrize("ls", [(1, 1, 1, 1), (2, 2, 1, 1), (3, 1, 2, 0), (2, 2, 2, 1)])
+def test_split_barrier_programs_match_oracle(ls, T, ilp):
+    """Split-barrier programs reproduce the oracle wave by wave, and the
+    verifier finds no hazard between adjacent waves."""
+    from paper_2605_10312_gb300.gen import verify
+    prog = program.make(*ls)
+    cp = coop.build(prog, T, ilp, 1, lag=2)
+    assert cp.lag == 2
+    assert verify.verify_coop(cp, prog.L, len(encode.coef_table())) == []
+    basis, q = synth.class_sweep(ls, 3, kset=(1, 2), seed=29, box_angstrom=3.0, exp_range=(0.1, 30))
+    ref, _ = blocks(basis, q)
+    got = run_coop(cp, prog, basis, q)
+    assert within(got, ref.reshape(q.shape[0], -1)).all()
+
+
+def test_verifier_catches_adjacent_wave_hazards():
+    """A full-barrier program read as a split-barrier one has values that the
+    next wave reads; the verifier reports that, and a planted in-wave
+    read-after-write conflict too."""
+    import copy
+    from paper_2605_10312_gb300.gen import verify
+    prog = program.make(2, 2, 1, 1)
+    ncoef = len(encode.coef_table())
+    cp = coop.build(prog, 64, 2)
+    assert verify.verify_coop(cp, prog.L, ncoef) == []
+    c = copy.deepcopy(cp)
+    c.lag = 2
+    assert any("split barriers" in m for m in verify.verify_coop(c, prog.L, ncoef))
+    # in one wave: make a node write the slot another node of the wave reads
+    c = copy.deepcopy(cp)
+    W = c.T * c.ilp
+    w0 = c.ph1[:int(c.steps1[0]) * W]
+    for wv in range(1, len(c.steps1)):
+        lo = int(np.sum(c.steps1[:wv])) * W
+        blk = c.ph1[lo:lo + int(c.steps1[wv]) * W]
+        meta = blk[:, 3] >> 16
+        term = np.flatnonzero((meta & 0xC000) == 0)
+        keep = np.flatnonzero(((meta & 0x8000) == 0) & ((blk[:, 0] & 0xFFFF) != 0xFFFF))
+        if term.size and keep.size:
+            src = int(blk[term[0], 1] & 0xFFFF)
+            i = lo + int(keep[0])
+            c.ph1[i, 0] = (c.ph1[i, 0] & 0xFFFF0000) | src
+            break
+    assert any("reads a slot it writes" in m for m in verify.verify_coop(c, prog.L, ncoef))

@@ -26,9 +26,9 @@ def _density(nbf, seed):
     return C @ C.T / nbf
 
 
-def _gpu_jk(eri, basis, quartets, D, via_blocks=True):
+def _gpu_jk(eri, basis, quartets, D, via_blocks=True, persistent=False, tier="auto"):
     import torch
-    p = eri.Plan(basis, quartets, digest=True)
+    p = eri.Plan(basis, quartets, digest=True, persistent=persistent, tier=tier)
     Dt = torch.from_numpy(D).cuda()
     J = torch.zeros_like(Dt)
     K = torch.zeros_like(Dt)
@@ -83,3 +83,28 @@ def test_jk_errors(eri):
     D2 = torch.zeros((14, 14), dtype=torch.float64, device="cuda")
     with pytest.raises(eri.EriError):
         p2.compute_jk(D2, torch.zeros_like(D2))
+
+
+@pytest.mark.parametrize("nwater,tier", [(1, "auto"), (2, "auto"), (1, "coop")])
+def test_jk_fused_into_persistent_launch(eri, nwater, tier):
+    """A persistent digest plan digests each quartet inside the evaluation
+    launch (the team finishing a quartet's last part; quartets whose parts
+    all run on the register tier in a pass after it); J and K against the
+    oracle's full-tensor contraction, for every unique quartet of one and two
+    waters (multi-part quartets included), each orbit through a random
+    representative.  tier "coop" puts every class in the persistent launch."""
+    basis = synth.water_cluster(nwater, seed=8)
+    q = synth.all_unique_quartets(basis.nshell)
+    rng = np.random.default_rng(4)
+    perms = [(0, 1, 2, 3), (1, 0, 2, 3), (0, 1, 3, 2), (1, 0, 3, 2), (2, 3, 0, 1), (3, 2, 0, 1), (2, 3, 1, 0), (3, 2, 1, 0)]
+    qr = np.array([row[list(perms[rng.integers(8)])] for row in q], dtype=np.int32)
+    nbf = int(oracle.basis_function_offsets(basis)[-1])
+    D = _density(nbf, 5)
+    J, K = _gpu_jk(eri, basis, qr, D, via_blocks=False, persistent=True, tier=tier)
+    Jr, Kr = oracle.jk(basis, D, nthreads=8)
+    assert within(J.ravel(), Jr.ravel()).all(), report(J.ravel(), Jr.ravel())
+    assert within(K.ravel(), Kr.ravel()).all(), report(K.ravel(), Kr.ravel())
+    # and the same as the separate digestion pass of an ordinary plan
+    J2, K2 = _gpu_jk(eri, basis, qr, D, via_blocks=False)
+    assert within(J.ravel(), J2.ravel(), atol=1e-13, rtol=1e-11).all()
+    assert within(K.ravel(), K2.ravel(), atol=1e-13, rtol=1e-11).all()

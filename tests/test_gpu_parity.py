@@ -102,3 +102,20 @@ def test_permutations_agree(eri):
             b = np.transpose(got[offp[i]:offp[i + 1]].reshape(dims), np.argsort(p)).ravel()
             r = base[off[i]:off[i + 1]]
             assert within(b, r, atol=1e-14, rtol=1e-12).all()
+
+
+@pytest.mark.parametrize("votes", ["off", "on"])
+@pytest.mark.parametrize("ls", [(1, 1, 1, 1), (2, 2, 2, 1), (2, 2, 2, 2), (3, 3, 2, 2), (3, 3, 3, 3), (4, 4, 4, 3),
+                                (4, 4, 4, 4)])
+def test_cooperative_program_forms(eri, ls, votes):
+    """Both forms of the team-cooperative programs -- optional FP64 terms
+    predicated per lane, or skipped by a warp none of whose lanes needs
+    them -- against the oracle, on deep, shallow and single-primitive
+    contractions (K per shell from {1, 2, 6}); (pp|pp) through the
+    cooperative tier instead of its compiled kernel."""
+    n = {1: 60, 2: 24, 3: 6, 4: 3}[ls[0]]
+    basis, q = synth.class_sweep(ls, n, kset=(1, 2, 6) if ls[0] < 4 else (1, 2), seed=90 + sum(ls),
+                                 box_angstrom=3.0, exp_range=(0.1, 60.0))
+    got, _ = _run(eri, basis, q, votes=votes, tier="coop")
+    ref, _ = adjudicated(got, basis, q)
+    assert within(got, ref).all(), report(got, ref)
