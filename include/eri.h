@@ -284,6 +284,33 @@ int eri_set_class_tier(int la, int lb, int lc, int ld, int tier);
  * the autotuner).  Applies to plans built afterwards, process-wide. */
 int eri_set_class_votes(int la, int lb, int lc, int ld, int votes);
 
+/* The team-cooperative shapes the build ships for a class (la lb | lc ld)
+ * under the default options: entry 0 is the shape taken for deep
+ * contractions, then the shape for shallow ones when it differs, then the
+ * alternatives an autotuner may time against them.  Each entry is five
+ * int32: team lanes T, nodes per lane per step, steps per Phase-1 wave,
+ * steps per Phase-2 wave, value slots.  Writes min(count, max) entries to
+ * info (host memory, 5 * max int32) and returns the count (0: the class has
+ * no cooperative program), or a negative error code.  The shapes are the
+ * generator's (the paper's Tier-2 kernel of Sec. III-C re-derived per
+ * class); the index into this list names a shape below. */
+int eri_class_shapes(int la, int lb, int lc, int ld, int32_t* info, int max);
+
+/* Preferred cooperative shape and vote form of a class for one kind of
+ * contraction: kind 0 deep (more than 12 primitive quartets per part), 1
+ * shallow (2 to 12), 2 single primitive quartet; shape = an index into
+ * eri_class_shapes (-1 clears the entry); votes 0 (the class table of
+ * eri_set_class_votes, else the static rule), 1 predicated, 2 warp votes.
+ * Written by the autotuner; applies to plans with default generator options
+ * built afterwards, process-wide.  An index beyond the class's list is
+ * ignored at plan time. */
+int eri_set_class_shape(int la, int lb, int lc, int ld, int kind, int shape, int votes);
+
+/* Cooperative shape of launch i of a plan (see eri_plan_launch_info): info
+ * (host, 4 int32) = {kind, shape index, team lanes T, vote form 1 or 2}, or
+ * {-1, -1, 0, 0} for a launch of another tier.  ERI_EINVAL for a bad index. */
+int eri_plan_launch_shape(const eri_plan_t* plan, int i, int32_t* info);
+
 /* Capture eri_compute(plan, out, stream) into a CUDA graph held by the plan
  * (stream must not be the legacy default stream; launch timing is off in the
  * graph), and replay it with eri_plan_graph_launch: all of the plan's class

@@ -40,6 +40,9 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + CS
 # straight-line size (VRR terms + 1.5 x Phase-2 operations) up to which a
 # class gets a compiled register-tier kernel; larger classes run as programs
 REG_TIER_MAX = 3000
+# cooperative shapes shipped per class besides the generator's choices, for
+# the autotuner to time (the next best by the generator's score)
+COOP_ALTS = 2
 
 # classes and option variants of the paper's ablations (Sec. V-B): axis rule,
 # DSA off, materialize-then-transform, Cartesian output
@@ -105,15 +108,22 @@ def _class_job(args):
                         steps1=cp.steps1.tobytes(), steps2=cp.steps2.tobytes(), nw1=int(cp.steps1.shape[0]),
                         nw2=int(cp.steps2.shape[0]), ph1=cp.ph1.tobytes(), ph2=cp.ph2.tobytes(),
                         n1=int(cp.ph1.shape[0]), n2=int(cp.ph2.shape[0]), eff1=cp.eff1, eff2=cp.eff2,
-                        issue=coop.fp64_issue(cp), lag=cp.lag)
-        deep, shallow = coop.choose_both(prog)
-        for cp in (deep, shallow):
+                        issue=coop.fp64_issue(cp), lag=cp.lag, steps=coop.shape_key(cp)[2:],
+                        wf=coop.shared_wavefronts(cp, cp.nslot * 8 + coop.DEEP_ROWS * coop.ROW_BYTES + cp.nh * 8
+                                                  <= 227 * 1024))
+        if want_reg:
+            deep, shallow, alts = coop.choose_both(prog, alts=COOP_ALTS)
+        else:
+            (deep, shallow), alts = coop.choose_both(prog), []
+        for cp in [deep, shallow] + list(alts):
             if cp is not None:
                 verify.check(ls, verify.verify_coop(cp, prog.L, ncoef))
         rec["coop"] = pack(deep)
         # a second shape for shallow contractions, when it differs
-        if shallow is not None and (shallow.T, shallow.ilp) != (deep.T, deep.ilp):
+        if shallow is not None and coop.shape_key(shallow) != coop.shape_key(deep):
             rec["coop_shallow"] = pack(shallow)
+        # other shapes the autotuner may time against these
+        rec["coop_alts"] = [pack(cp) for cp in alts]
     return rec
 
 
@@ -132,7 +142,7 @@ def generate(classes, opts=("prose", "dsa", "stepwise"), want_reg=True, jobs=Non
 
 def write_blob(path, recs, boys, c2s):
     with open(path + ".tmp", "wb") as f:
-        f.write(b"ERIPRG02")
+        f.write(b"ERIPRG03")
         f.write(struct.pack("<I", boys.size))
         f.write(np.ascontiguousarray(boys, dtype="<f8").tobytes())
         f.write(struct.pack("<I", len(c2s)))
@@ -146,19 +156,21 @@ def write_blob(path, recs, boys, c2s):
             f.write(r["ph1"])
             f.write(r["ph2"])
         # team-cooperative programs: the deep-contraction shape of every class,
-        # then the shallow-contraction shapes that differ from it
+        # then the shallow-contraction shapes that differ from it, then the
+        # autotuner's alternative shapes (any number per class)
         for key in ("coop", "coop_shallow"):
-            _write_coops(f, [r for r in recs if key in r], key)
+            _write_coops(f, [(r, r[key]) for r in recs if key in r])
+        _write_coops(f, [(r, c) for r in recs for c in r.get("coop_alts", ())])
     os.replace(path + ".tmp", path)
 
 
-def _write_coops(f, coops, key):
+def _write_coops(f, coops):
     f.write(struct.pack("<I", len(coops)))
-    for r in coops:
-        o, c = r["opts"], r[key]
+    for r, c in coops:
+        o = r["opts"]
         f.write(struct.pack("<8b", *r["ls"], AXIS[o[0]], SCHED[o[1]], SPH[o[2]], c["ilp"]))
-        f.write(struct.pack("<13i", c["T"], c["nh"], c["nslot"], c["L"], c["nw1"], c["nw2"], c["n1"], c["n2"],
-                            *c["dims"], c["lag"]))
+        f.write(struct.pack("<15i", c["T"], c["nh"], c["nslot"], c["L"], c["nw1"], c["nw2"], c["n1"], c["n2"],
+                            *c["dims"], c["lag"], *c["steps"]))
         f.write(struct.pack("<2d", r["flops_prim"], r["flops_p2"]))
         f.write(c["steps1"])
         f.write(c["steps2"])
@@ -244,7 +256,8 @@ def build(force=False, jobs=None, log=print):
         with open(os.path.join(BUILD, "classes.tsv"), "w") as f:
             f.write("la\tlb\tlc\tld\ttier\tvrr_nodes\tpeak_live\tnslot\tnh\tnout\tper_prim_flops\tp2_flops"
                     "\tcoop_T\tcoop_ilp\tcoop_nslot\tcoop_eff1\tcoop_eff2\tshallow_T\tshallow_ilp"
-                    "\tcoop_fp64_ceil1\tcoop_fp64_ceil2\n")
+                    "\tcoop_fp64_ceil1\tcoop_fp64_ceil2\tcoop_wave_steps1\tcoop_wave_steps2"
+                    "\tcoop_smem_wf1\tcoop_smem_ideal1\tcoop_smem_wf2\tcoop_smem_ideal2\n")
             for r in sorted(recs, key=lambda r: r["ls"]):
                 c = r["counts"]
                 cp = r.get("coop")
@@ -261,7 +274,13 @@ def build(force=False, jobs=None, log=print):
                                                    # flops / (64 x FP64 warp-instructions)
                                                    round(c["vrr_flops"] / (64 * max(1, cp["issue"][0])), 3) if cp else "",
                                                    round(c["p2_flops"] / (64 * max(1, cp["issue"][1])), 3)
-                                                   if cp else "")) + "\n")
+                                                   if cp else "",
+                                                   # steps per wave of each phase; modelled shared-memory
+                                                   # wavefronts of the value slots and the conflict-free
+                                                   # count (Phase 1 per primitive quartet, Phase 2 per
+                                                   # shell quartet)
+                                                   *(cp["steps"] if cp else ("", "")),
+                                                   *(cp["wf"] if cp else ("", "", "", "")))) + "\n")
         open(stamp, "w").write(gen_key)
     units = [os.path.join(CSRC, "eri_runtime.cu"), os.path.join(CSRC, "eri_exec.cu"),
              os.path.join(CSRC, "eri_coop.cu"), os.path.join(CSRC, "eri_digest.cu"),

@@ -103,6 +103,7 @@ struct CoopProg {
   int opts[3];
   int ilp;
   int T, nh, nslot, L, nw1, nw2, n1, n2;
+  int k1 = 1, k2 = 1;  // steps per Phase-1 / Phase-2 wave
   int dims[4];
   double flops_prim, flops_p2;
   std::vector<uint32_t> steps1, steps2, ph1, ph2;
@@ -119,6 +120,7 @@ struct Library {
   std::map<std::vector<int>, std::unique_ptr<ClassProg>> progs;  // key: ls[4] + opts[3]
   std::map<std::vector<int>, std::unique_ptr<CoopProg>> coops;   // key: ls[4] + opts[3]
   std::map<std::vector<int>, std::unique_ptr<CoopProg>> coops_shallow;  // shapes for K4 <= kShallowK4
+  std::map<std::vector<int>, std::vector<std::unique_ptr<CoopProg>>> coops_alt;  // autotuner candidates
   std::map<std::vector<int>, const void*> reg;                      // key: ls[4]
   std::map<std::vector<int>, const void*> reg_f32;                  // key: ls[4]
   double* d_boys = nullptr;
@@ -155,7 +157,7 @@ bool load_blob(Library& L, const std::string& path, bool tables) {
   if (!f) return false;
   char magic[8];
   uint32_t nb = 0, nc = 0, ncls = 0;
-  bool ok = rd(f, magic, 8) && memcmp(magic, "ERIPRG02", 8) == 0 && rd(f, &nb);
+  bool ok = rd(f, magic, 8) && memcmp(magic, "ERIPRG03", 8) == 0 && rd(f, &nb);
   std::vector<double> boys(nb);
   ok = ok && rd(f, boys.data(), nb) && rd(f, &nc);
   std::vector<double> c2s(nc);
@@ -185,18 +187,18 @@ bool load_blob(Library& L, const std::string& path, bool tables) {
     std::vector<int> key = {p->ls[0], p->ls[1], p->ls[2], p->ls[3], p->opts[0], p->opts[1], p->opts[2]};
     L.progs[key] = std::move(p);
   }
-  // team-cooperative programs: the deep-contraction section, then the
-  // shallow-contraction section (shapes that differ from the deep one)
-  for (int section = 0; section < 2 && ok; ++section) {
+  // team-cooperative programs: the deep-contraction section, the
+  // shallow-contraction section (shapes that differ from the deep one), then
+  // the autotuner's alternative shapes
+  for (int section = 0; section < 3 && ok; ++section) {
     uint32_t ncoop = 0;
     if (!rd(f, &ncoop)) break;
-    auto& dst = section == 0 ? L.coops : L.coops_shallow;
     for (uint32_t c = 0; ok && c < ncoop; ++c) {
       auto p = std::make_unique<CoopProg>();
       int8_t hdr[8];
-      int32_t iv[13];
+      int32_t iv[15];
       double fv[2];
-      ok = rd(f, hdr, 8) && rd(f, iv, 13) && rd(f, fv, 2);
+      ok = rd(f, hdr, 8) && rd(f, iv, 15) && rd(f, fv, 2);
       if (!ok) break;
       for (int k = 0; k < 4; ++k) p->ls[k] = hdr[k];
       for (int k = 0; k < 3; ++k) p->opts[k] = hdr[4 + k];
@@ -211,6 +213,8 @@ bool load_blob(Library& L, const std::string& path, bool tables) {
       p->n1 = iv[6];
       p->n2 = iv[7];
       for (int k = 0; k < 4; ++k) p->dims[k] = iv[8 + k];
+      p->k1 = iv[13];
+      p->k2 = iv[14];
       p->flops_prim = fv[0];
       p->flops_p2 = fv[1];
       p->steps1.resize(p->nw1);
@@ -221,7 +225,10 @@ bool load_blob(Library& L, const std::string& path, bool tables) {
            rd(f, p->ph1.data(), p->ph1.size()) && rd(f, p->ph2.data(), p->ph2.size());
       if (!ok) break;
       std::vector<int> key = {p->ls[0], p->ls[1], p->ls[2], p->ls[3], p->opts[0], p->opts[1], p->opts[2]};
-      dst[key] = std::move(p);
+      if (section == 2)
+        L.coops_alt[key].push_back(std::move(p));
+      else
+        (section == 0 ? L.coops : L.coops_shallow)[key] = std::move(p);
     }
   }
   fclose(f);
@@ -540,6 +547,8 @@ struct Bucket {
   int batch = 0;                 // cooperative tier: coefficient rows per team
   int single = 0;                // cooperative tier: every part has one primitive quartet
   int vote = 0;                  // cooperative tier: optional FP64 terms behind warp votes
+  int kind = -1;                 // cooperative tier: 0 deep, 1 shallow, 2 single-primitive parts
+  int shape = -1;                // cooperative tier: index of its program in class_shapes
   int fp32 = 0;                  // recurrences in FP32 (quartets with a small Schwarz bound)
   int round = 0;                 // part round: buckets of a round are independent
   int lane = 0;                  // stream of its round (0 = the caller's stream)
@@ -691,6 +700,23 @@ struct eri_plan_s {
 static int nfun(int l, bool cart) { return cart ? (l + 1) * (l + 2) / 2 : 2 * l + 1; }
 int preferred_tier(const int ls[4]);
 int preferred_votes(const int ls[4]);
+bool preferred_shape(const int ls[4], int kind, int* shape, int* votes);
+
+// The cooperative shapes shipped for a class (default options): the deep
+// shape, the shallow one when it differs, then the alternatives.  The index
+// into this list names a shape in eri_class_shapes / eri_set_class_shape.
+std::vector<CoopProg*> class_shapes(Library& L, const std::vector<int>& key) {
+  std::vector<CoopProg*> v;
+  auto d = L.coops.find(key);
+  if (d == L.coops.end()) return v;
+  v.push_back(d->second.get());
+  auto sh = L.coops_shallow.find(key);
+  if (sh != L.coops_shallow.end()) v.push_back(sh->second.get());
+  auto al = L.coops_alt.find(key);
+  if (al != L.coops_alt.end())
+    for (auto& p : al->second) v.push_back(p.get());
+  return v;
+}
 
 static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* basis, const int32_t* quartets,
                      int64_t nq, const double* qbound, double fp32_below, const eri_opts* opts_in,
@@ -1118,13 +1144,22 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
         auto sit = L.coops_shallow.find(pkey);
         if (sit != L.coops_shallow.end()) cp = sit->second.get();
       }
+      // the autotuner's shape for this class and kind of contraction
+      const int kind = coop_cat(k4_first);
+      int pshape = -1, pvotes = 0;
+      const std::vector<CoopProg*> shapes = class_shapes(L, pkey);
+      if (default_opts && preferred_shape(b.ls, kind, &pshape, &pvotes) && pshape >= 0 &&
+          pshape < (int)shapes.size())
+        cp = shapes[pshape];
+      b.kind = kind;
+      b.shape = (int)(std::find(shapes.begin(), shapes.end(), cp) - shapes.begin());
       // warp votes around the optional FP64 terms: on request, else the
       // class table's preference (autotuner), else the static rule, measured
       // on the sweep classes with K per shell from {1, 3, 6}: votes pay for
       // teams of 128 lanes or more ((ff|ff) 0.610 -> 0.690 of the FP64 rate,
       // (gg|gg) 0.620 -> 0.632) and cost 64-lane teams ((dd|dd) 0.602 -> 0.582)
       {
-        const int pv = preferred_votes(b.ls);
+        const int pv = pvotes ? pvotes : preferred_votes(b.ls);
         const int want_v = opts.votes ? opts.votes : pv ? pv : (cp->T >= 128 ? 2 : 1);
         b.vote = want_v == 2 ? 1 : 0;
       }
@@ -1837,6 +1872,22 @@ extern "C" int eri_plan_launch_info(const eri_plan_t* plan, int i, int32_t* info
   return ERI_OK;
 }
 
+extern "C" int eri_plan_launch_shape(const eri_plan_t* plan, int i, int32_t* info) {
+  if (!plan || !info || i < 0 || i >= eri_plan_launch_count(plan)) return fail(ERI_EINVAL, "bad launch index");
+  int32_t v[4] = {-1, -1, 0, 0};
+  if (i > 0) {
+    const Bucket& b = plan->buckets[i - 1];
+    if (b.tier == TIER_COOP || (b.tier == TIER_PERSIST && b.coop)) {
+      v[0] = b.kind;
+      v[1] = b.shape;
+      v[2] = b.coop ? b.coop->T : 0;
+      v[3] = b.vote ? 2 : 1;
+    }
+  }
+  memcpy(info, v, sizeof v);
+  return ERI_OK;
+}
+
 extern "C" int eri_compute_host(eri_plan_t* plan, double* host_out, void* stream_) {
   if (!plan) return fail(ERI_EINVAL, "NULL plan");
   if (plan->nq == 0) return ERI_OK;
@@ -2089,6 +2140,48 @@ int preferred_votes(const int ls[4]) {
   std::lock_guard<std::mutex> g(g_tier_mu);
   auto it = g_vote_table.find({ls[0], ls[1], ls[2], ls[3]});
   return it == g_vote_table.end() ? 0 : it->second;
+}
+
+namespace {
+// (class, kind) -> (shape index, vote form) (autotuner)
+std::map<std::vector<int>, std::pair<int, int>> g_shape_table;
+}  // namespace
+
+extern "C" int eri_set_class_shape(int la, int lb, int lc, int ld, int kind, int shape, int votes) {
+  if (la < 0 || lb < 0 || lc < 0 || ld < 0 || la > ERI_MAX_L || lb > ERI_MAX_L || lc > ERI_MAX_L ||
+      ld > ERI_MAX_L || kind < 0 || kind > 2 || shape < -1 || votes < 0 || votes > 2)
+    return fail(ERI_EINVAL, "bad class, kind, shape or vote form");
+  std::lock_guard<std::mutex> g(g_tier_mu);
+  if (shape < 0)
+    g_shape_table.erase({la, lb, lc, ld, kind});
+  else
+    g_shape_table[{la, lb, lc, ld, kind}] = {shape, votes};
+  return ERI_OK;
+}
+
+bool preferred_shape(const int ls[4], int kind, int* shape, int* votes) {
+  std::lock_guard<std::mutex> g(g_tier_mu);
+  auto it = g_shape_table.find({ls[0], ls[1], ls[2], ls[3], kind});
+  if (it == g_shape_table.end()) return false;
+  *shape = it->second.first;
+  *votes = it->second.second;
+  return true;
+}
+
+extern "C" int eri_class_shapes(int la, int lb, int lc, int ld, int32_t* info, int max) {
+  if (la < 0 || lb < 0 || lc < 0 || ld < 0 || la > ERI_MAX_L || lb > ERI_MAX_L || lc > ERI_MAX_L ||
+      ld > ERI_MAX_L || max < 0 || (max > 0 && !info))
+    return fail(ERI_EINVAL, "bad class or output");
+  int rc = ensure_library();
+  if (rc) return rc;
+  Library& L = lib();
+  const std::vector<CoopProg*> v = class_shapes(L, {la, lb, lc, ld, 0, 0, 0});
+  for (int i = 0; i < (int)v.size() && i < max; ++i) {
+    const CoopProg* p = v[i];
+    const int32_t e[5] = {p->T, p->ilp, p->k1, p->k2, p->nslot};
+    memcpy(info + 5 * i, e, sizeof e);
+  }
+  return (int)v.size();
 }
 
 extern "C" int eri_plan_graph_capture(eri_plan_t* plan, double* out, void* stream_) {

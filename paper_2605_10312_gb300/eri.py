@@ -113,6 +113,12 @@ def library(path: str = LIB):
         lib.eri_plan_graph_capture.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.eri_plan_graph_launch.restype = ctypes.c_int
         lib.eri_plan_graph_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_class_shapes.restype = ctypes.c_int
+        lib.eri_class_shapes.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p, ctypes.c_int]
+        lib.eri_set_class_shape.restype = ctypes.c_int
+        lib.eri_set_class_shape.argtypes = [ctypes.c_int] * 7
+        lib.eri_plan_launch_shape.restype = ctypes.c_int
+        lib.eri_plan_launch_shape.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         lib.eri_boys_eval.restype = ctypes.c_int
         lib.eri_boys_eval.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_void_p]
@@ -255,17 +261,23 @@ class Plan:
 
     def launches(self):
         """Per-launch records of the last compute (call after the stream has
-        completed): class, tier, grid, block, quartets, flops, ms."""
+        completed): class, tier, grid, block, quartets, flops, ms, and for the
+        cooperative tier the kind of contraction, the shape index (into
+        class_shapes), the team size and the vote form."""
         lib = library()
         out = []
         for i in range(lib.eri_plan_launch_count(self._h)):
             info = np.zeros(8, dtype=np.int32)
+            shp = np.zeros(4, dtype=np.int32)
             fl = ctypes.c_double()
             ms = ctypes.c_float()
             _check(lib.eri_plan_launch_info(self._h, i, info.ctypes.data, ctypes.byref(fl), ctypes.byref(ms)))
+            _check(lib.eri_plan_launch_shape(self._h, i, shp.ctypes.data))
             out.append(dict(cls=tuple(int(x) for x in info[:4]), tier=int(info[4]), grid=int(info[5]),
                             block=int(info[6]), quartets=int(info[7]), flops=fl.value, ms=ms.value,
-                            precision=int(lib.eri_plan_launch_precision(self._h, i))))
+                            precision=int(lib.eri_plan_launch_precision(self._h, i)),
+                            kind=KINDS_INV.get(int(shp[0])), shape=int(shp[1]), team=int(shp[2]),
+                            votes={1: "off", 2: "on"}.get(int(shp[3]))))
         return out
 
     def compute(self, out, stream=None):
@@ -362,6 +374,30 @@ def boys(T, L, form="coop", stream=None):
     _check(library().eri_boys_eval(T.data_ptr(), T.numel(), int(L), BOYS_FORMS[form], F.data_ptr(),
                                    _stream_handle(stream)))
     return F
+
+
+KINDS = {"deep": 0, "shallow": 1, "single": 2}
+KINDS_INV = {v: k for k, v in KINDS.items()}
+
+
+def class_shapes(ls):
+    """The cooperative shapes shipped for class ls (eri_class_shapes): a list
+    of dicts (T, ilp, k1, k2, nslot); index 0 is the deep shape."""
+    lib = library()
+    n = lib.eri_class_shapes(*[int(x) for x in ls], None, 0)
+    _check(min(n, 0))
+    buf = (ctypes.c_int32 * max(1, 5 * n))()
+    _check(min(lib.eri_class_shapes(*[int(x) for x in ls], buf, n), 0))
+    return [dict(zip(("T", "ilp", "k1", "k2", "nslot"), buf[5 * i:5 * i + 5])) for i in range(n)]
+
+
+def set_class_shape(ls, kind, shape, votes="auto"):
+    """Process-wide preferred cooperative shape (an index into class_shapes,
+    -1 clears) and vote form of class ls for one kind of contraction
+    ("deep", "shallow", "single")."""
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    v = VOTES[votes] if isinstance(votes, str) else int(votes)
+    _check(library().eri_set_class_shape(*[int(x) for x in ls], k, int(shape), v))
 
 
 def set_class_votes(ls, votes):

@@ -130,6 +130,68 @@ def _allocate(wave_of, last, needs_slot, order, first_slot=0, lag=1):
     return slot, nxt - first_slot
 
 
+NBANK = 16  # 8-byte shared-memory words: 32 four-byte banks serve 16 words per half-warp
+
+
+def _allocate_banked(wave_of, last, needs_slot, order, groups, fixed=None, lag=1):
+    """Slot allocation as _allocate, but a value takes, among the free slots,
+    one whose shared-memory bank its accesses share with the fewest values
+    already placed.  A 64-bit shared access of a warp is served in two
+    half-warp passes, each needing as many wavefronts as the most values it
+    finds in one bank (8-byte word index mod 16); ``groups[v]`` lists the
+    access groups (one per half-warp instruction) value v belongs to.  The
+    choice never creates a slot while one is free, so the slot count equals
+    _allocate's.  ``fixed``: (group, bank) pairs of operands outside the
+    slots (accumulators in shared memory) already in a group."""
+    n = len(wave_of)
+    ng = 1 + max((max(g) for g in groups if len(g)), default=-1)
+    if fixed is not None and len(fixed):
+        ng = max(ng, 1 + int(fixed[:, 0].max()))
+    hist = np.zeros((max(1, ng), NBANK), dtype=np.int32)
+    if fixed is not None and len(fixed):
+        np.add.at(hist, (fixed[:, 0], fixed[:, 1]), 1)
+    free = [[] for _ in range(NBANK)]
+    nxt = 0
+    nw = int(wave_of.max()) + 1 if n else 0
+    release_at = [[] for _ in range(max(nw, int(last.max()) + 1 if n else 0) + 1 + lag)]
+    pop, push = heapq.heappop, heapq.heappush
+    cur_w = -1
+    wl = wave_of.tolist()
+    ll = last.tolist()
+    nl = needs_slot.tolist()
+    out = [-1] * n
+    big = np.int64(1) << 40
+    for v in order:
+        w = wl[v]
+        while cur_w < w:
+            cur_w += 1
+            for s in release_at[cur_w]:
+                push(free[s % NBANK], s)
+        if not nl[v]:
+            continue
+        g = groups[v]
+        tops = np.array([f[0] if f else big for f in free], dtype=np.int64)
+        if len(g):
+            h = hist[g]
+            # groups whose most loaded bank this choice would deepen
+            cost = (h >= h.max(1)[:, None]).sum(0).astype(np.int64)
+        else:
+            cost = np.zeros(NBANK, dtype=np.int64)
+        # fewest conflicts first, then the lowest slot
+        key = np.where(tops == big, big, cost * (np.int64(1) << 32) + tops)
+        b = int(np.argmin(key))
+        if key[b] == big:
+            s = nxt
+            nxt += 1
+        else:
+            s = pop(free[b])
+        if len(g):
+            hist[g, s % NBANK] += 1
+        out[v] = s
+        release_at[ll[v] + lag].append(s)
+    return np.asarray(out, dtype=np.int64), nxt
+
+
 def _lifetimes(parents, waves, pinned_until_end=()):
     """Wave of every node and the last wave that reads it (its own wave if
     nothing does; pinned nodes: past the last wave)."""
@@ -353,19 +415,25 @@ def release(prog):
         prog.__dict__.pop(name, None)
 
 
-def _width_form(prog, width, lag=1):
-    """Waves, slots and descriptor rows of both phases for waves of up to
-    ``width`` nodes and parents at least ``lag`` waves back (cached per
-    program, width and lag: shapes of equal width share them)."""
+def _p1_waves(prog, width, lag):
     st = _static(prog)
-    cached = prog._coop_width.get((width, lag))
-    if cached is not None:
-        return cached
-    nh = st.nh
-    # ---------------- Phase 1
-    waves1 = _waves(st.cons1, list(st.npar1), st.prio1, width, lag)
-    wave_of, last = _lifetimes(st.par1, waves1)
-    slot1, nslot1 = _allocate(wave_of, last, st.consumed, [v for w in waves1 for v in w], lag=lag)
+    key = ("w1", width, lag)
+    if key not in prog._coop_width:
+        waves1 = _waves(st.cons1, list(st.npar1), st.prio1, width, lag)
+        prog._coop_width[key] = (waves1,) + _lifetimes(st.par1, waves1)
+    return prog._coop_width[key]
+
+
+def _p2_waves(prog, width, lag):
+    st = _static(prog)
+    key = ("w2", width, lag)
+    if key not in prog._coop_width:
+        waves2 = _waves(st.cons2, list(st.npar2), st.prio2, width, lag)
+        prog._coop_width[key] = (waves2,) + _lifetimes(st.par2, waves2)
+    return prog._coop_width[key]
+
+
+def _p1_rows(st, slot1):
     src = st.src1
     sl = np.where(src >= 0, slot1[np.maximum(src, 0)], 0)
     rows1 = np.empty((st.n1, 4), dtype=np.int64)
@@ -373,10 +441,11 @@ def _width_form(prog, width, lag=1):
     rows1[:, 1] = sl[:, 0] | (sl[:, 1] << 16)
     rows1[:, 2] = sl[:, 2] | (sl[:, 3] << 16)
     rows1[:, 3] = sl[:, 4] | (st.meta1 << 16)
-    # ---------------- Phase 2
-    waves2 = _waves(st.cons2, list(st.npar2), st.prio2, width, lag)
-    wave_of2, last2 = _lifetimes(st.par2, waves2)
-    slot2, nslot2 = _allocate(wave_of2, last2, st.needs2, [v for w in waves2 for v in w], lag=lag)
+    return rows1
+
+
+def _p2_rows(st, slot2):
+    nh = st.nh
     # operand id of a node: H index, or nh + its value slot
     oid = np.concatenate([np.arange(nh, dtype=np.int64), nh + slot2])
 
@@ -390,20 +459,156 @@ def _width_form(prog, width, lag=1):
     rows2[:, 1] = c[:, 1] | o[:, 0] | (o[:, 1] << 16)
     rows2[:, 2] = c[:, 2] | o[:, 2] | (o[:, 3] << 16)
     rows2[:, 3] = c[:, 3]
-    form = (waves1, rows1, int(nslot1), waves2, rows2, int(nslot2))
-    prog._coop_width[(width, lag)] = form
+    return rows2
+
+
+def _p1_form(prog, width, lag=1):
+    """Phase-1 waves, slots and descriptor rows for waves of up to ``width``
+    nodes and parents at least ``lag`` waves back (cached per program, width
+    and lag: shapes of equal width share them)."""
+    st = _static(prog)
+    key = (1, width, lag)
+    cached = prog._coop_width.get(key)
+    if cached is not None:
+        return cached
+    waves1, wave_of, last = _p1_waves(prog, width, lag)
+    slot1, nslot1 = _allocate(wave_of, last, st.consumed, [v for w in waves1 for v in w], lag=lag)
+    form = (waves1, _p1_rows(st, slot1), int(nslot1))
+    prog._coop_width[key] = form
     return form
 
 
-def build(prog, T=128, ilp=ILP, wave_steps=1, lag=1):
+def _p2_form(prog, width, lag=1):
+    """Phase-2 waves, slots and descriptor rows (as _p1_form)."""
+    st = _static(prog)
+    key = (2, width, lag)
+    cached = prog._coop_width.get(key)
+    if cached is not None:
+        return cached
+    waves2, wave_of2, last2 = _p2_waves(prog, width, lag)
+    slot2, nslot2 = _allocate(wave_of2, last2, st.needs2, [v for w in waves2 for v in w], lag=lag)
+    form = (waves2, _p2_rows(st, slot2), int(nslot2))
+    prog._coop_width[key] = form
+    return form
+
+
+def _positions(waves, T, ilp, shape):
+    """Where _pack puts each node: (global step, lane, node slot of the lane)
+    for every node of the waves (-1 elsewhere)."""
+    W = ilp * T
+    n = int(shape.shape[0])
+    step = np.full(n, -1, dtype=np.int64)
+    lane = np.full(n, -1, dtype=np.int64)
+    u = np.full(n, -1, dtype=np.int64)
+    if not len(waves):
+        return step, lane, u
+    sizes = np.array([len(w) for w in waves], dtype=np.int64)
+    steps = (sizes + W - 1) // W
+    idx = np.concatenate([np.asarray(w, dtype=np.int64) for w in waves])
+    wave_id = np.repeat(np.arange(len(waves)), sizes)
+    idx = idx[np.lexsort((np.arange(idx.size), shape[idx], wave_id))]
+    k = np.arange(idx.size) - np.repeat(np.cumsum(sizes) - sizes, sizes)
+    s, r = np.divmod(k, W)
+    step[idx] = np.repeat(np.cumsum(steps) - steps, sizes) + s
+    lane[idx] = r % T
+    u[idx] = r // T
+    return step, lane, u
+
+
+def _group_key(step, lane, u, k, T, ilp):
+    """Access group of a half-warp instruction: operand position k (0-4
+    loads, 5 the result store) of node slot u in one half of one warp in
+    one step."""
+    return (((step * (T // 32) + lane // 32) * 2 + (lane % 32) // 16) * ilp + u) * 6 + k
+
+
+def _groups_by_value(n, pairs):
+    """pairs: (value, group) arrays -> groups[value] (sorted, distinct)."""
+    v, g = pairs
+    groups = [np.empty(0, dtype=np.int64)] * n
+    if v.size == 0:
+        return groups
+    o = np.lexsort((g, v))
+    v, g = v[o], g[o]
+    keep = np.ones(v.size, dtype=bool)
+    keep[1:] = (v[1:] != v[:-1]) | (g[1:] != g[:-1])
+    v, g = v[keep], g[keep]
+    cuts = np.flatnonzero(np.diff(v)) + 1
+    for vv, gg in zip(np.split(v, cuts), np.split(g, cuts)):
+        groups[int(vv[0])] = gg
+    return groups
+
+
+def _p1_banked(prog, width, lag, T, ilp):
+    """Phase-1 form with bank-aware slots for teams of T lanes x ilp."""
+    st = _static(prog)
+    waves1, wave_of, last = _p1_waves(prog, width, lag)
+    step, lane, u = _positions(waves1, T, ilp, st.shape1)
+    vs, gs = [], []
+    node = np.arange(st.n1, dtype=np.int64)
+    live = st.consumed
+    vs.append(node[live])
+    gs.append(_group_key(step[live], lane[live], u[live], 5, T, ilp))
+    for k in range(5):
+        p = st.src1[:, k]
+        m = p >= 0
+        vs.append(p[m])
+        gs.append(_group_key(step[m], lane[m], u[m], k, T, ilp))
+    groups = _groups_by_value(st.n1, (np.concatenate(vs), np.concatenate(gs)))
+    slot1, nslot1 = _allocate_banked(wave_of, last, st.consumed, [v for w in waves1 for v in w], groups, lag=lag)
+    return waves1, _p1_rows(st, slot1), int(nslot1)
+
+
+def _p2_banked(prog, width, lag, T, ilp, h_shared):
+    """Phase-2 form with bank-aware slots; with h_shared the accumulators
+    an instruction reads sit in the same shared memory ([H | slots])."""
+    st = _static(prog)
+    nh = st.nh
+    waves2, wave_of2, last2 = _p2_waves(prog, width, lag)
+    step, lane, u = _positions(waves2, T, ilp, st.shape2)
+    kind = st.const2[:, 0] & 3
+    w = np.arange(st.n2w, dtype=np.int64)
+    vs, gs, fixed = [], [], []
+    m = st.needs2
+    vs.append(w[m])
+    gs.append(_group_key(step[m], lane[m], u[m], 5, T, ilp))
+    reads = [(st.ops2[:, k], kind != 2, k) for k in range(4)] + [(st.dnode2, kind == 2, 4)]
+    for p, sel, k in reads:
+        mv = sel & (p >= nh)
+        vs.append(p[mv] - nh)
+        gs.append(_group_key(step[mv], lane[mv], u[mv], k, T, ilp))
+        if h_shared:
+            mh = sel & (p >= 0) & (p < nh)
+            fixed.append(np.stack([_group_key(step[mh], lane[mh], u[mh], k, T, ilp), (p[mh] - nh) % NBANK], 1))
+    groups = _groups_by_value(st.n2w, (np.concatenate(vs), np.concatenate(gs)))
+    fx = np.concatenate(fixed) if fixed else None
+    slot2, nslot2 = _allocate_banked(wave_of2, last2, st.needs2, [v for wv in waves2 for v in wv], groups,
+                                     fixed=fx, lag=lag)
+    return waves2, _p2_rows(st, slot2), int(nslot2)
+
+
+def _width_form(prog, width, lag=1):
+    """Both phases' forms for one wave width."""
+    return _p1_form(prog, width, lag) + _p2_form(prog, width, lag)
+
+
+def build(prog, T=128, ilp=ILP, wave_steps=1, lag=1, wave_steps2=None, banked=False, h_shared=True):
     """CoopProgram of a class program for teams of T lanes taking ilp nodes
     per step; a wave (the nodes between two team barriers) holds up to
-    wave_steps steps of mutually independent nodes.  lag 2: split barriers
+    wave_steps steps of mutually independent nodes in Phase 1 and
+    wave_steps2 (default: wave_steps) in Phase 2.  lag 2: split barriers
     (teams of 64 lanes or more), parents at least two waves back."""
     if lag == 2 and T < 64:
         raise ValueError("split barriers need teams of 64 lanes or more")
     st = _static(prog)
-    waves1, rows1, nslot1, waves2, rows2, nslot2 = _width_form(prog, ilp * T * wave_steps, lag)
+    k2 = wave_steps if wave_steps2 is None else wave_steps2
+    if banked:
+        # bank-aware slots for this team shape (the slot counts are the same)
+        waves1, rows1, nslot1 = _p1_banked(prog, ilp * T * wave_steps, lag, T, ilp)
+        waves2, rows2, nslot2 = _p2_banked(prog, ilp * T * k2, lag, T, ilp, h_shared)
+    else:
+        waves1, rows1, nslot1 = _p1_form(prog, ilp * T * wave_steps, lag)
+        waves2, rows2, nslot2 = _p2_form(prog, ilp * T * k2, lag)
     ph1, steps1 = _pack(waves1, rows1, T, NOP1, ilp, st.shape1)
     ph2, steps2 = _pack(waves2, rows2, T, NOP2, ilp, st.shape2)
     nh = st.nh
@@ -413,8 +618,66 @@ def build(prog, T=128, ilp=ILP, wave_steps=1, lag=1):
     eff1 = st.n1 / max(1, int(steps1.sum()) * T * ilp)
     eff2 = st.n2w / max(1, int(steps2.sum()) * T * ilp)
     assert ph1.shape[0] == (int(steps1.sum()) + PREFETCH_STEPS) * T * ilp
-    return CoopProgram(T, ilp, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(prog.p2.out_dims), eff1, eff2,
-                       lag)
+    cp = CoopProgram(T, ilp, ph1, steps1, ph2, steps2, nh, nslot, prog.L, tuple(prog.p2.out_dims), eff1, eff2,
+                     lag)
+    cp.wave_steps, cp.wave_steps2 = wave_steps, k2
+    return cp
+
+
+def _half_warp_wavefronts(ids, mask):
+    """Wavefronts of 64-bit shared accesses: ids, mask [..., 32 lanes] per
+    warp instruction; each half-warp costs the most distinct words it finds
+    in one of the 16 bank pairs (a repeated word is a broadcast)."""
+    x = np.where(mask, ids, -1).reshape(-1, 16)
+    x = x[(x >= 0).any(axis=1)]
+    if x.size == 0:
+        return 0, 0
+    x = np.sort(x, axis=1)
+    dup = np.zeros_like(x, dtype=bool)
+    dup[:, 1:] = x[:, 1:] == x[:, :-1]
+    ok = (x >= 0) & ~dup
+    r, c = np.nonzero(ok)
+    cnt = np.zeros((x.shape[0], NBANK), dtype=np.int64)
+    np.add.at(cnt, (r, x[r, c] % NBANK), 1)
+    return int(cnt.max(axis=1).sum()), int(x.shape[0])
+
+
+def shared_wavefronts(cp, h_shared=False):
+    """Modelled shared-memory wavefronts of a cooperative program's value-slot
+    accesses and the conflict-free count: (Phase-1 wavefronts, Phase-1
+    ideal, Phase-2 wavefronts, Phase-2 ideal); Phase 1 per primitive
+    quartet, Phase 2 per shell quartet.  Each operand position of a step's
+    node slot is one warp instruction (loads a..e and the result store in
+    Phase 1; the four operands, the stored value and the result in Phase
+    2); with h_shared the accumulators Phase 2 reads count as shared
+    operands at their own banks."""
+    W = cp.T * cp.ilp
+    warps = cp.T // 32
+
+    def slots(ph, steps):
+        n = int(np.sum(steps))
+        d = ph[: n * W].astype(np.int64).reshape(n, warps, 32, cp.ilp, 4)
+        return np.moveaxis(d, 3, 2)          # [step, warp, ilp, lane, word]
+
+    d = slots(cp.ph1, cp.steps1)
+    meta = d[..., 3] >> 16
+    term = (meta & 0xC000) == 0
+    t2 = term & (((meta >> 4) & 31) > 0)
+    t3 = term & (((meta >> 9) & 15) > 0)
+    dst = d[..., 0] & 0xFFFF
+    acc = [(d[..., 1] & 0xFFFF, term), (d[..., 1] >> 16, term), (d[..., 2] & 0xFFFF, t2), (d[..., 2] >> 16, t2),
+           (d[..., 3] & 0xFFFF, t3), (dst, ((meta & 0x8000) == 0) & (dst != 0xFFFF))]
+    w1 = [_half_warp_wavefronts(a, m) for a, m in acc]
+    d = slots(cp.ph2, cp.steps2)
+    nh = cp.nh
+    kind = d[..., 0] & 3
+    nt = (d[..., 0] >> 2) & 7
+    lo = 0 if h_shared else nh              # lowest operand id in shared memory
+    ops = [(d[..., 1] & 0xFFFF, (kind == 0) | (kind == 1)), (d[..., 1] >> 16, (kind == 0) | ((kind == 1) & (nt > 1))),
+           (d[..., 2] & 0xFFFF, (kind == 1) & (nt > 2)), (d[..., 2] >> 16, (kind == 1) & (nt > 3)),
+           (d[..., 0] >> 16, kind == 2), (d[..., 0] >> 16, (kind <= 1))]
+    w2 = [_half_warp_wavefronts(a, m & (a >= lo)) for a, m in ops]
+    return (sum(a for a, _ in w1), sum(b for _, b in w1), sum(a for a, _ in w2), sum(b for _, b in w2))
 
 
 def fp64_issue(cp):
@@ -524,6 +787,67 @@ def _wide_waves(prog, cp, rows):
     return cp
 
 
+PHASE2_STEPS = (8, 4, 2)  # candidate steps per Phase-2 wave
+PHASE2_SMEM_GROWTH = 12 * 1024  # shared memory per SM a wider Phase 2 may add
+
+
+def _runtime_layout(cp, rows):
+    """(resident warps, shared memory per SM) of a shape as the runtime lays
+    it out: teams of up to 128 lanes share 128-thread blocks, wider teams
+    fill a block; H goes in shared memory when that keeps as many warps;
+    at most 512 threads per SM (256 for four nodes per lane)."""
+    elem, reserve = 8, 1024
+    max_threads = 256 if cp.ilp == 4 else 512
+    best = (-1, 0)
+    for h_in in (1, 0):
+        tpb_max = max(1, 128 // cp.T)
+        tpb = tpb_max
+        while tpb >= 1:
+            per_team = rows * (ROW_BYTES // 8) + cp.nslot + (cp.nh if h_in else 0)
+            bsm = (per_team * tpb * elem + 15) // 16 * 16
+            if bsm <= 227 * 1024:
+                bps = min(max_threads // (tpb * cp.T), max(1, SMEM_PER_SM // (bsm + reserve)))
+                warps = bps * tpb * cp.T // 32
+                if bps >= 1 and warps > best[0]:
+                    best = (warps, bps * bsm)
+            tpb //= 2
+    return best
+
+
+def _wide_phase2(prog, cp, rows):
+    """Phase 2 runs once per shell quartet (the HRR and the transform), after
+    the contraction: with few primitive quartets per shell quartet it weighs
+    as much as Phase 1, and its barriers more (the (gg|gg) Phase-2 graph
+    spreads over 159 two-step waves).  Its live set is smaller than Phase
+    1's, so wider Phase-2 waves often cost no value slots at all ((gg|gg):
+    four-step waves need 18,586 slots against Phase 1's 22,760).  Take the
+    widest of 8, 4 and 2 steps per Phase-2 wave that keeps the teams per SM;
+    Phase 1 keeps its form.  A wider Phase 2 must keep the warps the
+    runtime makes resident and add at most PHASE2_SMEM_GROWTH of shared
+    memory per SM: the rest of the SM's 256 KB is L1, which holds the
+    descriptor stream.  Measured with eight-step Phase-2 waves wherever the
+    generator's team count held: (ff|ff) grew from 4,965 to 6,766 slots,
+    which cut the runtime's warps per SM from 16 to 12 and cost 5% at K = 3
+    and 6; (gg|gg) grew 24 KB per SM at 16 warps and lost 1% at K = 6 (8%
+    gained at K = 1); (dd|dd) grew 10 KB at 16 warps and gained 18% at
+    K = 1 and 2% at K = 3 and 6."""
+    if cp is None:
+        return cp
+    k1 = getattr(cp, "wave_steps", 1)
+    k0 = getattr(cp, "wave_steps2", k1)
+    warps0, smem0 = _runtime_layout(cp, rows)
+    for k in PHASE2_STEPS:
+        if k <= k0:
+            break
+        ck = build(prog, cp.T, cp.ilp, k1, cp.lag, wave_steps2=k)
+        if _score(ck, rows) is None:
+            continue
+        warps, smem = _runtime_layout(ck, rows)
+        if warps >= warps0 and smem <= smem0 + PHASE2_SMEM_GROWTH:
+            return ck
+    return cp
+
+
 # split barriers cost no drain at a wave's end but put a node's parents at
 # least two waves back, which can stretch a narrow graph: they are taken when
 # the steps they need stay within this factor of the full-barrier form's
@@ -545,14 +869,38 @@ def _split_barriers(prog, cp, rows):
     return ck if steps(ck) <= SPLIT_STEP_RATIO * steps(cp) else None
 
 
-def choose_both(prog, shapes=SHAPES, split=None):
+BANKED = True  # bank-aware value slots in the shipped programs
+
+
+def _banked(prog, cp, rows):
+    """The same shape with bank-aware slots (same slot count).  Phase 2
+    counts the accumulators it reads as shared-memory operands when H fits
+    in shared memory beside the slots (the runtime's preference)."""
+    if cp is None or not BANKED:
+        return cp
+    h_shared = cp.nslot * 8 + rows * ROW_BYTES + cp.nh * 8 <= 227 * 1024
+    k1 = getattr(cp, "wave_steps", 1)
+    return build(prog, cp.T, cp.ilp, k1, cp.lag, wave_steps2=getattr(cp, "wave_steps2", k1), banked=True,
+                 h_shared=h_shared)
+
+
+def shape_key(cp):
+    """What tells two cooperative programs of one class apart: team size,
+    nodes per lane, steps per Phase-1 and per Phase-2 wave."""
+    k1 = getattr(cp, "wave_steps", 1)
+    return (cp.T, cp.ilp, k1, getattr(cp, "wave_steps2", k1))
+
+
+def choose_both(prog, shapes=SHAPES, split=None, wide2=True, alts=0):
     """(deep, shallow): the best (team size, nodes per lane) shape when a
     team holds DEEP_ROWS coefficient rows, and when it holds SHALLOW_ROWS
     (shallow contractions: fewer rows leave shared memory for more teams).
     Classes whose 128-lane team is alone on an SM also try one 256-lane team
     (eight warps on the same shared-memory live set), and those whose
     256-lane team is alone even with H in global memory one 512-lane team
-    (sixteen warps)."""
+    (sixteen warps).  With alts > 0 also a list of up to `alts` other
+    shapes, the next best by score with their wave depths chosen the same
+    way: candidates an autotuner can time against the static choice."""
     built = [build(prog, T, ilp) for T, ilp in shapes]
     if any(cp.T == 128 and _teams_per_sm(cp, DEEP_ROWS) <= 1 for cp in built):
         built += [build(prog, T, ilp) for T, ilp in WIDE_SHAPES]
@@ -571,7 +919,29 @@ def choose_both(prog, shapes=SHAPES, split=None):
         cp = _wide_waves(prog, built[max(scored)[1]], rows) if scored else None
         if SPLIT_BARRIERS if split is None else split:
             cp = _split_barriers(prog, cp, rows) or cp
+        elif wide2:
+            cp = _wide_phase2(prog, cp, rows)
         out.append(cp)
+    if alts > 0:
+        taken = {shape_key(cp) for cp in out if cp is not None}
+        scored = sorted(((sc, k) for k, cp in enumerate(built) for sc in [_score(cp, DEEP_ROWS)] if sc is not None),
+                        reverse=True)
+        extra = []
+        for _, k in scored:
+            if len(extra) >= alts:
+                break
+            cp = _wide_waves(prog, built[k], DEEP_ROWS)
+            if wide2:
+                cp = _wide_phase2(prog, cp, DEEP_ROWS)
+            if shape_key(cp) not in taken:
+                taken.add(shape_key(cp))
+                extra.append(cp)
+        out.append(extra)
+    out[0] = _banked(prog, out[0], DEEP_ROWS)
+    out[1] = (out[0] if out[1] is not None and out[0] is not None and shape_key(out[1]) == shape_key(out[0])
+              else _banked(prog, out[1], SHALLOW_ROWS))
+    if alts > 0:
+        out[2] = [_banked(prog, cp, DEEP_ROWS) for cp in out[2]]
     release(prog)
     return tuple(out)
 

@@ -155,6 +155,24 @@ def test_coop_multistep_waves_match_oracle(ls, T, ilp, k):
     assert within(got, ref.reshape(q.shape[0], -1)).all()
 
 
+@pytest.mark.parametrize("T,ilp,k2", [(32, 2, 8), (64, 2, 2), (128, 2, 4)])
+@pytest.mark.parametrize("ls", [(2, 2, 1, 1), (3, 2, 2, 1)])
+def test_coop_wider_phase2_waves_match_oracle(ls, T, ilp, k2):
+    """Phase-2 waves of several steps over one-step Phase-1 waves (the two
+    phases are scheduled and allocated apart; Phase 2 reads H and its own
+    slots) reproduce the oracle, and the verifier accepts the program."""
+    from paper_2605_10312_gb300.gen import verify
+    prog = program.make(*ls)
+    cp = coop.build(prog, T, ilp, 1, wave_steps2=k2)
+    assert int(cp.steps1.max()) == 1 and int(cp.steps2.max()) > 1
+    assert len(cp.steps2) < len(coop.build(prog, T, ilp, 1).steps2)
+    assert verify.verify_coop(cp, prog.L, len(encode.coef_table())) == []
+    basis, q = synth.class_sweep(ls, 3, kset=(1, 2), seed=23, box_angstrom=3.0, exp_range=(0.1, 30))
+    ref, _ = blocks(basis, q)
+    got = run_coop(cp, prog, basis, q)
+    assert within(got, ref.reshape(q.shape[0], -1)).all()
+
+
 @pytest.mark.parametrize("ls", [(2, 2, 1, 1), (3, 1, 2, 0)])
 def test_coop_512_lane_program_matches_oracle(ls):
     """The widest team (512 lanes, two nodes per lane, waves of up to two
@@ -185,7 +203,7 @@ def test_widest_team_only_where_a_256_lane_team_is_alone(monkeypatch):
     fit, the wider team would only lose lane efficiency."""
     built = []
 
-    def fake_build(prog, T, ilp, k=1, lag=1):
+    def fake_build(prog, T, ilp, k=1, lag=1, wave_steps2=None, **kw):
         built.append((T, ilp, k))
         width = T * ilp * k
         nslot = prog.slots + width
@@ -319,6 +337,8 @@ def test_gggg_production_program_matches_oracle():
     prog = program.make(4, 4, 4, 4)
     deep, _ = coop.choose_both(prog)
     assert (deep.T, deep.ilp, deep.lag) == coop.WIDEST_SHAPE + (1,) and int(deep.steps1.max()) == 2
+    # Phase 2 in waves of up to four steps (its live set fits Phase 1's slots)
+    assert int(deep.steps2.max()) == 4
     assert verify.verify_coop(deep, prog.L, len(encode.coef_table())) == []
     basis, q = synth.class_sweep((4, 4, 4, 4), 2, kset=(1, 2), seed=24, box_angstrom=0.5, exp_range=(0.3, 3.0))
     ref, _ = blocks(basis, q)
@@ -399,3 +419,39 @@ def test_verifier_catches_adjacent_wave_hazards():
             c.ph1[i, 0] = (c.ph1[i, 0] & 0xFFFF0000) | src
             break
     assert any("reads a slot it writes" in m for m in verify.verify_coop(c, prog.L, ncoef))
+
+
+def test_half_warp_wavefront_model():
+    """64-bit shared accesses: a half-warp of 16 lanes reading 16 words in
+    16 distinct bank pairs takes one wavefront; 16 words in one bank pair
+    take 16; one repeated word is a broadcast; masked lanes take none."""
+    ids = np.arange(32).reshape(1, 32)
+    on = np.ones_like(ids, dtype=bool)
+    assert coop._half_warp_wavefronts(ids, on) == (2, 2)
+    assert coop._half_warp_wavefronts(ids * 16, on) == (32, 2)
+    assert coop._half_warp_wavefronts(np.zeros_like(ids), on) == (2, 2)
+    half = on.copy()
+    half[0, 16:] = False
+    assert coop._half_warp_wavefronts(ids * 16, half) == (16, 1)
+    assert coop._half_warp_wavefronts(ids, np.zeros_like(on)) == (0, 0)
+
+
+@pytest.mark.parametrize("ls,T,ilp,k1,k2", [((2, 2, 2, 2), 64, 2, 1, 2), ((3, 3, 2, 2), 128, 2, 1, 4),
+                                          ((3, 2, 2, 1), 32, 2, 1, 4)])
+def test_bank_aware_slots(ls, T, ilp, k1, k2):
+    """Bank-aware slot choice keeps the slot count, lowers the modelled
+    shared-memory wavefronts of both phases, passes the bounds and hazard
+    verifier, and the program still reproduces the oracle."""
+    from paper_2605_10312_gb300.gen import verify
+    prog = program.make(*ls)
+    plain = coop.build(prog, T, ilp, k1, wave_steps2=k2)
+    banked = coop.build(prog, T, ilp, k1, wave_steps2=k2, banked=True, h_shared=True)
+    assert banked.nslot == plain.nslot
+    a, b = coop.shared_wavefronts(plain, True), coop.shared_wavefronts(banked, True)
+    assert b[1] == a[1] and b[3] == a[3]          # same instructions
+    assert b[0] < a[0] and b[2] < a[2]
+    assert verify.verify_coop(banked, prog.L, len(encode.coef_table())) == []
+    basis, q = synth.class_sweep(ls, 3, kset=(1, 2), seed=29, box_angstrom=3.0, exp_range=(0.1, 30))
+    ref, _ = blocks(basis, q)
+    got = run_coop(banked, prog, basis, q)
+    assert within(got, ref.reshape(q.shape[0], -1)).all()
