@@ -160,6 +160,21 @@ def oracle_rates(parts, budget_s=15.0, nthreads=None, sizes=None):
     return rates, out_sizes, nthreads
 
 
+def tuned_summary(tuned):
+    """The autotuner's choices per class: tier, and per kind of contraction
+    the cooperative shape (T x nodes per lane, steps per wave of each phase)
+    and vote form."""
+    if tuned is None:
+        return None
+    out = {}
+    for c, v in tuned.items():
+        e = {"tier": v["tier"]}
+        for kind, sh in (v.get("shapes") or {}).items():
+            e[kind] = "T{}x{} w{}/{} votes {}".format(sh["T"], sh["ilp"], sh["k1"], sh["k2"], sh["votes"])
+        out["".join(map(str, c))] = e
+    return out
+
+
 def cpu_model():
     """The host CPU as /proc/cpuinfo names it (model name, else the Arm
     implementer and part codes), else the machine type."""
@@ -266,6 +281,14 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     parts = workload(rank)
+    tuned = None
+    if args.autotune:
+        # tier, cooperative shape and vote form per class and kind of
+        # contraction, timed on a sample of each class's quartets
+        from paper_2605_10312_gb300 import tune
+        tuned = {}
+        for ls, basis, q in parts:
+            tuned.update(tune.autotune(basis, q, sample=args.tune_sample, shapes=True))
     plans, outs = [], []
     for ls, basis, q in parts:
         p = eri.Plan(basis, q, votes=args.votes, persistent=args.persistent)
@@ -327,7 +350,8 @@ def run_ours(args):
             "fp64_tflops": fl / (sum(ms) * 1e-3) / 1e12, "fp64_frac_of_peak": fl / (sum(ms) * 1e-3) / 1e12 / peak,
             "tier": [eri.TIERS_INV.get(r["tier"], r["tier"]) for r in p.launches()[1:]]}
     nlaunch = sum(len(p.launches()) for _, p in plans)
-    traffic = _traffic_for(dom_rec)
+    measured = _traffic_for(dom_rec)
+    traffic, executed = measured if measured else (None, None)
 
     # end to end through the public API with host buffers
     e2e_ms, h2d, d2h = [], 0, 0
@@ -381,6 +405,9 @@ def run_ours(args):
         "per_class": per_class,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     # executed FP64 flops (ncu) over the algorithmic count on
+                     # the dominant launch type; null when its counters are stale
+                     "fp64_executed_over_algorithmic": executed,
                      "kernel": "{} tier {} ({} quartets)".format(
                          "".join("spdfg"[x] for x in dom_rec["cls"]) if dom_rec["cls"][0] >= 0 else "pair set-up",
                          eri.TIERS_INV.get(dom_rec["tier"], dom_rec["tier"]), dom_rec["quartets"]),
@@ -391,6 +418,7 @@ def run_ours(args):
         "latency": latency,
         "gpu_launches": nlaunch * args.steps,
         "clocks": clk,
+        "autotuned": tuned_summary(tuned),
     }
     print(json.dumps(line))
     if world > 1:
@@ -442,10 +470,12 @@ def _traffic_for(rec):
         return None
     h = hashlib.sha256()
     for f in ent.get("source_files", []):
-        h.update(open(os.path.join(ROOT, "paper_2605_10312_gb300", "csrc", f), "rb").read())
+        # paths relative to the package (bare names: its csrc folder)
+        rel = f if "/" in f else os.path.join("csrc", f)
+        h.update(open(os.path.join(ROOT, "paper_2605_10312_gb300", rel), "rb").read())
     if ent.get("source_sha256") != h.hexdigest():
         return None
-    return ent["bytes_per_quartet"] * rec["quartets"]
+    return ent["bytes_per_quartet"] * rec["quartets"], ent.get("fp64_executed_over_algorithmic")
 
 
 # ---------------------------------------------------------------------------
@@ -524,16 +554,24 @@ def run_water(args):
     basis = synth.water_cluster(args.waters, seed=3, layout=args.layout)
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
-        pairs, qb = screen.pair_bounds(basis, stream=stream)
+        pairs, qd = screen.pair_bounds_device(basis, stream=stream)
         torch.cuda.synchronize()
         t_bounds = time.perf_counter() - t0
-        quartets = synth.screened_quartets(qb, pairs, args.threshold)
+        # the survivor list built on the device (count, prefix sum,
+        # compaction), then copied to the host for the planner
+        dp = torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.int32)).cuda()
+        t1 = time.perf_counter()
+        dq = eri.screen_quartets(qd.contiguous(), dp, args.threshold, stream)
+        torch.cuda.synchronize()
+        t_screen_dev = time.perf_counter() - t1
+        quartets = dq.cpu().numpy()
         t_screen = time.perf_counter() - t0
+        qb = qd.cpu().numpy()
         npairs = pairs.shape[0]
         total = npairs * (npairs + 1) // 2
         tuned = None
         if args.autotune:
-            tuned = tune.autotune(basis, quartets, sample=1024)
+            tuned = tune.autotune(basis, quartets, sample=args.tune_sample, shapes=True)
         t1 = time.perf_counter()
         plan = eri.Plan(basis, quartets, digest=args.jk, persistent=args.persistent)
         t_plan = time.perf_counter() - t1
@@ -566,13 +604,14 @@ def run_water(args):
                 args.waters, 3 * args.waters, args.layout, args.threshold),
             "nshell": int(basis.nshell), "pairs": int(npairs), "quartets_total": int(total),
             "quartets_survived": int(quartets.shape[0]), "survived_frac": quartets.shape[0] / total,
-            "bounds_s": t_bounds, "screen_s": t_screen, "plan_s": t_plan, "ms_per_step": ms,
+            "bounds_s": t_bounds, "screen_s": t_screen, "screen_device_s": t_screen_dev, "plan_s": t_plan,
+            "ms_per_step": ms,
             "output_gb": plan.output_count * 8 / 1e9,
             "value": quartets.shape[0] / (ms * 1e-3), "unit": "quartets/s",
             "fp64_tflops": st["flops"] / (ms * 1e-3) / 1e12,
             "fp64_frac_of_peak": st["flops"] / (ms * 1e-3) / 1e12 / fp64_peak_tflops(),
             "launches_per_step": st["launches"] + 1, "graph": True, "persistent": bool(args.persistent), "jk": jk,
-            "autotuned": None if tuned is None else {"".join(map(str, c)): v["tier"] for c, v in tuned.items()},
+            "autotuned": tuned_summary(tuned),
             "per_class": {k: {"parts": v["quartet_parts"], "ms": v["ms"], "tier": v["tier"],
                               "fp64_frac": v["flops"] / max(1e-9, v["ms"] * 1e-3) / 1e12 / fp64_peak_tflops()}
                           for k, v in sorted(per_class.items(), key=lambda kv: -kv[1]["ms"])}}
@@ -838,7 +877,9 @@ def main():
     ap.add_argument("--waters", type=int, default=20)
     ap.add_argument("--layout", default="dz", choices=["dz", "tz"])
     ap.add_argument("--threshold", type=float, default=1e-10)
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune tiers, cooperative shapes and vote forms on a sample before planning")
+    ap.add_argument("--tune-sample", type=int, default=1024, help="quartets per class group the autotuner times")
     ap.add_argument("--votes", default="auto", choices=["auto", "off", "on"],
                     help="team-cooperative programs: warp votes around optional FP64 terms")
     ap.add_argument("--persistent", action="store_true",

@@ -272,6 +272,24 @@ int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* stream);
  * Asynchronous on stream.  ERI_EINVAL for other plans. */
 int eri_schwarz(const eri_plan_t* plan, const double* blocks, double* bounds, void* stream);
 
+/* Schwarz screening of the unique quartet list on the device (the batched
+ * workload's survivor list).  |(ab|cd)| <= Q_ab Q_cd (Cauchy-Schwarz for the
+ * ERI inner product of Eq. 1) with the pair factors Q_ab = sqrt(max|(ab|ab)|)
+ * of eri_schwarz.  Q: device [npair] factors; pairs: device [npair][2] shell
+ * indices of each pair (8-byte aligned).  The unique quartets are the
+ * unordered pairs {P, R} of pairs, P = R included; with lo the pair of the
+ * smaller factor (the larger index among equal factors) and hi the other,
+ * a quartet survives iff Q_hi >= threshold / Q_lo (Q_lo = 0: iff
+ * threshold <= 0).  out: device [max_out][4] int32, 16-byte aligned, or
+ * NULL to count only; survivors are written as (P.a, P.b, R.a, R.b), P the
+ * larger pair index, ordered by P then R.  *count (host) receives the
+ * number of survivors.  Counts on the device (a prefix sum), reads the total
+ * back (the stream is synchronised), then writes; temporary device memory
+ * is taken stream-ordered and released.  ERI_EINVAL if out is not NULL and
+ * max_out < *count (nothing is written). */
+int eri_screen_quartets(const double* Q, const int32_t* pairs, int64_t npair, double threshold, int32_t* out,
+                        int64_t max_out, int64_t* count, void* stream);
+
 /* Preferred tier for a class (la lb | lc ld) when a plan asks for tier 0:
  * written by the autotuner (paper_2605_10312_gb300.tune); 0 clears the
  * entry.  A preference a class cannot honour falls back to the static rule.

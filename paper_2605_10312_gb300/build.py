@@ -284,6 +284,7 @@ def build(force=False, jobs=None, log=print):
         open(stamp, "w").write(gen_key)
     units = [os.path.join(CSRC, "eri_runtime.cu"), os.path.join(CSRC, "eri_exec.cu"),
              os.path.join(CSRC, "eri_coop.cu"), os.path.join(CSRC, "eri_digest.cu"),
+             os.path.join(CSRC, "eri_screen.cu"),
              os.path.join(GEN_DIR, "eri_registry.cu")]
     units += sorted(os.path.join(GEN_DIR, f) for f in os.listdir(GEN_DIR)
                     if f.endswith("_reg.cu") or f.endswith("_reg_f32.cu"))

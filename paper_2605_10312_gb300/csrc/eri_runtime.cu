@@ -1256,7 +1256,22 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
         g.grid = L.nsm;
         const size_t elem = prec ? sizeof(float) : sizeof(double);
         for (const Bucket* b : bs) {
+          // the persistent kernel runs two nodes per lane (512 threads per
+          // SM leave 128 registers a thread); a bucket whose shape takes
+          // four falls back to the class's first shipped two-node shape
           const CoopProg* cp = b->coop;
+          if (cp->ilp != 2) {
+            const CoopProg* alt = nullptr;
+            for (const CoopProg* c : class_shapes(L, {b->ls[0], b->ls[1], b->ls[2], b->ls[3], opts.axis_rule,
+                                                      opts.schedule, opts.sph_mode}))
+              if (c->ilp == 2 && c->T <= 512) {
+                alt = c;
+                break;
+              }
+            if (!alt) return fail(ERI_EUNSUPPORTED, "no two-node cooperative shape for the persistent launch");
+            if ((rc = upload_coop(const_cast<CoopProg*>(alt)))) return rc;
+            cp = alt;
+          }
           auto pit = prog_id.find(cp);
           if (pit == prog_id.end()) {
             EriCoopProgDesc d;
@@ -1443,6 +1458,24 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       (sm ? small : large).push_back(q);
       if (fuse && nparts_q[q] == 0) (sm ? rsmall : rlarge).push_back(q);
     }
+    // One thread digests one small quartet.  Neighbouring quartets of a
+    // screened list share shells, so a warp of neighbours would send its 32
+    // reductions to the same J and K entries at once; the list is dealt out
+    // so that the 32 lanes of a warp take quartets n / 32 apart (lane i of
+    // warp w: quartet i * ceil(n / 32) + w), each lane still walking its
+    // stretch of the list in order from warp to warp.
+    auto deal = [](std::vector<int64_t>& v) {
+      const size_t n = v.size(), s = (n + 31) / 32;
+      if (n < 64) return;
+      std::vector<int64_t> o;
+      o.reserve(n);
+      for (size_t w = 0; w < s; ++w)
+        for (size_t i = 0; i < 32; ++i)
+          if (i * s + w < n) o.push_back(v[i * s + w]);
+      v.swap(o);
+    };
+    deal(small);
+    deal(rsmall);
     if ((rc = plan->d_uq.upload(uq, "quartet list")) || (rc = plan->d_shell_bf.upload(bf, "shell offsets")) ||
         (rc = plan->d_small.upload(small, "digest list")) || (rc = plan->d_large.upload(large, "digest list")) ||
         (rc = plan->d_rsmall.upload(rsmall, "digest list")) || (rc = plan->d_rlarge.upload(rlarge, "digest list")))
@@ -2095,6 +2128,46 @@ extern "C" int eri_schwarz(const eri_plan_t* plan, const double* blocks, double*
       blocks, plan->d_offsets.p, plan->d_nab.p, nq, bounds);
   CUDA_OR(cudaGetLastError(), "schwarz launch");
   return ERI_OK;
+}
+
+extern "C" cudaError_t eri_screen_count_launch(const double* Q, int64_t npair, double t, int64_t* cnt, int64_t* off,
+                                               cudaStream_t stream);
+extern "C" cudaError_t eri_screen_write_launch(const double* Q, const int32_t* pairs, int64_t npair, double t,
+                                               const int64_t* off, int32_t* out, cudaStream_t stream);
+
+extern "C" int eri_screen_quartets(const double* Q, const int32_t* pairs, int64_t npair, double threshold,
+                                   int32_t* out, int64_t max_out, int64_t* count, void* stream_) {
+  if (!count || npair < 0 || (npair > 0 && (!Q || !pairs)) || std::isnan(threshold))
+    return fail(ERI_EINVAL, "bad argument");
+  *count = 0;
+  if (npair == 0) return ERI_OK;
+  if (((uintptr_t)Q & 7) || ((uintptr_t)pairs & 7) || (out && ((uintptr_t)out & 15)))
+    return fail(ERI_EINVAL, "Q and pairs must be 8-byte aligned, out 16-byte aligned");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  int64_t* tmp = nullptr;  // counts [npair], offsets [npair + 1]
+  CUDA_OR(cudaMallocAsync((void**)&tmp, (size_t)(2 * npair + 1) * sizeof(int64_t), stream), "screening scratch");
+  int64_t total = 0;
+  cudaError_t e = eri_screen_count_launch(Q, npair, threshold, tmp, tmp + npair, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&total, tmp + 2 * npair, sizeof(int64_t), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  int rc = ERI_OK;
+  if (e != cudaSuccess) {
+    rc = fail(ERI_ECUDA, std::string("screening: ") + cudaGetErrorString(e));
+  } else {
+    *count = total;
+    if (out) {
+      if (total > max_out) {
+        rc = fail(ERI_EINVAL, "out holds " + std::to_string(max_out) + " quartets, " + std::to_string(total) +
+                                  " survive");
+      } else {
+        e = eri_screen_write_launch(Q, pairs, npair, threshold, tmp + npair, out, stream);
+        if (e != cudaSuccess) rc = fail(ERI_ECUDA, std::string("screening write: ") + cudaGetErrorString(e));
+      }
+    }
+  }
+  cudaFreeAsync(tmp, stream);
+  return rc;
 }
 
 namespace {

@@ -113,6 +113,10 @@ def library(path: str = LIB):
         lib.eri_plan_graph_capture.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.eri_plan_graph_launch.restype = ctypes.c_int
         lib.eri_plan_graph_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_screen_quartets.restype = ctypes.c_int
+        lib.eri_screen_quartets.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                            ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.c_void_p]
         lib.eri_class_shapes.restype = ctypes.c_int
         lib.eri_class_shapes.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p, ctypes.c_int]
         lib.eri_set_class_shape.restype = ctypes.c_int
@@ -374,6 +378,28 @@ def boys(T, L, form="coop", stream=None):
     _check(library().eri_boys_eval(T.data_ptr(), T.numel(), int(L), BOYS_FORMS[form], F.data_ptr(),
                                    _stream_handle(stream)))
     return F
+
+
+def screen_quartets(Q, pairs, threshold, stream=None):
+    """Device Schwarz screening (eri_screen_quartets): Q a CUDA float64
+    tensor [npair] of pair factors, pairs a CUDA int32 tensor [npair, 2];
+    returns the surviving unique quartets as a CUDA int32 tensor [n, 4]."""
+    import torch
+    for t, dt in ((Q, torch.float64), (pairs, torch.int32)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError("Q must be a contiguous CUDA float64 tensor, pairs a contiguous CUDA int32 tensor")
+    npair = Q.numel()
+    if pairs.numel() != 2 * npair:
+        raise ValueError("pairs must be [npair, 2]")
+    lib = library()
+    n = ctypes.c_int64()
+    h = _stream_handle(stream)
+    _check(lib.eri_screen_quartets(Q.data_ptr(), pairs.data_ptr(), npair, float(threshold), None, 0,
+                                   ctypes.byref(n), h))
+    out = torch.empty((max(1, n.value), 4), dtype=torch.int32, device=Q.device)
+    _check(lib.eri_screen_quartets(Q.data_ptr(), pairs.data_ptr(), npair, float(threshold), out.data_ptr(),
+                                   n.value, ctypes.byref(n), h))
+    return out[: n.value]
 
 
 KINDS = {"deep": 0, "shallow": 1, "single": 2}

@@ -12,8 +12,9 @@ import numpy as np
 from . import eri, synth
 
 
-def pair_bounds(basis, pairs=None, stream=None):
-    """(pairs [npair, 2], Q [npair]) for every unique shell pair (a >= b)."""
+def pair_bounds_device(basis, pairs=None, stream=None):
+    """(pairs [npair, 2] host int32, Q [npair] CUDA float64 tensor) for every
+    unique shell pair (a >= b); Q stays on the device."""
     import torch
     if pairs is None:
         pairs = synth.shell_pairs(basis.nshell)
@@ -23,15 +24,31 @@ def pair_bounds(basis, pairs=None, stream=None):
     bounds = torch.empty(max(1, diag.shape[0]), dtype=torch.float64, device="cuda")
     p.compute(blocks, stream)
     p.schwarz(blocks, bounds, stream)
-    q = bounds[: diag.shape[0]].cpu().numpy()
     p.close()
-    return pairs, q
+    return pairs, bounds[: diag.shape[0]]
+
+
+def pair_bounds(basis, pairs=None, stream=None):
+    """(pairs [npair, 2], Q [npair]) for every unique shell pair (a >= b)."""
+    pairs, q = pair_bounds_device(basis, pairs, stream)
+    return pairs, q.cpu().numpy()
 
 
 def screened(basis, threshold=1e-10, stream=None):
-    """Unique quartets of the basis surviving Schwarz screening, [n, 4]."""
+    """Unique quartets of the basis surviving Schwarz screening, [n, 4]
+    (host enumeration of the device bounds)."""
     pairs, q = pair_bounds(basis, stream=stream)
     return synth.screened_quartets(q, pairs, threshold)
+
+
+def screened_device(basis, threshold=1e-10, stream=None):
+    """The same survivors listed on the device (eri_screen_quartets: a
+    counting pass, a prefix sum and a compaction over the device bounds);
+    a CUDA int32 tensor [n, 4], the pair of the larger index first."""
+    import torch
+    pairs, q = pair_bounds_device(basis, stream=stream)
+    dp = torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.int32)).to(q.device)
+    return eri.screen_quartets(q.contiguous(), dp, threshold, stream)
 
 
 def quartet_bounds(pair_q, quartets):

@@ -297,15 +297,31 @@ def shell_pairs(nshell: int) -> np.ndarray:
     return np.stack([a, b], axis=1).astype(np.int32)
 
 
+def survives(q_p, q_r, p, r, threshold):
+    """The screening rule, elementwise: for pairs p, r with factors q_p, q_r,
+    lo is the one with the smaller factor (the larger index among equal
+    factors) and hi the other; the quartet survives iff
+    q_hi >= threshold / q_lo (q_lo = 0: iff threshold <= 0).  Phrased with
+    the division so that the sorted-prefix enumeration below, the count and
+    a device kernel all pick the same set."""
+    q_p, q_r = np.asarray(q_p, dtype=np.float64), np.asarray(q_r, dtype=np.float64)
+    p_lo = (q_p < q_r) | ((q_p == q_r) & (np.asarray(p) > np.asarray(r)))
+    lo, hi = np.where(p_lo, q_p, q_r), np.where(p_lo, q_r, q_p)
+    with np.errstate(divide="ignore"):
+        return np.where(lo > 0, hi >= threshold / np.where(lo > 0, lo, 1.0), threshold <= 0)
+
+
 def screened_quartets(pair_bound: np.ndarray, pairs: np.ndarray, threshold: float) -> np.ndarray:
-    """Unique quartets (pair P >= pair Q) whose Schwarz bound
-    Q_P Q_Q >= threshold, given per-pair bounds; [n, 4] int32.  Pure
+    """Unique quartets (unordered pairs of pairs, a pair with itself
+    included) that pass the screening rule (survives) on the per-pair
+    Schwarz bounds; [n, 4] int32, the pair of the smaller bound first.  Pure
     bookkeeping on bounds computed elsewhere."""
     order = np.argsort(-pair_bound, kind="stable")
     qb = pair_bound[order]
     out = []
     for i in range(order.size):
-        if qb[i] * qb[0] < threshold:
+        # nothing from here on has a partner (bounds only fall)
+        if (qb[i] > 0 and qb[0] < threshold / qb[i]) or (qb[i] <= 0 and threshold > 0):
             break
         # partners j <= i in the sorted order with qb[i] qb[j] >= threshold:
         # a prefix, since qb is sorted descending
@@ -356,7 +372,7 @@ def sample_screened_quartets(pair_bound: np.ndarray, pairs: np.ndarray, threshol
         i -= (i * (i + 1) // 2 > t)
         i += ((i + 1) * (i + 2) // 2 <= t)
         j = t - i * (i + 1) // 2
-        t = t[pair_bound[i] * pair_bound[j] >= threshold]
+        t = t[survives(pair_bound[i], pair_bound[j], i, j, threshold)]
         got = np.unique(np.concatenate([got, t]))
     t = rng.permutation(got)[:n]
     i = ((np.sqrt(8.0 * t + 1.0) - 1.0) // 2).astype(np.int64)

@@ -1,10 +1,17 @@
-"""Autotuner: per-class tier choice from timed trials.
+"""Autotuner: per-class tier choice, and per-(class, kind of contraction)
+cooperative shape and vote form, from timed trials.
 
 For every class a workload touches, the quartets of that class group are run
 on each feasible tier (compiled register, team-cooperative, shared-memory or
 global-scratch program) with launch timing on, and the fastest per quartet
 becomes the class's preferred tier in the runtime (eri_set_class_tier).
-Results can be saved and reloaded as JSON keyed by class.
+For the classes that then run on the team-cooperative tier, every shape the
+build ships (eri_class_shapes: team size, nodes per lane, steps per wave of
+each phase) is timed with the optional FP64 terms predicated and behind warp
+votes, separately for deep, shallow and single-primitive parts (the launch
+records say which), and the fastest per kind is installed
+(eri_set_class_shape).  Results can be saved and reloaded as JSON keyed by
+class.
 """
 from __future__ import annotations
 
@@ -24,47 +31,88 @@ def _group_key(basis, q):
     return a + b if a >= b else b + a
 
 
-def autotune(basis, quartets, sample=2048, reps=2, tiers=TIERS, apply=True, seed=0):
-    """Time each tier on up to `sample` quartets of every class group; returns
-    {class: {"tier": best, "us_per_quartet": {tier: t}}} and, with apply,
-    installs the choices in the runtime."""
-    import torch
+def _samples(basis, quartets, sample, seed):
     q = np.asarray(quartets, dtype=np.int32).reshape(-1, 4)
     keys = [_group_key(basis, x) for x in q]
     groups = {}
     for i, k in enumerate(keys):
         groups.setdefault(k, []).append(i)
     rng = np.random.default_rng(seed)
-    stream = torch.cuda.current_stream()
-    per_cls = {}
+    out = {}
     for k, idx in groups.items():
         idx = np.array(idx)
         if idx.size > sample:
             idx = rng.choice(idx, sample, replace=False)
-        sub = q[idx]
+        out[k] = q[idx]
+    return out
+
+
+FILL_MS = 10.0    # a trial's launches run at least this long (the sample is repeated)
+FILL_MAX = 1024   # at most this many copies of a sample
+
+
+def _filled(basis, sub, stream):
+    """The sample repeated until the default plan's launches take about
+    FILL_MS: a few hundred quartets leave most SMs idle, and per-quartet
+    times of launches that small measure launch overhead and the tail of
+    the last wave of teams, not throughput."""
+    import torch
+    p = eri.Plan(basis, sub)
+    out = torch.empty(max(1, p.output_count), dtype=torch.float64, device="cuda")
+    p.set_timing(True)
+    p.compute(out, stream)
+    p.compute(out, stream)
+    stream.synchronize()
+    ms = sum(max(0.0, r["ms"]) for r in p.launches())
+    p.close()
+    rep = int(min(FILL_MAX, max(1, np.ceil(FILL_MS / max(ms, 1e-3)))))
+    return np.ascontiguousarray(np.tile(sub, (rep, 1))) if rep > 1 else sub
+
+
+def _timed(plan, out, stream, reps, by_kind=True):
+    """{(class, tier, kind): microseconds per quartet part} -- the time of all
+    of a key's launches in one run (a class has one launch per part round
+    and contraction group) over their parts, the best of reps runs after a
+    warm-up (launch timing on).  by_kind False: kind None, all of a class's
+    launches on one tier together."""
+    plan.set_timing(True)
+    plan.compute(out, stream)  # warm-up (program upload, caches)
+    best = {}
+    for _ in range(reps):
+        plan.compute(out, stream)
+        stream.synchronize()
+        tot = {}
+        for rec in plan.launches()[1:]:
+            key = (rec["cls"], rec["tier"], rec.get("kind") if by_kind else None)
+            ms, n = tot.get(key, (0.0, 0))
+            tot[key] = (ms + rec["ms"], n + rec["quartets"])
+        for key, (ms, n) in tot.items():
+            best[key] = min(best.get(key, float("inf")), ms * 1e3 / max(1, n))
+    return best
+
+
+def autotune(basis, quartets, sample=2048, reps=2, tiers=TIERS, apply=True, seed=0, shapes=False):
+    """Time each tier on up to `sample` quartets of every class group; returns
+    {class: {"tier": best, "us_per_quartet": {tier: t}}} and, with apply,
+    installs the choices in the runtime.  shapes: then tune the cooperative
+    shapes of the classes whose best tier is the cooperative one
+    (autotune_shapes; their entries gain "shapes")."""
+    import torch
+    stream = torch.cuda.current_stream()
+    per_cls = {}
+    subs = _samples(basis, quartets, sample, seed)
+    for k, sub in subs.items():
+        sub = _filled(basis, sub, stream)
         for tier in tiers:
             try:
                 p = eri.Plan(basis, sub, tier=tier)
             except eri.EriError:
                 continue
             out = torch.empty(max(1, p.output_count), dtype=torch.float64, device="cuda")
-            p.set_timing(True)
-            p.compute(out, stream)  # warm-up (program upload, caches)
-            best = {}
-            for _ in range(reps):
-                p.compute(out, stream)
-                stream.synchronize()
-                for rec in p.launches()[1:]:
-                    c = rec["cls"]
-                    key = (c, rec["tier"])
-                    t = rec["ms"] * 1e3 / max(1, rec["quartets"])
-                    best.setdefault(c, {})
-                    best[c][key] = min(best[c].get(key, float("inf")), t)
-            for c, d in best.items():
+            for (c, t_id, _), t in _timed(p, out, stream, reps, by_kind=False).items():
                 ent = per_cls.setdefault(c, {})
-                for (cc, t_id), t in d.items():
-                    name = eri.TIERS_INV[t_id]
-                    ent[name] = min(ent.get(name, float("inf")), t)
+                name = eri.TIERS_INV[t_id]
+                ent[name] = min(ent.get(name, float("inf")), t)
             p.close()
     result = {}
     for c, d in per_cls.items():
@@ -72,6 +120,60 @@ def autotune(basis, quartets, sample=2048, reps=2, tiers=TIERS, apply=True, seed
         result[c] = {"tier": bt, "us_per_quartet": d}
         if apply:
             eri.set_class_tier(c, bt)
+    if shapes:
+        coop_cls = {c for c, v in result.items() if v["tier"] == "coop"}
+        found = autotune_shapes(basis, quartets, sample=sample, reps=reps, apply=apply, seed=seed,
+                                classes=coop_cls)
+        for c, v in found.items():
+            result.setdefault(c, {"tier": "coop", "us_per_quartet": {}})["shapes"] = v
+    return result
+
+
+def autotune_shapes(basis, quartets, sample=2048, reps=2, apply=True, seed=0, classes=None):
+    """Per class on the cooperative tier (all of them, or those in
+    ``classes``) and per kind of contraction present: time every shipped
+    shape with both vote forms and keep the fastest.  Returns {class: {kind:
+    {"shape": index, "T", "ilp", "k1", "k2": the shape, "votes": "off"|"on",
+    "us_per_quartet": {"<index>/<votes>": t}}}}; with apply the choices are
+    installed (eri_set_class_shape)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    result = {}
+    for _, sub in _samples(basis, quartets, sample, seed).items():
+        sub = _filled(basis, sub, stream)
+        base = eri.Plan(basis, sub)
+        out = torch.empty(max(1, base.output_count), dtype=torch.float64, device="cuda")
+        t0 = _timed(base, out, stream, 1)
+        base.close()
+        present = {}
+        for (c, tier, kind) in t0:
+            if tier == eri.TIERS["coop"] and kind is not None and (classes is None or c in classes):
+                present.setdefault(c, set()).add(kind)
+        for c, kinds in present.items():
+            cands = eri.class_shapes(c)
+            times = {}
+            for i in range(len(cands)):
+                for votes in ("off", "on"):
+                    for kind in eri.KINDS:
+                        eri.set_class_shape(c, kind, i, votes)
+                    try:
+                        p = eri.Plan(basis, sub)
+                    except eri.EriError:
+                        continue
+                    finally:
+                        for kind in eri.KINDS:
+                            eri.set_class_shape(c, kind, -1)
+                    for (cc, tier, kind), t in _timed(p, out, stream, reps).items():
+                        if cc == c and tier == eri.TIERS["coop"] and kind in kinds:
+                            times.setdefault(kind, {})["{}/{}".format(i, votes)] = t
+                    p.close()
+            ent = result.setdefault(c, {})
+            for kind, d in times.items():
+                best = min(d, key=d.get)
+                i, votes = best.split("/")
+                ent[kind] = dict(shape=int(i), votes=votes, us_per_quartet=d, **cands[int(i)])
+                if apply:
+                    eri.set_class_shape(c, kind, int(i), votes)
     return result
 
 
@@ -81,10 +183,19 @@ def save(result, path):
 
 
 def load(path, apply=True):
+    """Read a saved result; with apply, install its tiers and its shapes (a
+    shape is found again by its team size, nodes per lane and wave steps
+    among the shapes this build ships; one no longer shipped is skipped)."""
     with open(path) as f:
         raw = json.load(f)
     result = {tuple(int(ch) for ch in k): v for k, v in raw.items()}
     if apply:
         for c, v in result.items():
             eri.set_class_tier(c, v["tier"])
+            if v.get("shapes"):
+                cands = [tuple(s[k] for k in ("T", "ilp", "k1", "k2")) for s in eri.class_shapes(c)]
+                for kind, e in v["shapes"].items():
+                    key = tuple(e[k] for k in ("T", "ilp", "k1", "k2"))
+                    if key in cands:
+                        eri.set_class_shape(c, kind, cands.index(key), e["votes"])
     return result

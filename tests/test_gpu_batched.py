@@ -41,7 +41,8 @@ def test_screened_list_is_complete_and_bounded(eri):
     pairs, q = screen.pair_bounds(basis)
     thr = 1e-8
     got = synth.screened_quartets(q, pairs, thr)
-    want = sum(1 for i in range(q.size) for j in range(i + 1) if q[i] * q[j] >= thr)
+    i, j = np.tril_indices(q.size)
+    want = int(synth.survives(q[i], q[j], i, j, thr).sum())
     assert got.shape[0] == want
     # every dropped quartet is below the threshold: spot check by the oracle
     rng = np.random.default_rng(0)
@@ -54,6 +55,59 @@ def test_screened_list_is_complete_and_bounded(eri):
             dropped.append(quad)
     v, _ = oracle.eri(basis, np.array(dropped), nthreads=8)
     assert np.abs(v).max() <= thr * (1 + 1e-9)
+
+
+def _canon(quartets, pairs):
+    """Quartets -> set of (larger pair id, smaller pair id)."""
+    pid = {(int(a), int(b)): k for k, (a, b) in enumerate(pairs)}
+    out = set()
+    for a, b, c, d in np.asarray(quartets).tolist():
+        x, y = pid[(a, b)], pid[(c, d)]
+        out.add((max(x, y), min(x, y)))
+    return out
+
+
+@pytest.mark.parametrize("thr", [1e-10, 1e-8, 1e-4])
+def test_device_screening_matches_host(eri, thr):
+    """The device survivor list (counting pass, prefix sum, compaction) is
+    the host enumeration's set exactly, each unordered pair of pairs once,
+    written as (larger pair index, smaller) in increasing order."""
+    import torch
+    from paper_2605_10312_gb300 import screen
+    basis = synth.water_cluster(3, seed=6)
+    pairs, qd = screen.pair_bounds_device(basis)
+    q = qd.cpu().numpy()
+    host = synth.screened_quartets(q, pairs, thr)
+    dp = torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.int32)).cuda()
+    dev = eri.screen_quartets(qd.contiguous(), dp, thr).cpu().numpy()
+    assert dev.shape == host.shape
+    got = _canon(dev, pairs)
+    assert len(got) == dev.shape[0] and got == _canon(host, pairs)
+    pid = {(int(a), int(b)): k for k, (a, b) in enumerate(pairs)}
+    order = [(pid[(a, b)], pid[(c, d)]) for a, b, c, d in dev.tolist()]
+    assert all(x >= y for x, y in order) and order == sorted(order)
+
+
+def test_device_screening_edges(eri):
+    """Threshold 0 keeps every unique quartet, an unreachable one none; a too
+    small output is refused with the count still reported; no pairs, no
+    quartets."""
+    import ctypes
+    import torch
+    from paper_2605_10312_gb300 import screen
+    basis = synth.water_cluster(1, seed=7)
+    pairs, qd = screen.pair_bounds_device(basis)
+    dp = torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.int32)).cuda()
+    n = pairs.shape[0]
+    assert eri.screen_quartets(qd.contiguous(), dp, 0.0).shape == (n * (n + 1) // 2, 4)
+    assert eri.screen_quartets(qd.contiguous(), dp, 1e300).shape == (0, 4)
+    lib = eri.library()
+    cnt = ctypes.c_int64()
+    small = torch.empty((3, 4), dtype=torch.int32, device="cuda")
+    rc = lib.eri_screen_quartets(qd.data_ptr(), dp.data_ptr(), n, 0.0, small.data_ptr(), 3, ctypes.byref(cnt), None)
+    assert rc == -1 and cnt.value == n * (n + 1) // 2
+    rc = lib.eri_screen_quartets(qd.data_ptr(), dp.data_ptr(), 0, 1e-10, None, 0, ctypes.byref(cnt), None)
+    assert rc == 0 and cnt.value == 0
 
 
 def test_graph_replay_and_parity(eri):

@@ -131,3 +131,22 @@ def test_tiny_set_and_class_sweep_recipes():
     xyz = b.centers / synth.ANGSTROM_TO_BOHR
     assert xyz.min() >= 0.0 and xyz.max() <= 10.0
     assert b.exps.min() >= 0.05 and b.exps.max() <= 500.0
+
+
+def test_screening_rule_by_brute_force():
+    """The sorted-prefix enumeration and the count pick exactly the
+    unordered pairs of pairs {p, r} (p >= r) that pass the elementwise rule,
+    on bounds with ties, zeros and values at the threshold's edge."""
+    rng = np.random.default_rng(11)
+    for thr in (1e-10, 0.0, 1.0, 3.0e-3):
+        q = np.concatenate([10.0 ** rng.uniform(-8, 0, 40), np.zeros(3), np.full(4, 0.05), [np.sqrt(thr) if thr else 0]])
+        rng.shuffle(q)
+        npair = q.size
+        pairs = np.stack([np.arange(npair), np.arange(npair)], axis=1).astype(np.int32)   # pair id in both columns
+        p, r = np.tril_indices(npair)
+        keep = synth.survives(q[p], q[r], p, r, thr)
+        want = {(int(a), int(b)) for a, b in zip(p[keep], r[keep])}
+        got = synth.screened_quartets(q, pairs, thr)
+        got_set = {(max(int(x[0]), int(x[2])), min(int(x[0]), int(x[2]))) for x in got}
+        assert got.shape[0] == len(got_set) == len(want) and got_set == want
+        assert synth.count_screened(q, thr) == len(want)
