@@ -178,18 +178,37 @@ def _write_coops(f, coops):
         f.write(c["ph2"])
 
 
-def _registry(recs):
+def _registry(knames):
+    """Registry unit of the compiled register-tier kernels: the names
+    eri_<la><lb><lc><ld>_reg (FP64) and ..._reg_f32 (FP32 recurrences)."""
     lines = ['#include "eri_common.cuh"', "struct EriRegEntry { int8_t ls[4]; const void* fn; };"]
-    for table, key in (("eri_reg", "kname"), ("eri_reg_f32", "kname_f32")):
-        regs = [r for r in recs if key in r]
-        for r in regs:
-            lines.append('extern "C" __global__ void {}(const EriLaunchArgs a);'.format(r[key]))
+    for table, suffix in (("eri_reg", "_reg"), ("eri_reg_f32", "_reg_f32")):
+        regs = sorted(k for k in knames if k.endswith(suffix))
+        for k in regs:
+            lines.append('extern "C" __global__ void {}(const EriLaunchArgs a);'.format(k))
         lines.append('extern "C" const EriRegEntry {}_table[] = {{'.format(table))
-        for r in regs:
-            lines.append("  {{{{{}, {}, {}, {}}}, (const void*){}}},".format(*r["ls"], r[key]))
+        for k in regs:
+            ls = k.split("_")[1]
+            lines.append("  {{{{{}, {}, {}, {}}}, (const void*){}}},".format(*ls, k))
         lines.append("  {{0, 0, 0, 0}, nullptr}};")
         lines.append('extern "C" const int {}_count = {};'.format(table, len(regs)))
     return "\n".join(lines) + "\n"
+
+
+# A register-tier kernel whose ptxas spill stores exceed this is left out of
+# the registry: its class runs on the cooperative tier.  Measured: the FP64
+# (fp|pp) kernel came out at 32 registers with 47 KB of spill stores (every
+# other kernel of its size uses 255 registers and spills at most 13 KB).
+REG_SPILL_MAX = 16 * 1024
+
+
+def _spill_bytes(obj):
+    """Spill stores ptxas reported for a unit (the largest of its functions),
+    kept beside the object when it was compiled."""
+    try:
+        return int(open(obj + ".spill").read())
+    except (OSError, ValueError):
+        return 0
 
 
 def _write_if_changed(path, text):
@@ -209,16 +228,21 @@ def _compile(src, obj, extra=()):
             heads.append(h)
     for p in [src] + heads:
         key.update(open(p, "rb").read())
-    key.update(" ".join(NVCC_ARCH + NVCC_FLAGS + list(extra)).encode())
+    report = os.path.basename(src).startswith("eri_") and "_reg" in os.path.basename(src)
+    key.update(" ".join(NVCC_ARCH + NVCC_FLAGS + list(extra) + (["-Xptxas", "-v"] if report else [])).encode())
     stamp = obj + ".key"
     h = key.hexdigest()
     if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == h:
         return 0.0
     t = time.time()
-    cmd = [_nvcc()] + NVCC_ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
+    cmd = [_nvcc()] + NVCC_ARCH + NVCC_FLAGS + list(extra) + (["-Xptxas", "-v"] if report else []) + \
+        ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for {}:\n{}".format(src, r.stderr[-4000:]))
+    if report:
+        spills = [int(x) for x in re.findall(r"(\d+) bytes spill stores", r.stderr)]
+        open(obj + ".spill", "w").write(str(max(spills, default=0)))
     open(stamp, "w").write(h)
     return time.time() - t
 
@@ -251,7 +275,6 @@ def build(force=False, jobs=None, log=print):
                 _write_if_changed(os.path.join(GEN_DIR, r["kname"] + ".cu"), r["cuda"])
             if "cuda_f32" in r:
                 _write_if_changed(os.path.join(GEN_DIR, r["kname_f32"] + ".cu"), r["cuda_f32"])
-        _write_if_changed(os.path.join(GEN_DIR, "eri_registry.cu"), _registry(recs))
         # class table for the docs and the benchmark: per-class counts
         with open(os.path.join(BUILD, "classes.tsv"), "w") as f:
             f.write("la\tlb\tlc\tld\ttier\tvrr_nodes\tpeak_live\tnslot\tnh\tnout\tper_prim_flops\tp2_flops"
@@ -284,8 +307,7 @@ def build(force=False, jobs=None, log=print):
         open(stamp, "w").write(gen_key)
     units = [os.path.join(CSRC, "eri_runtime.cu"), os.path.join(CSRC, "eri_exec.cu"),
              os.path.join(CSRC, "eri_coop.cu"), os.path.join(CSRC, "eri_digest.cu"),
-             os.path.join(CSRC, "eri_screen.cu"),
-             os.path.join(GEN_DIR, "eri_registry.cu")]
+             os.path.join(CSRC, "eri_screen.cu")]
     units += sorted(os.path.join(GEN_DIR, f) for f in os.listdir(GEN_DIR)
                     if f.endswith("_reg.cu") or f.endswith("_reg_f32.cu"))
     units.sort(key=lambda u: -os.path.getsize(u))  # largest first: the pool ends evenly
@@ -299,7 +321,20 @@ def build(force=False, jobs=None, log=print):
     t1 = time.time()
     with ThreadPoolExecutor(jobs) as ex:
         times = list(ex.map(lambda so: _compile(*so), zip(units, objs)))
-    log("compiled {} units ({} rebuilt) in {:.1f}s".format(len(units), sum(1 for t in times if t > 0),
+    # the registry of the register-tier kernels, less those that spill past
+    # REG_SPILL_MAX (their classes fall to the cooperative tier)
+    regs, dropped = [], []
+    for u, o in zip(units, objs):
+        name = os.path.basename(u)[:-3]
+        if name.endswith("_reg") or name.endswith("_reg_f32"):
+            (dropped if _spill_bytes(o) > REG_SPILL_MAX else regs).append(name)
+    if dropped:
+        log("register-tier kernels left out for spilling over {} B: {}".format(REG_SPILL_MAX, ", ".join(dropped)))
+    reg_src = os.path.join(GEN_DIR, "eri_registry.cu")
+    _write_if_changed(reg_src, _registry(regs))
+    objs.append(os.path.join(BUILD, "eri_registry.o"))
+    times.append(_compile(reg_src, objs[-1]))
+    log("compiled {} units ({} rebuilt) in {:.1f}s".format(len(objs), sum(1 for t in times if t > 0),
                                                           time.time() - t1))
     cmd = [_nvcc()] + NVCC_ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)

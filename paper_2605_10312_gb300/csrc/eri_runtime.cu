@@ -1458,24 +1458,6 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       (sm ? small : large).push_back(q);
       if (fuse && nparts_q[q] == 0) (sm ? rsmall : rlarge).push_back(q);
     }
-    // One thread digests one small quartet.  Neighbouring quartets of a
-    // screened list share shells, so a warp of neighbours would send its 32
-    // reductions to the same J and K entries at once; the list is dealt out
-    // so that the 32 lanes of a warp take quartets n / 32 apart (lane i of
-    // warp w: quartet i * ceil(n / 32) + w), each lane still walking its
-    // stretch of the list in order from warp to warp.
-    auto deal = [](std::vector<int64_t>& v) {
-      const size_t n = v.size(), s = (n + 31) / 32;
-      if (n < 64) return;
-      std::vector<int64_t> o;
-      o.reserve(n);
-      for (size_t w = 0; w < s; ++w)
-        for (size_t i = 0; i < 32; ++i)
-          if (i * s + w < n) o.push_back(v[i * s + w]);
-      v.swap(o);
-    };
-    deal(small);
-    deal(rsmall);
     if ((rc = plan->d_uq.upload(uq, "quartet list")) || (rc = plan->d_shell_bf.upload(bf, "shell offsets")) ||
         (rc = plan->d_small.upload(small, "digest list")) || (rc = plan->d_large.upload(large, "digest list")) ||
         (rc = plan->d_rsmall.upload(rsmall, "digest list")) || (rc = plan->d_rlarge.upload(rlarge, "digest list")))

@@ -47,15 +47,18 @@ def _samples(basis, quartets, sample, seed):
     return out
 
 
-FILL_MS = 10.0    # a trial's launches run at least this long (the sample is repeated)
-FILL_MAX = 1024   # at most this many copies of a sample
+FILL_QUARTETS = 32768   # a trial evaluates at least this many quartets (the sample is repeated) ...
+FILL_MS = 200.0         # ... unless that would take longer than this
+BIG_MS = 20.0           # a sample whose plan already runs this long is used as it is
 
 
 def _filled(basis, sub, stream):
-    """The sample repeated until the default plan's launches take about
-    FILL_MS: a few hundred quartets leave most SMs idle, and per-quartet
-    times of launches that small measure launch overhead and the tail of
-    the last wave of teams, not throughput."""
+    """The sample repeated until a trial measures throughput: a few hundred
+    quartets leave most SMs idle, and small plans are bound by the latency
+    of their deepest quartets (a 512-quartet (pp|pp) sample ran 3.7 ms, 40
+    times its share of the full sweep, on the register tier, whose lanes
+    walk a deep contraction serially).  At least FILL_QUARTETS quartets, as
+    long as the trial stays within about FILL_MS."""
     import torch
     p = eri.Plan(basis, sub)
     out = torch.empty(max(1, p.output_count), dtype=torch.float64, device="cuda")
@@ -65,15 +68,17 @@ def _filled(basis, sub, stream):
     stream.synchronize()
     ms = sum(max(0.0, r["ms"]) for r in p.launches())
     p.close()
-    rep = int(min(FILL_MAX, max(1, np.ceil(FILL_MS / max(ms, 1e-3)))))
+    if ms >= BIG_MS:
+        return sub
+    rep = int(max(1, min(np.ceil(FILL_QUARTETS / max(1, sub.shape[0])), np.floor(FILL_MS / max(ms, 1e-3)))))
     return np.ascontiguousarray(np.tile(sub, (rep, 1))) if rep > 1 else sub
 
 
 def _timed(plan, out, stream, reps, by_kind=True):
-    """{(class, tier, kind): microseconds per quartet part} -- the time of all
-    of a key's launches in one run (a class has one launch per part round
-    and contraction group) over their parts, the best of reps runs after a
-    warm-up (launch timing on).  by_kind False: kind None, all of a class's
+    """{(class, tier, kind): (milliseconds, parts)} -- the time of all of a
+    key's launches in one run (a class has one launch per part round and
+    contraction group) and their quartet parts, the best of reps runs after
+    a warm-up (launch timing on).  by_kind False: kind None, all of a class's
     launches on one tier together."""
     plan.set_timing(True)
     plan.compute(out, stream)  # warm-up (program upload, caches)
@@ -86,8 +91,9 @@ def _timed(plan, out, stream, reps, by_kind=True):
             key = (rec["cls"], rec["tier"], rec.get("kind") if by_kind else None)
             ms, n = tot.get(key, (0.0, 0))
             tot[key] = (ms + rec["ms"], n + rec["quartets"])
-        for key, (ms, n) in tot.items():
-            best[key] = min(best.get(key, float("inf")), ms * 1e3 / max(1, n))
+        for key, v in tot.items():
+            if key not in best or v[0] < best[key][0]:
+                best[key] = v
     return best
 
 
@@ -109,10 +115,13 @@ def autotune(basis, quartets, sample=2048, reps=2, tiers=TIERS, apply=True, seed
             except eri.EriError:
                 continue
             out = torch.empty(max(1, p.output_count), dtype=torch.float64, device="cuda")
-            for (c, t_id, _), t in _timed(p, out, stream, reps, by_kind=False).items():
+            # tiers cut a class into different parts (the cooperative tier
+            # chunks deep contractions), so they compare by the whole
+            # class's time on the same sample, per sample quartet
+            for (c, t_id, _), (ms, _) in _timed(p, out, stream, reps, by_kind=False).items():
                 ent = per_cls.setdefault(c, {})
                 name = eri.TIERS_INV[t_id]
-                ent[name] = min(ent.get(name, float("inf")), t)
+                ent[name] = min(ent.get(name, float("inf")), ms * 1e3 / max(1, sub.shape[0]))
             p.close()
     result = {}
     for c, d in per_cls.items():
@@ -163,9 +172,10 @@ def autotune_shapes(basis, quartets, sample=2048, reps=2, apply=True, seed=0, cl
                     finally:
                         for kind in eri.KINDS:
                             eri.set_class_shape(c, kind, -1)
-                    for (cc, tier, kind), t in _timed(p, out, stream, reps).items():
+                    # shapes and vote forms cut the same parts: per part
+                    for (cc, tier, kind), (ms, n) in _timed(p, out, stream, reps).items():
                         if cc == c and tier == eri.TIERS["coop"] and kind in kinds:
-                            times.setdefault(kind, {})["{}/{}".format(i, votes)] = t
+                            times.setdefault(kind, {})["{}/{}".format(i, votes)] = ms * 1e3 / max(1, n)
                     p.close()
             ent = result.setdefault(c, {})
             for kind, d in times.items():

@@ -128,3 +128,37 @@ def test_mixed_bad_arguments(eri):
         eri.Plan(basis, q, qbound=np.ones(q.shape[0]), fp32_below=float("inf"))
     with pytest.raises(ValueError):
         eri.Plan(basis, q, qbound=np.ones(3), fp32_below=1e-6)
+
+
+def test_mixed_error_vs_oracle_per_class(eri):
+    """The mixed-precision workload's layout (tz water cluster, Schwarz 1e-10,
+    FP32 below 1e-6) on a seeded sample of its screened list, against the
+    FP64 oracle (long-double adjudicated): every element within 1e-10
+    absolute, per class; the per-class max and RMS errors are printed (run
+    with -s)."""
+    import torch
+    from paper_2605_10312_gb300 import screen
+    basis = synth.water_cluster(5, seed=3, layout="tz")
+    pairs, qp = screen.pair_bounds(basis)
+    q = synth.sample_screened_quartets(qp, pairs, 1e-10, 3000, seed=7)
+    qb = screen.quartet_bounds(qp, q)
+    assert (qb < FP32_BELOW).sum() > 1000
+    p = eri.Plan(basis, q, qbound=qb, fp32_below=FP32_BELOW)
+    out = torch.empty(p.output_count, dtype=torch.float64, device="cuda")
+    p.compute(out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref, off = adjudicated(got, basis, q)
+    d = np.abs(got - ref)
+    ls = basis.shell_l[q]
+    labels = np.array(["".join("spdfg"[x] for x in row) for row in ls])
+    elem_label = np.repeat(labels, np.diff(off))
+    elem_fp32 = np.repeat(qb < FP32_BELOW, np.diff(off))
+    worst = 0.0
+    for lab in sorted(set(labels)):
+        m = elem_label == lab
+        mx, rms = d[m].max(), float(np.sqrt(np.mean(d[m] ** 2)))
+        worst = max(worst, mx)
+        print("class {} quartets {} fp32 {} max|d| {:.3g} rms {:.3g}".format(
+            lab, int((labels == lab).sum()), int((m & elem_fp32).sum()), mx, rms))
+    assert worst <= MIXED_ATOL, worst
