@@ -561,7 +561,8 @@ def run_water(args):
         # compaction), then copied to the host for the planner
         dp = torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.int32)).cuda()
         t1 = time.perf_counter()
-        dq = eri.screen_quartets(qd.contiguous(), dp, args.threshold, stream)
+        qs, ps = screen.sort_pairs(qd, dp)
+        dq = eri.screen_quartets(qs, ps, args.threshold, stream)
         torch.cuda.synchronize()
         t_screen_dev = time.perf_counter() - t1
         quartets = dq.cpu().numpy()
@@ -787,7 +788,17 @@ def run_per_k(args):
         for K in (1, 3, 6):
             n = max(1, int(counts[ls[0]][K] * SCALE))
             basis, q = synth.class_sweep(ls, n, kset=(K,), seed=SEED + 10 * ls[0] + K)
+            tuned = None
+            if args.autotune:
+                from paper_2605_10312_gb300 import tune
+                tuned = tune.autotune(basis, q, sample=args.tune_sample, shapes=True)
             p = eri.Plan(basis, q, votes=args.votes, persistent=args.persistent)
+            if tuned:
+                # this (class, K) only: the next one starts from the static choices
+                for c in tuned:
+                    eri.set_class_tier(c, 0)
+                    for kind in eri.KINDS:
+                        eri.set_class_shape(c, kind, -1)
             out = torch.empty(p.output_count, dtype=torch.float64, device="cuda")
             ms = []
             for it in range(args.warmup + args.steps):
@@ -804,7 +815,7 @@ def run_per_k(args):
             rows["{}_K{}".format("".join("spdfg"[x] for x in ls), K)] = {
                 "quartets": n, "ms": t, "quartets_per_s": n / (t * 1e-3),
                 "fp64_frac_of_peak": fl / (t * 1e-3) / 1e12 / fp64_peak_tflops(),
-                "flops_per_quartet": fl / n}
+                "flops_per_quartet": fl / n, "autotuned": tuned_summary(tuned)}
             p.close()
             del out
     print(json.dumps({"workload": "per-class sweep at fixed K (all four shells), 10 Angstrom box",
@@ -824,7 +835,9 @@ def run_serve(args):
     torch.cuda.set_device(0)
     eri.library()
     rng = np.random.default_rng(5)
-    planners = max(1, min(8, (os.cpu_count() or 2) - 1))
+    # host planner threads: all cores but two (the request loop and the CUDA
+    # driver's own threads), at most 16
+    planners = args.planners or max(1, min(16, (os.cpu_count() or 3) - 2))
     srv = serve.Server(budget_bytes=args.serve_budget_gb << 30, slots=args.slots, planners=planners,
                        fp32_below=args.fp32_below if args.fp32_below is not None else 1e-6, timeout_s=30.0)
     t0 = time.perf_counter()
@@ -873,6 +886,7 @@ def main():
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per phase")
     ap.add_argument("--molecules", type=int, default=8, help="serve: molecules in the pool")
     ap.add_argument("--slots", type=int, default=8, help="serve: concurrent requests (streams)")
+    ap.add_argument("--planners", type=int, default=0, help="serve: host planner threads (0: cores - 2)")
     ap.add_argument("--serve-budget-gb", type=int, default=16, help="serve: device-memory budget")
     ap.add_argument("--waters", type=int, default=20)
     ap.add_argument("--layout", default="dz", choices=["dz", "tz"])

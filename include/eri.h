@@ -282,7 +282,8 @@ int eri_schwarz(const eri_plan_t* plan, const double* blocks, double* bounds, vo
  * a quartet survives iff Q_hi >= threshold / Q_lo (Q_lo = 0: iff
  * threshold <= 0).  out: device [max_out][4] int32, 16-byte aligned, or
  * NULL to count only; survivors are written as (P.a, P.b, R.a, R.b), P the
- * larger pair index, ordered by P then R.  *count (host) receives the
+ * larger pair index, ordered by P then R (pairs given in order of falling
+ * factor give the sorted-prefix enumeration's list).  *count (host) receives the
  * number of survivors.  Counts on the device (a prefix sum), reads the total
  * back (the stream is synchronised), then writes; temporary device memory
  * is taken stream-ordered and released.  ERI_EINVAL if out is not NULL and

@@ -756,7 +756,12 @@ WIDE_SHAPES = ((256, 2), (256, 4))
 # sixteen warps on one live set: 512 lanes, two nodes per lane (the register
 # file holds 128 registers for each of 512 threads)
 WIDEST_SHAPE = (512, 2)
-WAVE_NODES_MAX = 2048   # nodes in a multi-step wave of a 512-lane team
+# nodes in a multi-step wave of a 512-lane team: four steps.  Measured on
+# (gg|gg) against two-step waves (27 instead of 44 Phase-1 barriers per
+# primitive quartet, 25,523 instead of 22,760 slots, still one team and 16
+# warps per SM): 0.653 -> 0.672 of the FP64 rate on the sweep, 0.647 ->
+# 0.663 at K = 6, 0.466 -> 0.485 at K = 1.
+WAVE_NODES_MAX = 4096
 
 
 def _teams_per_sm(cp, rows, h_in_smem=True):
@@ -772,8 +777,7 @@ def _wide_waves(prog, cp, rows):
     barriers about fourfold (measured: (gg|gg) 0.45 -> 0.52 of the FP64 rate
     with 256 lanes) at the cost of a larger live set.  Take the widest of 4
     and 2 steps that keeps the teams per SM, with at most WAVE_NODES_MAX nodes
-    in a wave (512 lanes x 2 nodes x 2 steps: the live set and the barrier
-    count of the 256-lane, 4-step waves); narrower teams keep one step per
+    in a wave (512 lanes x 2 nodes x 4 steps); narrower teams keep one step per
     wave (measured: the larger live set costs them residency or lane
     efficiency)."""
     if cp is None or cp.T < 256:

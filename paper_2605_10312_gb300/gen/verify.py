@@ -131,6 +131,9 @@ def verify_coop(cp, L, ncoef):
     assert 28 + 8 + MAX_K < ROW_ENTRIES and 44 + MAX_K < ROW_ENTRIES
     hs = h[live & (h > 0)]
     _bad(np.bincount(hs, minlength=1)[hs] > 1, "phase 1: accumulator with more than one owner", out)
+    # every accumulator has an owner (Phase 2 reads all of H)
+    if np.unique(hs).size != nh:
+        out.append("phase 1: {} of {} accumulators have no owner".format(nh - np.unique(hs).size, nh))
     # ---- Phase 2
     _phase2(cp.ph2, nh + nslot, ncoef, cp.out_dims, out, nop=NOP2)
     # ---- hazards between and within waves

@@ -44,11 +44,24 @@ def screened(basis, threshold=1e-10, stream=None):
 def screened_device(basis, threshold=1e-10, stream=None):
     """The same survivors listed on the device (eri_screen_quartets: a
     counting pass, a prefix sum and a compaction over the device bounds);
-    a CUDA int32 tensor [n, 4], the pair of the larger index first."""
+    a CUDA int32 tensor [n, 4].  The pairs go in sorted by falling bound
+    (stably), so the list comes out in the host enumeration's order and
+    orientation, element for element: screened quartets of one pair of
+    small bound together, which keeps the J/K digestion's reads and
+    reductions of neighbouring quartets on shared L2 lines."""
     import torch
     pairs, q = pair_bounds_device(basis, stream=stream)
     dp = torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.int32)).to(q.device)
-    return eri.screen_quartets(q.contiguous(), dp, threshold, stream)
+    qs, ps = sort_pairs(q, dp)
+    return eri.screen_quartets(qs, ps, threshold, stream)
+
+
+def sort_pairs(q, pairs):
+    """Pair factors (CUDA float64 [npair]) and pairs (CUDA int32 [npair, 2])
+    reordered by falling factor, ties in index order, on the device."""
+    import torch
+    order = torch.argsort(-q, stable=True)
+    return q[order].contiguous(), pairs[order].contiguous()
 
 
 def quartet_bounds(pair_q, quartets):

@@ -217,8 +217,8 @@ def test_widest_team_only_where_a_256_lane_team_is_alone(monkeypatch):
     deep, shallow = coop.choose_both(_FakeProg(21000, 21025))
     assert coop.WIDEST_SHAPE + (1,) in built
     assert (deep.T, deep.ilp) == coop.WIDEST_SHAPE
-    # its waves hold at most WAVE_NODES_MAX nodes: two steps, never four
-    assert coop.WIDEST_SHAPE + (2,) in built and coop.WIDEST_SHAPE + (4,) not in built
+    # its waves hold at most WAVE_NODES_MAX nodes: four steps
+    assert coop.WIDEST_SHAPE + (4,) in built
     # a live set two 256-lane teams can share (H in global memory): no 512
     built.clear()
     deep, shallow = coop.choose_both(_FakeProg(11000, 12000))
@@ -304,7 +304,12 @@ def test_bounds_verifier_catches_planted_errors():
         c.ph2[lins[0], 3] = (c.ph2[lins[0], 3] & 0xFFFFFF00) | ncoef
     def prefetch(c):
         c.ph1[-1] = c.ph1[live1[0]]
-    for fn in (operand, accumulator, element, coefficient, prefetch):
+
+    def orphan(c):
+        # drop one target: its accumulator then has no owner
+        t = np.flatnonzero((((c.ph1[:, 3] >> 16) & 0x8000) == 0) & ((c.ph1[:, 0] >> 16) > 0))[0]
+        c.ph1[t, 0] = c.ph1[t, 0] & 0xFFFF
+    for fn in (operand, accumulator, element, coefficient, prefetch, orphan):
         assert planted(fn), fn.__name__
     enc = encode.encode(prog)
     term = int(np.flatnonzero(((enc.ph1[:, 3] >> 16) & 3) != 2)[0])   # first node with operands
@@ -331,14 +336,14 @@ def test_fp64_issue_count_bounds():
 
 def test_gggg_production_program_matches_oracle():
     """The (gg|gg) cooperative program the build ships (512-lane teams,
-    waves of up to two steps), walked wave by wave on the CPU, reproduces the
+    waves of up to four steps), walked wave by wave on the CPU, reproduces the
     oracle on compact quartets with O(1e-2) integrals."""
     from paper_2605_10312_gb300.gen import verify
     prog = program.make(4, 4, 4, 4)
     deep, _ = coop.choose_both(prog)
-    assert (deep.T, deep.ilp, deep.lag) == coop.WIDEST_SHAPE + (1,) and int(deep.steps1.max()) == 2
-    # Phase 2 in waves of up to four steps (its live set fits Phase 1's slots)
-    assert int(deep.steps2.max()) == 4
+    assert (deep.T, deep.ilp, deep.lag) == coop.WIDEST_SHAPE + (1,) and int(deep.steps1.max()) == 4
+    # Phase 2 in waves of up to eight steps
+    assert int(deep.steps2.max()) == 8
     assert verify.verify_coop(deep, prog.L, len(encode.coef_table())) == []
     basis, q = synth.class_sweep((4, 4, 4, 4), 2, kset=(1, 2), seed=24, box_angstrom=0.5, exp_range=(0.3, 3.0))
     ref, _ = blocks(basis, q)

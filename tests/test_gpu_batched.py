@@ -86,6 +86,10 @@ def test_device_screening_matches_host(eri, thr):
     pid = {(int(a), int(b)): k for k, (a, b) in enumerate(pairs)}
     order = [(pid[(a, b)], pid[(c, d)]) for a, b, c, d in dev.tolist()]
     assert all(x >= y for x, y in order) and order == sorted(order)
+    # pairs sorted by falling bound: the host's list, element for element
+    qs, ps = screen.sort_pairs(qd, dp)
+    dev_sorted = eri.screen_quartets(qs, ps, thr).cpu().numpy()
+    assert np.array_equal(dev_sorted, host)
 
 
 def test_device_screening_edges(eri):

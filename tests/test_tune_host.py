@@ -165,3 +165,12 @@ def test_autotune_shapes_picks_per_kind(monkeypatch, tmp_path):
     table.clear()
     tune.load(path)
     assert table[((2, 2, 2, 2), "deep")] == (1, "on") and table[((2, 2, 2, 2), "single")] == (2, "off")
+
+
+def test_pick_keeps_the_static_choice_within_the_margin():
+    """A trial winner replaces the static choice only when it is more than
+    MARGIN faster; an unknown static choice leaves the fastest."""
+    t = {"reg": 1.0, "coop": 0.97}
+    assert tune._pick(t, "reg") == "reg"
+    assert tune._pick({"reg": 1.0, "coop": 0.90}, "reg") == "coop"
+    assert tune._pick(t, None) == "coop" and tune._pick(t, "shared") == "coop"
