@@ -460,3 +460,14 @@ def test_bank_aware_slots(ls, T, ilp, k1, k2):
     ref, _ = blocks(basis, q)
     got = run_coop(banked, prog, basis, q)
     assert within(got, ref.reshape(q.shape[0], -1)).all()
+
+
+def test_largest_global_tier_program_fits_the_fixed_scratch():
+    """eri_compute_fixed_scratch refuses a class whose global-scratch
+    program needs more than its 64 MiB array for one 128-thread block
+    (slots x 128 threads x 8 bytes).  The largest class, (gg|gg), needs about
+    41 MB, so every class of the library (l <= 4) is accepted and the
+    refusal is reachable only by larger programs."""
+    enc = encode.encode(program.make(4, 4, 4, 4))
+    need = enc.nslot * 128 * 8
+    assert 32 << 20 < need <= 64 << 20, need
