@@ -885,7 +885,7 @@ def main():
     ap.add_argument("--rate", type=float, default=50.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per phase")
     ap.add_argument("--molecules", type=int, default=8, help="serve: molecules in the pool")
-    ap.add_argument("--slots", type=int, default=8, help="serve: concurrent requests (streams)")
+    ap.add_argument("--slots", type=int, default=16, help="serve: concurrent requests (streams)")
     ap.add_argument("--planners", type=int, default=0, help="serve: host planner threads (0: cores - 2)")
     ap.add_argument("--serve-budget-gb", type=int, default=16, help="serve: device-memory budget")
     ap.add_argument("--waters", type=int, default=20)

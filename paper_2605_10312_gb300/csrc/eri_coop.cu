@@ -265,11 +265,15 @@ __device__ __forceinline__ void eri_coop_team(const EriLaunchArgs& a, const EriC
   const bool single = p.single != 0;
   int gi = 0;  // single: position of quartet q in its group of rows
   for (int q = q0; q < a.nq; q += stride) {
-    const EriQuartetRec qr = a.quartets[q];
-    const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];
-    const bool acc = ERI_ACCUMULATE(qr.bra);
-    const bool red = ERI_REDUCE(qr.bra);
-    const EriPairRec ket = a.pairs[qr.ket];
+    // Phase 1 needs only the two pairs' primitive ranges; the records' other
+    // fields (the A - B displacements, the output offset and strides) are
+    // read again for Phase 2, so that they hold no registers through the
+    // recurrence
+    const int32_t qbra = __ldg(&a.quartets[q].bra), qket = __ldg(&a.quartets[q].ket);
+    const int32_t bra_off = __ldg(&a.pairs[ERI_PAIR_INDEX(qbra)].prim_off);
+    const int32_t bra_n = __ldg(&a.pairs[ERI_PAIR_INDEX(qbra)].nprim);
+    const int32_t ket_off = __ldg(&a.pairs[qket].prim_off);
+    const int kk = __ldg(&a.pairs[qket].nprim);
     if (single && gi == 0) {
       const int qi = q + l * stride;
       if (l < p.batch && qi < a.nq) {
@@ -279,15 +283,13 @@ __device__ __forceinline__ void eri_coop_team(const EriLaunchArgs& a, const EriC
       }
     }
     for (int h = l; h < p.nh; h += T) Hs[h] = (R)0;
-    const int kk = ket.nprim;
-    const int k4 = bra.nprim * kk;
+    const int k4 = bra_n * kk;
     for (int b0 = 0; b0 < k4; b0 += p.batch) {
       const int nb = min(p.batch, k4 - b0);
       if (!single && l < nb) {
         const int pidx = b0 + l;
         const int i = pidx / kk, j = pidx - (pidx / kk) * kk;
-        eri_coop_row(a.pprims[bra.prim_off + i], a.pprims[ket.prim_off + j], p.L, a.boys_tab,
-                     rows + l * ERI_COOP_NC);
+        eri_coop_row(a.pprims[bra_off + i], a.pprims[ket_off + j], p.L, a.boys_tab, rows + l * ERI_COOP_NC);
       }
       team_sync();
       for (int pi = 0; pi < nb; ++pi) {
@@ -333,6 +335,11 @@ __device__ __forceinline__ void eri_coop_team(const EriLaunchArgs& a, const EriC
       }
     }
     // Phase 2 and the stores, once per shell quartet
+    const EriQuartetRec qr = a.quartets[q];
+    const EriPairRec bra = a.pairs[ERI_PAIR_INDEX(qr.bra)];
+    const EriPairRec ket = a.pairs[qr.ket];
+    const bool acc = ERI_ACCUMULATE(qr.bra);
+    const bool red = ERI_REDUCE(qr.bra);
     double* const o = a.out + qr.out_off;
     const uint4* dp = p.ph2 + ILP * l;
     uint4 d[ILP], dn[ILP];
