@@ -5,19 +5,16 @@ server keeps each molecule's basis and Schwarz data resident (pair factors
 Q_ab computed once on the device at registration), and runs requests as they
 arrive:
 
-  * admission: a request enters planning when its device-memory footprint
-    (output blocks, quartet records, pair data) fits in the remaining budget
-    and fewer than twice the planner threads are being planned; requests are
-    admitted in arrival order;
+  * admission: a request enters when a slot (a CUDA stream) is free and its
+    device-memory footprint (output blocks, quartet records, pair data) fits
+    in the remaining budget; requests are admitted in arrival order;
   * planning: a pool of host threads builds each admitted request's plan on
     its molecule (eri_plan_on_mol: the molecule's primitive-pair records are
-    reused), on a planner stream: the plan's device memory is stream-ordered
-    there, so retiring one request never synchronises the device under the
-    others; the native planner releases the interpreter lock;
-  * execution: built plans take a slot (a CUDA stream) in admission order;
-    the slot's stream waits for the plan's uploads and runs it, so requests
-    that arrive while others are on the device overlap with them, and a slot
-    is held only for device work;
+    reused, and the plan's device memory is stream-ordered, so that retiring
+    one request never synchronises the device under the others); the native
+    planner releases the interpreter lock;
+  * execution: each plan runs on its slot's stream, so requests that arrive
+    while others are on the device overlap with them;
   * completion: polled with CUDA events; a request that has not finished
     within its timeout is reported with status "timeout" (the host stops
     waiting for it; its memory is reclaimed when the device finishes);
@@ -84,11 +81,6 @@ class Server:
         self.torch = torch
         self.budget = int(budget_bytes)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
-        # plans are built on streams of their own (their uploads and
-        # stream-ordered allocations), before a slot is taken: a slot is held
-        # only while a request's work is on the device
-        self.plan_streams = [torch.cuda.Stream() for _ in range(max(1, planners))]
-        self.max_planning = 2 * max(1, planners)
         self.pool = cf.ThreadPoolExecutor(max_workers=planners)
         self.fp32_below = fp32_below
         self.timeout_s = timeout_s
@@ -129,20 +121,14 @@ class Server:
 
     # -- one request --------------------------------------------------------
     def _build(self, req, stream):
-        """The request's plan, built on ``stream`` (a planner stream), and an
-        event after its uploads: the slot stream that runs it waits on it."""
         mol = self.molecules[req.mol]
         # a request's class launches spread over the plan's streams (measured:
         # one stream per plan leaves small requests' kernels too narrow to
         # fill the GPU -- capacity 106 against 138 requests/s)
         if self.fp32_below is None:
-            plan = eri.Plan(None, req.quartets, mol=mol.mol, stream=stream)
-        else:
-            qb = self.bounds(mol, req.quartets)
-            plan = eri.Plan(None, req.quartets, qbound=qb, fp32_below=self.fp32_below, mol=mol.mol, stream=stream)
-        ev = self.torch.cuda.Event()
-        ev.record(stream)
-        return plan, ev
+            return eri.Plan(None, req.quartets, mol=mol.mol, stream=stream)
+        qb = self.bounds(mol, req.quartets)
+        return eri.Plan(None, req.quartets, qbound=qb, fp32_below=self.fp32_below, mol=mol.mol, stream=stream)
 
     def run_alone(self, req):
         """The request evaluated by itself (plain plan, default stream
@@ -169,9 +155,8 @@ class Server:
         queue = collections.deque()
         free_slots = list(range(len(self.streams)))[::-1]
         free_bytes = self.budget
-        planning = collections.deque()   # (future, req, nbytes), admission order
+        planning = {}   # future -> (req, slot, nbytes)
         running = []    # [req, slot, nbytes, plan, out, event, timed_out]
-        nps = 0         # next planner stream
         t0 = time.perf_counter()
         while pending or queue or planning or running:
             now = time.perf_counter() - t0
@@ -179,8 +164,8 @@ class Server:
             while pending and pending[0].arrival <= now:
                 queue.append(pending.popleft())
                 progressed = True
-            # admission to planning in arrival order while the head fits
-            while queue and len(planning) < self.max_planning:
+            # admission in arrival order while the head fits
+            while queue and free_slots:
                 req = queue[0]
                 nbytes = self.footprint(self.molecules[req.mol], req.quartets)
                 if nbytes > self.budget:
@@ -192,19 +177,17 @@ class Server:
                 if nbytes > free_bytes:
                     break
                 queue.popleft()
+                slot = free_slots.pop()
                 free_bytes -= nbytes
                 results[req.rid].admitted = now
-                fut = self.pool.submit(self._build, req, self.plan_streams[nps])
-                nps = (nps + 1) % len(self.plan_streams)
-                planning.append((fut, req, nbytes))
+                fut = self.pool.submit(self._build, req, self.streams[slot])
+                planning[fut] = (req, slot, nbytes)
                 progressed = True
-            # launch built plans in admission order as slots free up
-            while planning and planning[0][0].done() and free_slots:
-                fut, req, nbytes = planning.popleft()
-                plan, built = fut.result()
-                slot = free_slots.pop()
+            # launch the plans that are built
+            for fut in [f for f in planning if f.done()]:
+                req, slot, nbytes = planning.pop(fut)
+                plan = fut.result()
                 st = self.streams[slot]
-                st.wait_event(built)
                 with torch.cuda.stream(st):
                     out = torch.empty(max(1, plan.output_count), dtype=torch.float64, device="cuda")
                     plan.compute(out, st)
@@ -224,7 +207,7 @@ class Server:
                     t = time.perf_counter() - t0
                     if not timed_out:
                         res.finished = t
-                    plan.close()   # the work is done: its planner stream frees the memory
+                    plan.close()   # stream-ordered: frees after the work on the slot's stream
                     if self.keep_outputs and not timed_out:
                         res.output = out
                     del out

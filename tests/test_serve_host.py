@@ -179,23 +179,3 @@ def test_timeout_is_reported_and_the_slot_held_until_the_work_ends(monkeypatch):
     assert res[0].finished - res[0].arrival < 0.25          # reported at the deadline, not at the end
     assert res[1].launched >= 0.29                          # the slot was held until the work ended
 
-
-def test_planning_does_not_hold_a_slot(monkeypatch):
-    """Plans are built on planner threads before a slot is taken: with one
-    slot, two planner threads and a plan that takes 0.1 s to build, two
-    requests arriving together are planned at the same time, and the second
-    launches as soon as the first's short device work ends -- not after its
-    own planning has waited for the slot."""
-    srv, tr, _ = _server(monkeypatch, budget=1 << 30, slots=1, timeout_s=5.0, duration=lambda q: 0.01)
-    base = serve.eri.Plan
-
-    class SlowPlan(base):
-        def __init__(self, *a, **kw):
-            time.sleep(0.1)
-            super().__init__(*a, **kw)
-    monkeypatch.setattr(serve.eri, "Plan", SlowPlan)
-    res = srv.serve(_requests([10, 10], [0.0, 0.0]))
-    srv.close()
-    assert [r.status for r in res] == ["ok", "ok"]
-    assert res[1].launched < 0.17, res[1].launched
-    assert res[0].finished <= res[1].launched + 1e-3      # one slot: one request on the device at a time
