@@ -90,7 +90,9 @@ class _Tracker:
     and the slot count at every launch."""
 
     def __init__(self, budget, slots, mol, duration):
+        import threading
         self.budget, self.slots, self.mol, self.duration = budget, slots, mol, duration
+        self.lock = threading.Lock()   # plans are launched from planner threads
         self.live = set()
         self.max_live = 0
         self.launch_order = []
@@ -104,19 +106,21 @@ class _Tracker:
                 self.output_count = int(self.q.shape[0])
 
             def compute(self, out, st):
-                st.busy_until = max(st.busy_until, time.perf_counter()) + tr.duration(self.q)
-                tr.live.add(self)
-                tr.launch_order.append(int(self.q[0, 0]))
-                tr.max_live = max(tr.max_live, len(tr.live))
-                used = sum(serve.Server.footprint(tr.mol, p.q) for p in tr.live)
-                assert used <= tr.budget, "admitted beyond the memory budget"
-                assert len(tr.live) <= tr.slots, "more requests in flight than slots"
+                with tr.lock:
+                    st.busy_until = max(st.busy_until, time.perf_counter()) + tr.duration(self.q)
+                    tr.live.add(self)
+                    tr.launch_order.append(int(self.q[0, 0]))
+                    tr.max_live = max(tr.max_live, len(tr.live))
+                    used = sum(serve.Server.footprint(tr.mol, p.q) for p in tr.live)
+                    assert used <= tr.budget, "admitted beyond the memory budget"
+                    assert len(tr.live) <= tr.slots, "more requests in flight than slots"
 
             def stats(self):
                 return {"fp32_parts": 0}
 
             def close(self):
-                tr.live.discard(self)
+                with tr.lock:
+                    tr.live.discard(self)
         return FakePlan
 
 
@@ -145,7 +149,8 @@ def _requests(sizes, arrivals):
 
 def test_admission_holds_the_memory_budget_and_the_slots(monkeypatch):
     """Twelve requests at once, memory for two: never more than two in
-    flight, all served, admitted and launched in arrival order."""
+    flight, all served, admitted in arrival order (the planner threads
+    launch each plan as soon as it is built)."""
     one = serve.Server.footprint(serve.Molecule("m", None, np.zeros((10, 2)), np.ones(10), None,
                                                 nsph=np.ones(64, dtype=np.int64)), np.zeros((1000, 4), dtype=np.int32))
     srv, tr, _ = _server(monkeypatch, budget=2 * one + 100, slots=4, timeout_s=5.0, duration=lambda q: 0.05)
@@ -153,7 +158,8 @@ def test_admission_holds_the_memory_budget_and_the_slots(monkeypatch):
     srv.close()
     assert [r.status for r in res] == ["ok"] * 12
     assert tr.max_live == 2
-    assert tr.launch_order == sorted(tr.launch_order)
+    adm = [r.admitted for r in res]
+    assert adm == sorted(adm) and sorted(tr.launch_order) == list(range(12))
     assert all(r.admitted <= r.launched <= r.finished for r in res)
 
 
