@@ -42,6 +42,7 @@ LATENCY_REPEATS = 100
 KSET = (1, 3, 6)
 SEED = 2000
 ONLY = None     # --classes: subset of the sweep (profiling runs)
+E2E_CHUNK = 250_000  # quartets per plan in the end-to-end leg (planned in parallel)
 SCALE = 1.0     # --scale: quartet counts multiplied by this (profiling runs)
 # FP64 fused multiply-add lanes per SM per clock, measured on GB300 with the
 # fp_peak microbenchmark (independent FMA chains on every SM)
@@ -361,21 +362,38 @@ def run_ours(args):
     else:
         args_e2e_steps = e2e_warmup + args.steps
     host_outs = [torch.empty(p.output_count, dtype=torch.float64).pin_memory() for _, p in plans]
+    # A plan is built on one host thread (about 1.7 us per quartet when every
+    # quartet brings new shell pairs), so a class's list is planned in
+    # contiguous chunks of about E2E_CHUNK quartets on several threads; the
+    # chunks' blocks, in order, are the class's blocks.
+    chunks = []
+    for k, (ls, basis, q) in enumerate(parts):
+        nch = max(1, int(round(q.shape[0] / E2E_CHUNK)))
+        edges = np.linspace(0, q.shape[0], nch + 1).astype(np.int64)
+        for c in range(nch):
+            chunks.append((k, basis, q[edges[c]:edges[c + 1]]))
     from concurrent.futures import ThreadPoolExecutor
-    pool = ThreadPoolExecutor(max_workers=len(parts))
+    pool = ThreadPoolExecutor(max_workers=max(1, min(len(chunks), (os.cpu_count() or 2) - 1)))
+    e2e_streams = [stream, torch.cuda.Stream()]
     for it in range(args_e2e_steps):
         barrier()
         t0 = time.perf_counter()
         h2d = d2h = 0
-        # the class plans are independent: build them concurrently (the
-        # native planner releases the interpreter lock), then evaluate each
-        # and copy its blocks to pinned host memory
-        built = list(pool.map(lambda part: eri.Plan(part[1], part[2]), parts))
-        for p, ho in zip(built, host_outs):
-            p.compute_host(ho, stream)
+        # the plans are independent: build them concurrently (the native
+        # planner releases the interpreter lock), then evaluate each and copy
+        # its blocks to its stretch of the class's pinned host buffer
+        built = list(pool.map(lambda ch: eri.Plan(ch[1], ch[2]), chunks))
+        at = [0] * len(parts)
+        for i, ((k, _, _), p) in enumerate(zip(chunks, built)):
+            n = p.output_count
+            # two streams in turn: a plan's copy to the host overlaps the
+            # next plan's evaluation
+            p.compute_host(host_outs[k][at[k]:at[k] + n], e2e_streams[i % 2])
+            at[k] += n
             h2d += p.stats()["h2d_bytes"]
-            d2h += ho.numel() * 8
-        stream.synchronize()
+            d2h += n * 8
+        for st in e2e_streams:
+            st.synchronize()
         for p in built:
             p.close()
         barrier()
@@ -414,7 +432,8 @@ def run_ours(args):
                      "peak_basis": "FP64 FMA issue rate measured by fp_peak ({} lanes/SM/clk) x 2 x 152 SMs x "
                                    "2070 MHz".format(FP64_LANES_PER_SM_CLK)},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "plans_per_step": len(chunks), "plan_threads": pool._max_workers},
         "latency": latency,
         "gpu_launches": nlaunch * args.steps,
         "clocks": clk,
