@@ -1157,10 +1157,13 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       // class table's preference (autotuner), else the static rule, measured
       // on the sweep classes with K per shell from {1, 3, 6}: votes pay for
       // teams of 128 lanes or more ((ff|ff) 0.610 -> 0.690 of the FP64 rate,
-      // (gg|gg) 0.620 -> 0.632) and cost 64-lane teams ((dd|dd) 0.602 -> 0.582)
+      // (gg|gg) 0.620 -> 0.632) and cost 64-lane teams ((dd|dd) 0.602 -> 0.582);
+      // single-primitive parts of 512-lane teams run better predicated
+      // (autotuner, (gg|gg) at K = 1: 0.485 -> 0.513)
       {
         const int pv = pvotes ? pvotes : preferred_votes(b.ls);
-        const int want_v = opts.votes ? opts.votes : pv ? pv : (cp->T >= 128 ? 2 : 1);
+        const int stat = cp->T >= 512 && k4_first == 1 ? 1 : cp->T >= 128 ? 2 : 1;
+        const int want_v = opts.votes ? opts.votes : pv ? pv : stat;
         b.vote = want_v == 2 ? 1 : 0;
       }
       b.coop = cp;
