@@ -335,6 +335,11 @@ int eri_plan_launch_shape(const eri_plan_t* plan, int i, int32_t* info);
  * graph), and replay it with eri_plan_graph_launch: all of the plan's class
  * launches go out as one graph launch. */
 int eri_plan_graph_capture(eri_plan_t* plan, double* out, void* stream);
+/* The same for eri_compute_jk(plan, density, nbf, J, K, stream): each replay
+ * adds into J and K (zero them between replays as needed).  The plan's block
+ * buffer is allocated before the capture.  Errors as eri_compute_jk. */
+int eri_plan_graph_capture_jk(eri_plan_t* plan, const double* density, int32_t nbf, double* J, double* K,
+                              void* stream);
 int eri_plan_graph_launch(eri_plan_t* plan, void* stream);
 
 /* Release the plan and its device memory.  A plan from eri_plan_on_stream

@@ -1004,7 +1004,9 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   };
   std::vector<PartKey> pk(nparts);
   std::vector<EriQuartetRec> recs(nparts);
-  std::vector<int32_t> rec_q(fuse ? nparts : 0);
+  // record -> quartet: for the fused epilogue, and for the digestion lists
+  // (ordered by the launch that evaluates a quartet's last part)
+  std::vector<int32_t> rec_q(opts.digest == 1 ? nparts : 0);
   {
     // dense ids: used (round, class, precision) groups and (K4, kb) signatures
     std::vector<int32_t> gdense(4 * ncls * 2, -1);
@@ -1042,7 +1044,7 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       const QInfo& x = qi[q];
       const int64_t p = start[key[q]]++;
       recs[p] = x.rec;
-      if (fuse) rec_q[p] = x.uq;
+      if (opts.digest == 1) rec_q[p] = x.uq;
       pk[p] = {x.cls, x.round, x.prec, x.kb, x.kk};
     }
   }
@@ -1456,7 +1458,27 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     std::vector<int32_t> bf(nshell + 1, 0);
     for (int s = 0; s < nshell; ++s) bf[s + 1] = bf[s] + nfun(shells[s].l, cart);
     std::vector<int64_t> small, large, rsmall, rlarge;
-    for (int64_t q = 0; q < nq; ++q) {
+    // the lists hold the quartets grouped by the launch (bucket) that
+    // evaluates their last part (the highest part round; quartets whose
+    // parts all run in a persistent launch come last), bucket by bucket, in
+    // increasing quartet order within a bucket: the 32 quartets of a warp of
+    // the small-block kernel then mostly belong to one class, with blocks of
+    // one size, and take the same loop bounds (in quartet order the warp's
+    // classes mix: measured on the 60-atom water cluster, 54 ms in quartet
+    // order against 36.5 ms grouped)
+    const size_t nbk = plan->buckets.size();
+    std::vector<int32_t> lastb(nq, (int32_t)nbk);
+    for (size_t k = 0; k < nbk; ++k) {
+      const Bucket& b = plan->buckets[k];
+      if (b.tier == TIER_PERSIST) continue;
+      for (int64_t r = b.first; r < b.first + b.count; ++r) lastb[rec_q[r]] = (int32_t)k;
+    }
+    std::vector<int64_t> start(nbk + 2, 0), order(nq);
+    for (int64_t q = 0; q < nq; ++q) ++start[lastb[q] + 1];
+    for (size_t k = 0; k <= nbk; ++k) start[k + 1] += start[k];
+    for (int64_t q = 0; q < nq; ++q) order[start[lastb[q]]++] = q;
+    std::vector<int32_t>().swap(lastb);
+    for (const int64_t q : order) {
       const bool sm = plan->offsets[q + 1] - plan->offsets[q] <= kSmallBlock;
       (sm ? small : large).push_back(q);
       if (fuse && nparts_q[q] == 0) (sm ? rsmall : rlarge).push_back(q);
@@ -1834,18 +1856,23 @@ extern "C" int eri_compute_jk(eri_plan_t* plan, const double* density, int32_t n
     plan->outbuf.reset();
     if (int rc = plan->outbuf.alloc(n, "output buffer")) return rc;
   }
-  if (plan->persistent) {
-    // the digestion runs in the evaluation launch itself
-    if (!density) return fail(ERI_EINVAL, "NULL density");
-    if (nbf != plan->nbf) return fail(ERI_EINVAL, "nbf does not match the plan's basis functions");
-    if (!J && !K) return eri_compute(plan, plan->outbuf.p, stream);
-    const FuseIn fz = {density, J, K, nbf};
-    if (int rc = compute_impl(plan, plan->outbuf.p, stream, &fz)) return rc;
-    // quartets whose parts all ran on the register tier
-    return digest_lists(plan, plan->outbuf.p, density, nbf, J, K, stream, true);
+  if (!density) return fail(ERI_EINVAL, "NULL density");
+  if (nbf != plan->nbf) return fail(ERI_EINVAL, "nbf does not match the plan's basis functions");
+  if (!J && !K) return eri_compute(plan, plan->outbuf.p, stream);
+  if (!plan->persistent) {
+    // the separate digestion pass after the evaluation.  Digesting each
+    // bucket's quartets on its stream right after its launch was measured
+    // slower (the 60-atom water cluster: 307.6 ms against 294.4 ms per
+    // step): the latency-bound digestion blocks then hold SMs that the
+    // concurrent FP64-bound class launches would use.
+    if (int rc = eri_compute(plan, plan->outbuf.p, stream)) return rc;
+    return digest_lists(plan, plan->outbuf.p, density, nbf, J, K, stream, false);
   }
-  if (int rc = eri_compute(plan, plan->outbuf.p, stream)) return rc;
-  return eri_digest_jk(plan, plan->outbuf.p, density, nbf, J, K, stream);
+  // the digestion runs in the evaluation launch itself, then the quartets
+  // whose parts all ran on the register tier
+  const FuseIn fz = {density, J, K, nbf};
+  if (int rc = compute_impl(plan, plan->outbuf.p, stream, &fz)) return rc;
+  return digest_lists(plan, plan->outbuf.p, density, nbf, J, K, stream, true);
 }
 
 extern "C" int eri_plan_set_timing(eri_plan_t* plan, int enable) {
@@ -2242,7 +2269,10 @@ extern "C" int eri_class_shapes(int la, int lb, int lc, int ld, int32_t* info, i
   return (int)v.size();
 }
 
-extern "C" int eri_plan_graph_capture(eri_plan_t* plan, double* out, void* stream_) {
+// Capture run(stream) -- eri_compute or eri_compute_jk of the plan -- into
+// the plan's graph.
+template <typename Run>
+static int graph_capture(eri_plan_t* plan, void* stream_, Run run) {
   if (!plan) return fail(ERI_EINVAL, "NULL plan");
   cudaStream_t stream = (cudaStream_t)stream_;
   if (stream == nullptr) return fail(ERI_EINVAL, "capture needs a non-default stream");
@@ -2253,7 +2283,7 @@ extern "C" int eri_plan_graph_capture(eri_plan_t* plan, double* out, void* strea
   const bool timing = plan->timing;
   plan->timing = false;
   CUDA_OR(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-  const int rc = eri_compute(plan, out, stream_);
+  const int rc = run(stream_);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(stream, &graph);
   plan->timing = timing;
@@ -2266,6 +2296,20 @@ extern "C" int eri_plan_graph_capture(eri_plan_t* plan, double* out, void* strea
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(ERI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
   return ERI_OK;
+}
+
+extern "C" int eri_plan_graph_capture(eri_plan_t* plan, double* out, void* stream) {
+  return graph_capture(plan, stream, [&](void* st) { return eri_compute(plan, out, st); });
+}
+
+extern "C" int eri_plan_graph_capture_jk(eri_plan_t* plan, const double* density, int32_t nbf, double* J, double* K,
+                                         void* stream) {
+  if (plan && plan->nq > 0 && plan->digest && (size_t)plan->offsets.back() > plan->outbuf.n) {
+    // the plan's block buffer is allocated before the capture, not inside it
+    plan->outbuf.reset();
+    if (int rc = plan->outbuf.alloc((size_t)plan->offsets.back(), "output buffer")) return rc;
+  }
+  return graph_capture(plan, stream, [&](void* st) { return eri_compute_jk(plan, density, nbf, J, K, st); });
 }
 
 extern "C" int eri_plan_graph_launch(eri_plan_t* plan, void* stream_) {

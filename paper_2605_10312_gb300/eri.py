@@ -111,6 +111,9 @@ def library(path: str = LIB):
         lib.eri_set_class_votes.argtypes = [ctypes.c_int] * 5
         lib.eri_plan_graph_capture.restype = ctypes.c_int
         lib.eri_plan_graph_capture.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.eri_plan_graph_capture_jk.restype = ctypes.c_int
+        lib.eri_plan_graph_capture_jk.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_void_p]
         lib.eri_plan_graph_launch.restype = ctypes.c_int
         lib.eri_plan_graph_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         lib.eri_screen_quartets.restype = ctypes.c_int
@@ -317,6 +320,14 @@ class Plan:
         """Capture compute(out) on ``stream`` (not the default stream) into a
         CUDA graph; replay with ``replay``."""
         _check(library().eri_plan_graph_capture(self._h, out.data_ptr(), _stream_handle(stream)))
+
+    def capture_jk(self, density, J, K, stream):
+        """Capture compute_jk(density, J, K) on ``stream`` into a CUDA graph;
+        each ``replay`` adds into J and K."""
+        n = int(density.shape[0])
+        _check(library().eri_plan_graph_capture_jk(self._h, self._square(density, n, "density"), n,
+                                                   self._square(J, n, "J"), self._square(K, n, "K"),
+                                                   _stream_handle(stream)))
 
     def replay(self, stream=None):
         _check(library().eri_plan_graph_launch(self._h, _stream_handle(stream)))

@@ -54,7 +54,8 @@ def test_jk_tiny_set(eri, via_blocks):
     assert within(K.ravel(), Kr.ravel()).all(), report(K.ravel(), Kr.ravel())
 
 
-def test_jk_water_any_representative(eri):
+@pytest.mark.parametrize("via_blocks", [True, False])
+def test_jk_water_any_representative(eri, via_blocks):
     """One water (O 3s 2p 1d, H 2s 1p): 12 shells, 24 functions.  Each orbit
     is passed through a random one of its 8 representatives."""
     basis = synth.water_cluster(1, seed=8)
@@ -64,10 +65,45 @@ def test_jk_water_any_representative(eri):
     qr = np.array([row[list(perms[rng.integers(8)])] for row in q], dtype=np.int32)
     nbf = int(oracle.basis_function_offsets(basis)[-1])
     D = _density(nbf, 3)
-    J, K = _gpu_jk(eri, basis, qr, D)
+    J, K = _gpu_jk(eri, basis, qr, D, via_blocks=via_blocks)
     Jr, Kr = oracle.jk(basis, D, nthreads=8)
     assert within(J.ravel(), Jr.ravel()).all(), report(J.ravel(), Jr.ravel())
     assert within(K.ravel(), Kr.ravel()).all(), report(K.ravel(), Kr.ravel())
+
+
+def test_jk_graph_capture(eri):
+    """eri_compute_jk and its captured graph (evaluation and digestion pass in
+    one graph), replayed twice with J and K zeroed in between, against the
+    oracle: two waters, every unique quartet (multi-part quartets in later
+    part rounds, classes spread over several streams; the digestion lists
+    are grouped by the launch that completes each quartet)."""
+    import torch
+    basis = synth.water_cluster(2, seed=8)
+    q = synth.all_unique_quartets(basis.nshell)
+    nbf = int(oracle.basis_function_offsets(basis)[-1])
+    D = _density(nbf, 6)
+    Jr, Kr = oracle.jk(basis, D, nthreads=8)
+    p = eri.Plan(basis, q, digest=True)
+    # some quartets have several parts (later part rounds add into them)
+    assert sum(r["quartets"] for r in p.launches()[1:]) > q.shape[0]
+    Dt = torch.from_numpy(D).cuda()
+    J = torch.zeros_like(Dt)
+    K = torch.zeros_like(Dt)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        p.compute_jk(Dt, J, K, st)
+        st.synchronize()
+        assert within(J.cpu().numpy().ravel(), Jr.ravel()).all()
+        assert within(K.cpu().numpy().ravel(), Kr.ravel()).all()
+        p.capture_jk(Dt, J, K, st)
+        for _ in range(2):
+            J.zero_()
+            K.zero_()
+            p.replay(st)
+        st.synchronize()
+    Jg, Kg = J.cpu().numpy(), K.cpu().numpy()
+    assert within(Jg.ravel(), Jr.ravel()).all(), report(Jg.ravel(), Jr.ravel())
+    assert within(Kg.ravel(), Kr.ravel()).all(), report(Kg.ravel(), Kr.ravel())
 
 
 def test_jk_errors(eri):
