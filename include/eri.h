@@ -115,10 +115,11 @@ int eri_plan(const eri_shell* shells, int32_t nshell, const eri_basis* basis, co
  * paper evaluates everything in FP64 and has no counterpart).  Like eri_plan,
  * plus qbound (host, nq doubles >= 0): an upper bound on |(ab|cd)| for each
  * quartet, normally the Schwarz product Q_ab Q_cd.  Quartets with
- * qbound[q] < fp32_below run the recurrences (VRR, contraction sums, HRR and
- * the spherical transform) in FP32; the pair and primitive-quartet set-up,
- * the Boys function, every other quartet and the output (stores and the
- * accumulation of split parts) stay FP64.  The absolute error of an FP32
+ * qbound[q] < fp32_below run the primitive-quartet set-up (W - P, W - Q, T,
+ * the prefactor and the recurrence coefficients, from an FP32 copy of the
+ * primitive-pair data) and the recurrences (VRR, contraction sums, HRR and
+ * the spherical transform) in FP32; the Boys function, every other quartet
+ * and the output (stores and the accumulation of split parts) stay FP64.  The absolute error of an FP32
  * quartet is then about qbound[q] times a small multiple of 2^-24 per
  * recurrence level.  FP32 is used only with the default generator options
  * and tier 0, 1 or 4; otherwise the plan is all FP64.  Errors: ERI_EINVAL

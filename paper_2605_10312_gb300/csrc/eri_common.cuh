@@ -19,6 +19,32 @@ struct EriPairPrim {   // 72 bytes
   double K;            // sqrt(2) pi^(5/4) c_i N_i c_j N_j exp(-a_i b_j |A-B|^2 / zeta) / zeta
 };
 
+// The same quantities rounded to FP32, for quartets whose recurrences run
+// in FP32 (written by the pair set-up kernel beside the FP64 record).  P is
+// kept as an unevaluated sum P_hi + P_lo of two floats, so that P - Q of
+// two pairs keeps FP32 relative accuracy when P and Q are close (a plain
+// float P would lose it to cancellation at coordinates of tens of bohr).
+struct EriPairPrimF {  // 48 bytes
+  float zeta;
+  float inv2z;
+  float Phi[3], Plo[3];
+  float PA[3];
+  float K;
+};
+
+__device__ __forceinline__ EriPairPrimF eri_pair_prim_f32(const EriPairPrim& q) {
+  EriPairPrimF f;
+  f.zeta = (float)q.zeta;
+  f.inv2z = (float)q.inv2z;
+  for (int d = 0; d < 3; ++d) {
+    f.Phi[d] = (float)q.P[d];
+    f.Plo[d] = (float)(q.P[d] - (double)f.Phi[d]);
+    f.PA[d] = (float)q.PA[d];
+  }
+  f.K = (float)q.K;
+  return f;
+}
+
 struct EriPairRec {    // 32 bytes
   int32_t prim_off;    // first EriPairPrim
   int32_t nprim;       // K_a * K_b
@@ -52,6 +78,7 @@ struct EriLaunchArgs {
   const EriQuartetRec* __restrict__ quartets;  // this launch's quartets
   const EriPairRec* __restrict__ pairs;
   const EriPairPrim* __restrict__ pprims;
+  const EriPairPrimF* __restrict__ pprims_f;   // FP32 copy (plans with FP32 quartets, else null)
   const double* __restrict__ boys_tab;         // Taylor table, see below
   double* __restrict__ out;
   double* __restrict__ scratch;                // slot tiers: [slot][thread]
@@ -149,4 +176,30 @@ __device__ __forceinline__ void eri_prim_quartet(const EriPairPrim& b, const Eri
   const double rho = b.zeta * te;
   o.T = rho * fma(pq0, pq0, fma(pq1, pq1, pq2 * pq2));
   o.pref = b.K * k.K * sqrt(s);
+}
+
+// The same in FP32, for quartets whose recurrences run in FP32: only the
+// Boys function (and the accumulation into the block) stays in FP64.
+struct EriPrimQuartetF {
+  float s, te, tz;
+  float WP[3], WQ[3];
+  float T, pref;
+};
+
+__device__ __forceinline__ void eri_prim_quartet_f32(const EriPairPrimF& b, const EriPairPrimF& k,
+                                                     EriPrimQuartetF& o) {
+  const float s = 1.0f / (b.zeta + k.zeta);
+  const float te = k.zeta * s, tz = b.zeta * s;
+  float pq[3];
+  for (int d = 0; d < 3; ++d) pq[d] = (b.Phi[d] - k.Phi[d]) + (b.Plo[d] - k.Plo[d]);
+  o.s = s;
+  o.te = te;
+  o.tz = tz;
+  for (int d = 0; d < 3; ++d) {
+    o.WP[d] = -te * pq[d];
+    o.WQ[d] = tz * pq[d];
+  }
+  const float rho = b.zeta * te;
+  o.T = rho * fmaf(pq[0], pq[0], fmaf(pq[1], pq[1], pq[2] * pq[2]));
+  o.pref = b.K * k.K * sqrtf(s);
 }

@@ -61,8 +61,7 @@ __device__ __forceinline__ void eri_coop_boys(int L, double T, double* F, const 
 #define ERI_COOP_NC 56
 #define ERI_COOP_BATCH 32  // largest row batch (one row per lane of a warp)
 
-// The row is formed in FP64 (Boys function included) and rounded once to the
-// value type R of the recurrences.
+// The FP64 row (value type R = double).
 template <typename R>
 __device__ __forceinline__ void eri_coop_row(const EriPairPrim& bp, const EriPairPrim& kp, int L,
                                              const double* __restrict__ tab, R* row) {
@@ -85,6 +84,41 @@ __device__ __forceinline__ void eri_coop_row(const EriPairPrim& bp, const EriPai
   row[53] = (R)(-pq.te);
   row[54] = (R)(-pq.tz);
 }
+
+// The FP32 row of a quartet whose recurrences run in FP32: formed in FP32
+// from the FP32 pair data, with the Boys function in FP64.
+__device__ __forceinline__ void eri_coop_row(const EriPairPrimF& bp, const EriPairPrimF& kp, int L,
+                                             const double* __restrict__ tab, float* row) {
+  EriPrimQuartetF pq;
+  eri_prim_quartet_f32(bp, kp, pq);
+  double F[ERI_BOYS_LMAX + 1];
+  eri_coop_boys(L, (double)pq.T, F, tab);
+  for (int m = 0; m <= L; ++m) row[m] = pq.pref * (float)F[m];
+  for (int i = 0; i < 3; ++i) {
+    row[17 + i] = bp.PA[i];
+    row[20 + i] = pq.WP[i];
+    row[23 + i] = kp.PA[i];
+    row[26 + i] = pq.WQ[i];
+  }
+  const float c3 = 0.5f * pq.s;
+  for (int k = 0; k < 8; ++k) {
+    row[29 + k] = (float)(k + 1) * bp.inv2z;
+    row[37 + k] = (float)(k + 1) * kp.inv2z;
+    row[45 + k] = (float)(k + 1) * c3;
+  }
+  row[53] = -pq.te;
+  row[54] = -pq.tz;
+}
+
+// The primitive-pair records a team of value type R forms its rows from.
+template <typename R>
+struct EriPrimsOf {
+  static __device__ __forceinline__ const EriPairPrim* get(const EriLaunchArgs& a) { return a.pprims; }
+};
+template <>
+struct EriPrimsOf<float> {
+  static __device__ __forceinline__ const EriPairPrimF* get(const EriLaunchArgs& a) { return a.pprims_f; }
+};
 
 __device__ __forceinline__ double eri_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float eri_fma(float a, float b, float c) { return fmaf(a, b, c); }
@@ -278,7 +312,8 @@ __device__ __forceinline__ void eri_coop_team(const EriLaunchArgs& a, const EriC
       const int qi = q + l * stride;
       if (l < p.batch && qi < a.nq) {
         const EriQuartetRec r = a.quartets[qi];
-        eri_coop_row(a.pprims[a.pairs[ERI_PAIR_INDEX(r.bra)].prim_off], a.pprims[a.pairs[r.ket].prim_off], p.L,
+        const auto* const pp = EriPrimsOf<R>::get(a);
+        eri_coop_row(pp[a.pairs[ERI_PAIR_INDEX(r.bra)].prim_off], pp[a.pairs[r.ket].prim_off], p.L,
                      a.boys_tab, rows + l * ERI_COOP_NC);
       }
     }
@@ -289,7 +324,8 @@ __device__ __forceinline__ void eri_coop_team(const EriLaunchArgs& a, const EriC
       if (!single && l < nb) {
         const int pidx = b0 + l;
         const int i = pidx / kk, j = pidx - (pidx / kk) * kk;
-        eri_coop_row(a.pprims[bra_off + i], a.pprims[ket_off + j], p.L, a.boys_tab, rows + l * ERI_COOP_NC);
+        const auto* const pp = EriPrimsOf<R>::get(a);
+        eri_coop_row(pp[bra_off + i], pp[ket_off + j], p.L, a.boys_tab, rows + l * ERI_COOP_NC);
       }
       team_sync();
       for (int pi = 0; pi < nb; ++pi) {

@@ -473,7 +473,7 @@ struct PairBuilder {
 __global__ void eri_pair_setup_kernel(const DevPairIn* __restrict__ pin, int npair, const DevShell* __restrict__ sh,
                                       const double* __restrict__ ex, const double* __restrict__ co,
                                       const uint32_t* __restrict__ plist, EriPairRec* __restrict__ pairs,
-                                      EriPairPrim* __restrict__ pp) {
+                                      EriPairPrim* __restrict__ pp, EriPairPrimF* __restrict__ ppf) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npair) return;
   const DevPairIn in = pin[p];
@@ -523,6 +523,7 @@ __global__ void eri_pair_setup_kernel(const DevPairIn* __restrict__ pin, int npa
     }
     q.K = C0 * co[A.prim + i] * na * co[B.prim + j] * nb * exp(-a * b * iz * ab2) * iz;
     pp[in.prim_off + k] = q;
+    if (ppf) ppf[in.prim_off + k] = eri_pair_prim_f32(q);
   }
 }
 
@@ -636,6 +637,7 @@ struct eri_mol_s {
   DevBuf<uint32_t> plist_d;
   DevBuf<EriPairRec> pairs_d;
   DevBuf<EriPairPrim> pprims_d;
+  DevBuf<EriPairPrimF> pprims_f;  // FP32 copy, for mixed-precision plans
 };
 
 struct eri_plan_s {
@@ -654,6 +656,7 @@ struct eri_plan_s {
   DevBuf<uint32_t> plist;
   DevBuf<EriPairRec> pairs;
   DevBuf<EriPairPrim> pprims;
+  DevBuf<EriPairPrimF> pprims_f;  // FP32 copy, when the plan has FP32 parts
   DevBuf<EriQuartetRec> quartets;
   DevBuf<double> scratch;
   DevBuf<double> outbuf;
@@ -1425,6 +1428,7 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
         (rc = plan->coefs.upload(co, "coefficients")) || (rc = plan->pin.upload(pin, "pair list")) ||
         (rc = plan->plist.upload(pb.plist, "primitive-pair lists")) ||
         (rc = plan->pairs.alloc(pin.size(), "pairs")) || (rc = plan->pprims.alloc(pb.pprim, "primitive pairs")) ||
+        (plan->nparts32 > 0 && (rc = plan->pprims_f.alloc(pb.pprim, "primitive pairs (FP32)"))) ||
         (rc = plan->quartets.upload(recs, "quartet records")))
       return rc;
     plan->npair = (int)pin.size();
@@ -1590,11 +1594,13 @@ extern "C" int eri_mol_create(const eri_shell* shells, int32_t nshell, const eri
   if ((rc = m->shells_d.upload(dsh, "shells")) || (rc = m->exps_d.upload(m->exps, "exponents")) ||
       (rc = m->coefs_d.upload(m->coefs, "coefficients")) || (rc = m->pin_d.upload(m->pb.pin, "pair list")) ||
       (rc = m->plist_d.upload(m->pb.plist, "primitive-pair lists")) ||
-      (rc = m->pairs_d.alloc(m->npair, "pairs")) || (rc = m->pprims_d.alloc(m->pb.pprim, "primitive pairs")))
+      (rc = m->pairs_d.alloc(m->npair, "pairs")) || (rc = m->pprims_d.alloc(m->pb.pprim, "primitive pairs")) ||
+      (rc = m->pprims_f.alloc(m->pb.pprim, "primitive pairs (FP32)")))
     return rc;
   const int threads = 128;
   eri_pair_setup_kernel<<<(m->npair + threads - 1) / threads, threads>>>(
-      m->pin_d.p, m->npair, m->shells_d.p, m->exps_d.p, m->coefs_d.p, m->plist_d.p, m->pairs_d.p, m->pprims_d.p);
+      m->pin_d.p, m->npair, m->shells_d.p, m->exps_d.p, m->coefs_d.p, m->plist_d.p, m->pairs_d.p, m->pprims_d.p,
+      m->pprims_f.p);
   CUDA_OR(cudaGetLastError(), "pair set-up launch");
   CUDA_OR(cudaDeviceSynchronize(), "pair set-up");
   *out = m.release();
@@ -1703,7 +1709,7 @@ static int compute_impl(eri_plan_t* plan, double* out, void* stream_, const Fuse
     if (blocks > 0) {
       eri_pair_setup_kernel<<<blocks, threads, 0, stream>>>(plan->pin.p, plan->npair, plan->shells.p, plan->exps.p,
                                                             plan->coefs.p, plan->plist.p, plan->pairs.p,
-                                                            plan->pprims.p);
+                                                            plan->pprims.p, plan->pprims_f.p);
       CUDA_OR(cudaGetLastError(), "pair set-up launch");
     }
     CUDA_OR(mark(1), "cudaEventRecord");
@@ -1729,6 +1735,7 @@ static int compute_impl(eri_plan_t* plan, double* out, void* stream_, const Fuse
     a.quartets = plan->quartets.p + b.first;
     a.pairs = plan->pairs.p;
     a.pprims = plan->mol ? plan->mol->pprims_d.p : plan->pprims.p;
+    a.pprims_f = plan->mol ? plan->mol->pprims_f.p : plan->pprims_f.p;
     a.boys_tab = L.d_boys;
     a.out = out;
     a.scratch = plan->scratch.p;
@@ -2042,7 +2049,7 @@ extern "C" int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* st
     if (blocks > 0) {
       eri_pair_setup_kernel<<<blocks, threads, 0, stream>>>(plan->pin.p, plan->npair, plan->shells.p, plan->exps.p,
                                                             plan->coefs.p, plan->plist.p, plan->pairs.p,
-                                                            plan->pprims.p);
+                                                            plan->pprims.p, plan->pprims_f.p);
       CUDA_OR(cudaGetLastError(), "pair set-up launch");
     }
   }
@@ -2055,6 +2062,7 @@ extern "C" int eri_compute_fixed_scratch(eri_plan_t* plan, double* out, void* st
     a.quartets = plan->quartets.p + b.first;
     a.pairs = plan->pairs.p;
     a.pprims = plan->mol ? plan->mol->pprims_d.p : plan->pprims.p;
+    a.pprims_f = plan->mol ? plan->mol->pprims_f.p : plan->pprims_f.p;
     a.boys_tab = L.d_boys;
     a.out = out;
     a.scratch = scratch;

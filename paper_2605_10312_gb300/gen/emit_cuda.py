@@ -54,16 +54,16 @@ def _coef_defs(syms, real="double"):
     """Definitions of the integer-multiple coefficients a class uses:
     c1z_k = k/(2 zeta), c2z_k = -k rho/(2 zeta^2), likewise for eta, and
     c3_k = k/(2(zeta+eta)).  In single precision every coefficient is
-    formed in FP64 and rounded once."""
+    formed in FP32 from the FP32 pair and primitive-quartet data."""
     lines = []
     if real == "float":
         src = {"PA": "bp.PA[{}]", "QC": "kp.PA[{}]", "WP": "pq.WP[{}]", "WQ": "pq.WQ[{}]"}
         for kind, k in sorted(s for s in syms if s[0] in src):
-            lines.append("    const float f{}_{} = (float){};".format(kind, k, src[kind].format(k)))
+            lines.append("    const float f{}_{} = {};".format(kind, k, src[kind].format(k)))
         base = {"c1z": "bp.inv2z", "c1e": "kp.inv2z", "c2z": "(-bp.inv2z * pq.te)",
-                "c2e": "(-kp.inv2z * pq.tz)", "c3": "(0.5 * pq.s)"}
+                "c2e": "(-kp.inv2z * pq.tz)", "c3": "(0.5f * pq.s)"}
         for kind, k in sorted(s for s in syms if s[0] in base):
-            lines.append("    const float {}_{} = (float)({}.0 * {});".format(kind, k, k, base[kind]))
+            lines.append("    const float {}_{} = {}.0f * {};".format(kind, k, k, base[kind]))
         return lines
     need = sorted(s for s in syms if s[0] in ("c1z", "c2z", "c1e", "c2e", "c3"))
     have = set()
@@ -152,18 +152,28 @@ def emit_class(prog, tier="reg", threads=128, real="double"):
     w("  const int nk = valid ? bra.nprim : 0;")
     w("  int i = r / kk, j = r - (r / kk) * kk;")
     w("  while (i < nk) {")
-    w("    const EriPairPrim bp = a.pprims[bra.prim_off + i];")
-    w("    const EriPairPrim kp = a.pprims[ket.prim_off + j];")
+    if real == "float":
+        # FP32 set-up from the FP32 pair data; the Boys function in FP64
+        w("    const EriPairPrimF bp = a.pprims_f[bra.prim_off + i];")
+        w("    const EriPairPrimF kp = a.pprims_f[ket.prim_off + j];")
+    else:
+        w("    const EriPairPrim bp = a.pprims[bra.prim_off + i];")
+        w("    const EriPairPrim kp = a.pprims[ket.prim_off + j];")
     w("    j += G;")
     w("    while (j >= kk) { j -= kk; ++i; }")
-    w("    EriPrimQuartet pq;")
-    w("    eri_prim_quartet(bp, kp, pq);")
-    w("    double F[{}];".format(L + 1))
-    w("    eri_boys<{}>(pq.T, F, a.boys_tab);".format(L))
     if real == "float":
+        w("    EriPrimQuartetF pq;")
+        w("    eri_prim_quartet_f32(bp, kp, pq);")
+        w("    double F[{}];".format(L + 1))
+        w("    eri_boys<{}>((double)pq.T, F, a.boys_tab);".format(L))
         used_m = sorted(set(g.keys[v][2] for v in prog.order if not g.terms[v]))
         for m in used_m:
-            w("    const float fF{0} = (float)(pq.pref * F[{0}]);".format(m))
+            w("    const float fF{0} = pq.pref * (float)F[{0}];".format(m))
+    else:
+        w("    EriPrimQuartet pq;")
+        w("    eri_prim_quartet(bp, kp, pq);")
+        w("    double F[{}];".format(L + 1))
+        w("    eri_boys<{}>(pq.T, F, a.boys_tab);".format(L))
     for ln in _coef_defs(prog.coef_syms, real):
         w(ln)
     slot = prog.slot
