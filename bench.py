@@ -872,7 +872,8 @@ def run_serve(args):
     # driver's own threads), at most 16
     planners = args.planners or max(1, min(16, (os.cpu_count() or 3) - 2))
     srv = serve.Server(budget_bytes=args.serve_budget_gb << 30, slots=args.slots, planners=planners,
-                       fp32_below=args.fp32_below if args.fp32_below is not None else 1e-6, timeout_s=30.0)
+                       fp32_below=args.fp32_below if args.fp32_below is not None else 1e-6, timeout_s=30.0,
+                       chunk_quartets=args.chunk or None)
     t0 = time.perf_counter()
     pools = {}
     sizes = sorted(int(x) for x in rng.integers(4, 67, size=args.molecules))
@@ -895,6 +896,7 @@ def run_serve(args):
                         "Schwarz {:g}, requests of 1e3-1e6 quartets, FP32 below {:g}".format(
                             len(sizes), sizes, args.threshold, srv.fp32_below),
             "slots": args.slots, "planners": planners, "budget_gb": args.serve_budget_gb,
+            "chunk_quartets": args.chunk or None,
             "requests_per_phase": args.requests, "setup_s": setup_s, "capacity_requests_per_s": cap,
             "phases": phases}
     print(json.dumps(line))
@@ -919,6 +921,9 @@ def main():
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per phase")
     ap.add_argument("--molecules", type=int, default=8, help="serve: molecules in the pool")
     ap.add_argument("--slots", type=int, default=16, help="serve: concurrent requests (streams)")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="serve: requests above this many quartets run as parallel chunk plans while few "
+                         "requests are in flight (0: never)")
     ap.add_argument("--planners", type=int, default=0, help="serve: host planner threads (0: cores - 2)")
     ap.add_argument("--serve-budget-gb", type=int, default=16, help="serve: device-memory budget")
     ap.add_argument("--waters", type=int, default=20)

@@ -17,6 +17,18 @@ arrive:
     its slot's stream, so requests that arrive while others are on the
     device overlap with them, and the request loop only admits, polls and
     retires;
+  * large requests (off by default): with chunk_quartets set, while fewer
+    than chunk_inflight requests are in flight, a request of more than
+    chunk_quartets quartets is cut into contiguous chunks whose plans are
+    built in parallel on a second pool of host threads, then launched in
+    order on the slot's stream into consecutive ranges of one output
+    buffer.  Chunk plans add class launches of their own: measured on the
+    serving benchmark, chunking every large request cut the burst capacity
+    from 194 to 154 requests/s (chunks of 250,000 quartets) and 88
+    (100,000) and raised p50 at 50 requests/s from 18 to 22 ms while it cut
+    p99 there from 213 to 150 ms; chunking only while fewer than half the
+    planner threads were busy kept the capacity (191) but left p99 at 337
+    ms;
   * completion: polled with CUDA events; a request that has not finished
     within its timeout is reported with status "timeout" (the host stops
     waiting for it; its memory is reclaimed when the device finishes);
@@ -78,12 +90,19 @@ class Result:
 
 class Server:
     def __init__(self, budget_bytes=8 << 30, slots=8, planners=4, fp32_below=1e-6, timeout_s=10.0,
-                 keep_outputs=False, poll_s=50e-6):
+                 keep_outputs=False, poll_s=50e-6, chunk_quartets=None, chunk_inflight=None):
         import torch
         self.torch = torch
         self.budget = int(budget_bytes)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.pool = cf.ThreadPoolExecutor(max_workers=planners)
+        # chunk plans of large requests (a planner thread waits on them, so
+        # they need threads of their own)
+        self.chunk_quartets = chunk_quartets
+        self.chunk_pool = cf.ThreadPoolExecutor(max_workers=planners)
+        # chunking applies while fewer requests than this are in flight
+        self.chunk_inflight = chunk_inflight if chunk_inflight is not None else max(1, planners // 2)
+        self.chunked = 0  # requests run as several chunk plans
         self.fp32_below = fp32_below
         self.timeout_s = timeout_s
         self.keep_outputs = keep_outputs
@@ -92,6 +111,7 @@ class Server:
 
     def close(self):
         self.pool.shutdown(wait=True)
+        self.chunk_pool.shutdown(wait=True)
         for m in self.molecules.values():
             if m.mol is not None:
                 m.mol.close()
@@ -108,22 +128,33 @@ class Server:
 
     # -- accounting ---------------------------------------------------------
     @staticmethod
-    def footprint(mol, quartets):
+    def chunks(n, chunk_quartets):
+        """Quartet ranges [lo, hi) of the plans of a request of n quartets."""
+        k = 1 if not chunk_quartets or n <= chunk_quartets else -(-n // chunk_quartets)
+        cuts = [n * i // k for i in range(k + 1)]
+        return list(zip(cuts[:-1], cuts[1:]))
+
+    @staticmethod
+    def footprint(mol, quartets, chunk_quartets=None):
         """Device bytes a request holds while it runs: its output blocks, up
-        to four quartet-part records per quartet and its copy of the
-        molecule's pair records."""
+        to four quartet-part records per quartet and, per plan (one per
+        chunk), a copy of the molecule's pair records."""
         q = np.asarray(quartets)
         ns = mol.nsph if mol.nsph is not None else NSPH[mol.basis.shell_l].astype(np.int64)
         out = int((ns[q[:, 0]] * ns[q[:, 1]] * ns[q[:, 2]] * ns[q[:, 3]]).sum())
         npair = 2 * mol.pairs.shape[0]
-        return 8 * out + 4 * 32 * q.shape[0] + 32 * npair + (1 << 16)
+        nplan = len(Server.chunks(q.shape[0], chunk_quartets))
+        return 8 * out + 4 * 32 * q.shape[0] + nplan * (32 * npair + (1 << 16))
 
     def bounds(self, mol, quartets):
         return screen.quartet_bounds(mol.pair_q, quartets)
 
     # -- one request --------------------------------------------------------
-    def _build(self, req, stream):
+    def _build(self, req, stream, lo=0, hi=None):
+        """The plan of quartets [lo, hi) of a request."""
         mol = self.molecules[req.mol]
+        if lo != 0 or hi is not None:
+            req = Request(req.rid, req.mol, req.quartets[lo:hi], req.arrival)
         # a request's class launches spread over the plan's streams (measured:
         # one stream per plan leaves small requests' kernels too narrow to
         # fill the GPU -- capacity 106 against 138 requests/s)
@@ -132,7 +163,7 @@ class Server:
         qb = self.bounds(mol, req.quartets)
         return eri.Plan(None, req.quartets, qbound=qb, fp32_below=self.fp32_below, mol=mol.mol, stream=stream)
 
-    def _build_and_launch(self, req, stream):
+    def _build_and_launch(self, req, stream, chunk=None):
         """On a planner thread: the request's plan, its output buffer and its
         launches on the slot's stream, then an event after them.  Launching
         a plan's few hundred class kernels takes milliseconds of host time,
@@ -140,13 +171,22 @@ class Server:
         request (measured: it bounded capacity at 167 requests/s with 16
         slots)."""
         torch = self.torch
-        plan = self._build(req, stream)
+        ranges = self.chunks(req.quartets.shape[0], chunk)
+        if len(ranges) == 1:
+            plans = [self._build(req, stream)]
+        else:
+            futs = [self.chunk_pool.submit(self._build, req, stream, lo, hi) for lo, hi in ranges[1:]]
+            plans = [self._build(req, stream, *ranges[0])] + [f.result() for f in futs]
+        counts = [p.output_count for p in plans]
         with torch.cuda.stream(stream):
-            out = torch.empty(max(1, plan.output_count), dtype=torch.float64, device="cuda")
-            plan.compute(out, stream)
+            out = torch.empty(max(1, sum(counts)), dtype=torch.float64, device="cuda")
+            off = 0
+            for p, c in zip(plans, counts):
+                p.compute(out[off:off + c], stream)
+                off += c
             ev = torch.cuda.Event()
             ev.record(stream)
-        return plan, out, ev, plan.stats()["fp32_parts"]
+        return plans, out, ev, sum(p.stats()["fp32_parts"] for p in plans)
 
     def run_alone(self, req):
         """The request evaluated by itself (plain plan, default stream
@@ -185,7 +225,12 @@ class Server:
             # admission in arrival order while the head fits
             while queue and free_slots:
                 req = queue[0]
-                nbytes = self.footprint(self.molecules[req.mol], req.quartets)
+                # chunk plans only while the planner threads have room
+                light = len(planning) + len(running) < self.chunk_inflight
+                chunk = self.chunk_quartets if light else None
+                if len(self.chunks(req.quartets.shape[0], chunk)) > 1:
+                    self.chunked += 1
+                nbytes = self.footprint(self.molecules[req.mol], req.quartets, chunk)
                 if nbytes > self.budget:
                     queue.popleft()
                     res = results[req.rid]
@@ -198,28 +243,29 @@ class Server:
                 slot = free_slots.pop()
                 free_bytes -= nbytes
                 results[req.rid].admitted = now
-                fut = self.pool.submit(self._build_and_launch, req, self.streams[slot])
+                fut = self.pool.submit(self._build_and_launch, req, self.streams[slot], chunk)
                 planning[fut] = (req, slot, nbytes)
                 progressed = True
             # plans built and launched by the planner threads
             for fut in [f for f in planning if f.done()]:
                 req, slot, nbytes = planning.pop(fut)
-                plan, out, ev, fp32_parts = fut.result()
+                plans, out, ev, fp32_parts = fut.result()
                 res = results[req.rid]
                 res.launched = time.perf_counter() - t0
                 res.fp32_parts = fp32_parts
-                running.append([req, slot, nbytes, plan, out, ev, False])
+                running.append([req, slot, nbytes, plans, out, ev, False])
                 progressed = True
             # completions (bounded waits)
             still = []
             for item in running:
-                req, slot, nbytes, plan, out, ev, timed_out = item
+                req, slot, nbytes, plans, out, ev, timed_out = item
                 res = results[req.rid]
                 if ev.query():
                     t = time.perf_counter() - t0
                     if not timed_out:
                         res.finished = t
-                    plan.close()   # stream-ordered: frees after the work on the slot's stream
+                    for p in plans:
+                        p.close()  # stream-ordered: frees after the work on the slot's stream
                     if self.keep_outputs and not timed_out:
                         res.output = out
                     del out
@@ -258,7 +304,19 @@ def summary(results, offered_span=None):
         "offered_requests_per_s": (len(results) - 1) / span if span > 0 else None,
         "offered_quartets_per_s": sum(r.quartets for r in results) / span if span > 0 else None,
         "fp32_parts": int(sum(r.fp32_parts for r in ok)),
+        # where the time of the largest 5% of requests goes: waiting for
+        # admission, planning and launching, and the device work
+        "largest_5pct": _stages([r for r in ok if r.quartets >= np.percentile([x.quartets for x in ok], 95)])
+        if ok else None,
     }
+
+
+def _stages(rs):
+    ms = lambda xs: float(np.mean(xs) * 1e3) if len(xs) else None
+    return {"requests": len(rs), "quartets_mean": float(np.mean([r.quartets for r in rs])) if rs else None,
+            "admit_ms": ms([r.admitted - r.arrival for r in rs]),
+            "plan_launch_ms": ms([r.launched - r.admitted for r in rs]),
+            "device_ms": ms([r.finished - r.launched for r in rs])}
 
 
 def screened_pool(mol, threshold, n, seed):

@@ -27,9 +27,13 @@ def _setup(serve, srv, sizes=(2, 3, 4), nq=(200, 4000), nreq=16, rate=2000.0, se
     return serve.poisson_requests(pools, rate=rate, nreq=nreq, nq_range=nq, seed=seed)
 
 
-def test_results_alone_equal_results_in_the_mix(server_mod):
+@pytest.mark.parametrize("chunk", [None, 1500])
+def test_results_alone_equal_results_in_the_mix(server_mod, chunk):
+    """chunk 1500: requests of more than 1,500 quartets run as two or three
+    chunk plans built in parallel, into one output buffer."""
     serve = server_mod
-    srv = serve.Server(budget_bytes=1 << 30, slots=4, planners=3, fp32_below=1e-6, keep_outputs=True)
+    srv = serve.Server(budget_bytes=1 << 30, slots=4, planners=3, fp32_below=1e-6, keep_outputs=True,
+                       chunk_quartets=chunk, chunk_inflight=100)
     reqs = _setup(serve, srv)
     res = srv.serve(reqs)
     assert all(r.status == "ok" for r in res)
@@ -37,6 +41,8 @@ def test_results_alone_equal_results_in_the_mix(server_mod):
     order = sorted(res, key=lambda r: r.admitted)
     assert any(b.admitted < a.finished for a, b in zip(order, order[1:]))
     assert sum(r.fp32_parts for r in res) > 0
+    if chunk:
+        assert srv.chunked > 0
     for req, r in zip(reqs, res):
         alone = srv.run_alone(req).cpu().numpy()
         mixed = r.output.cpu().numpy()[: alone.shape[0]]

@@ -94,6 +94,8 @@ class _Tracker:
         self.budget, self.slots, self.mol, self.duration = budget, slots, mol, duration
         self.lock = threading.Lock()   # plans are launched from planner threads
         self.live = set()
+        self.plans_of = {}
+        self.streams_of = {}
         self.max_live = 0
         self.launch_order = []
 
@@ -113,7 +115,12 @@ class _Tracker:
                     tr.max_live = max(tr.max_live, len(tr.live))
                     used = sum(serve.Server.footprint(tr.mol, p.q) for p in tr.live)
                     assert used <= tr.budget, "admitted beyond the memory budget"
-                    assert len(tr.live) <= tr.slots, "more requests in flight than slots"
+                    # a request may run as several chunk plans (its id is
+                    # the first shell index of its quartets)
+                    tr.plans_of.setdefault(int(self.q[0, 0]), []).append(self)
+                    tr.streams_of.setdefault(int(self.q[0, 0]), set()).add(id(st))
+                    reqs = {int(p.q[0, 0]) for p in tr.live}
+                    assert len(reqs) <= tr.slots, "more requests in flight than slots"
 
             def stats(self):
                 return {"fp32_parts": 0}
@@ -185,3 +192,37 @@ def test_timeout_is_reported_and_the_slot_held_until_the_work_ends(monkeypatch):
     assert res[0].finished - res[0].arrival < 0.25          # reported at the deadline, not at the end
     assert res[1].launched >= 0.29                          # the slot was held until the work ended
 
+
+
+def test_large_request_runs_as_chunk_plans(monkeypatch):
+    """A request of more than chunk_quartets quartets runs as ceil(n / chunk)
+    plans of contiguous quartet ranges, launched in order on its slot's
+    stream and all closed when its work ends; its footprint counts each chunk
+    plan's copy of the pair records (the sum of the chunk plans' footprints)."""
+    srv, tr, mol = _server(monkeypatch, budget=1 << 30, slots=2, timeout_s=5.0, duration=lambda q: 0.01)
+    srv.chunk_quartets = 400
+    reqs = _requests([1000, 300], [0.0, 0.0])
+    res = srv.serve(reqs)
+    srv.close()
+    assert [r.status for r in res] == ["ok", "ok"]
+    assert srv.chunked == 1
+    assert [p.q.shape[0] for p in tr.plans_of[0]] == [333, 333, 334]
+    assert len(tr.plans_of[1]) == 1
+    assert len(tr.streams_of[0]) == 1
+    assert not tr.live
+    assert serve.Server.chunks(1000, 400) == [(0, 333), (333, 666), (666, 1000)]
+    assert serve.Server.chunks(400, 400) == [(0, 400)] and serve.Server.chunks(7, None) == [(0, 7)]
+    whole = serve.Server.footprint(mol, reqs[0].quartets, 400)
+    assert whole == sum(serve.Server.footprint(mol, p.q) for p in tr.plans_of[0])
+
+
+def test_no_chunks_under_load(monkeypatch):
+    """With as many requests in flight as chunk_inflight, a large request
+    runs as one plan."""
+    srv, tr, _ = _server(monkeypatch, budget=1 << 30, slots=4, timeout_s=5.0, duration=lambda q: 0.05)
+    srv.chunk_quartets = 400
+    srv.chunk_inflight = 1
+    res = srv.serve(_requests([100, 1000], [0.0, 0.0]))
+    srv.close()
+    assert [r.status for r in res] == ["ok", "ok"]
+    assert len(tr.plans_of[1]) == 1 and srv.chunked == 0
