@@ -917,6 +917,15 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   std::vector<std::vector<int>> cls_keys;
   for (int64_t q = 0; q < nq; ++q) {
     const int32_t* s = quartets + 4 * q;
+    if (mol && q + 16 < nq) {
+      // the molecule's split table holds every shell pair, and a request's
+      // quartets index it at random: fetch quartet q + 16's entries early
+      const int32_t* t = s + 64;
+      const int64_t h0 = std::max(t[0], t[1]), l0 = std::min(t[0], t[1]);
+      const int64_t h1 = std::max(t[2], t[3]), l1 = std::min(t[2], t[3]);
+      __builtin_prefetch(&mol->splits[h0 * (h0 + 1) / 2 + l0]);
+      __builtin_prefetch(&mol->splits[h1 * (h1 + 1) / 2 + l1]);
+    }
     const int prec = mixed && qbound[q] < fp32_below ? 1 : 0;
     int n[4];
     for (int k = 0; k < 4; ++k) n[k] = nfun(shells[s[k]].l, cart);
@@ -1437,10 +1446,13 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
   {
     // a plan whose every quartet is (ab|ab) can also produce Schwarz bounds
     bool diag = true;
-    std::vector<int32_t> nab(nq);
     for (int64_t q = 0; q < nq && diag; ++q) {
       const int32_t* s4 = quartets + 4 * q;
       diag = s4[0] == s4[2] && s4[1] == s4[3];
+    }
+    std::vector<int32_t> nab(diag ? nq : 0);
+    for (int64_t q = 0; q < (int64_t)nab.size(); ++q) {
+      const int32_t* s4 = quartets + 4 * q;
       nab[q] = nfun(shells[s4[0]].l, cart) * nfun(shells[s4[1]].l, cart);
     }
     if (diag || opts.digest) {
