@@ -90,6 +90,13 @@ typedef struct {
                            512-thread block per SM takes items -- runs of one class's quartets -- from a
                            counter); the parts of a quartet reduce into its zeroed block in any order; tier
                            must be 0 or 4.  0: one launch per class bucket */
+  int32_t ordered;      /* a quartet evaluated in several parts (the two orientations of a split shell pair,
+                           chunks of a deep contraction): 0: every part runs in the same launch round and
+                           reduces into the quartet's zeroed block with FP64 atomic additions, so the last bits
+                           of such blocks depend on the order of the additions; 1: part k runs in launch round
+                           k and adds into the block in that order (bitwise reproducible; more launches, each
+                           round joined before the next).  Chunks of one part reduce atomically either way.
+                           A persistent plan takes 0 */
 } eri_opts;
 
 typedef struct eri_plan_s eri_plan_t;

@@ -43,7 +43,8 @@ class _Basis(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("axis_rule", ctypes.c_int32), ("schedule", ctypes.c_int32), ("sph_mode", ctypes.c_int32),
                 ("tier", ctypes.c_int32), ("orientation", ctypes.c_int32), ("streams", ctypes.c_int32),
-                ("digest", ctypes.c_int32), ("votes", ctypes.c_int32), ("persistent", ctypes.c_int32)]
+                ("digest", ctypes.c_int32), ("votes", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("ordered", ctypes.c_int32)]
 
 
 _lib = None
@@ -194,12 +195,15 @@ class Plan:
 
     def __init__(self, basis, quartets, axis_rule="prose", schedule="dsa", sph_mode="stepwise", tier="auto",
                  orientation="split", qbound=None, fp32_below=None, streams=0, stream=None, digest=False,
-                 mol=None, votes="auto", persistent=False):
+                 mol=None, votes="auto", persistent=False, ordered=False):
         """qbound/fp32_below: mixed precision (eri_plan_mixed) -- quartets whose
         bound is below fp32_below run their recurrences in FP32.  stream: a
         stream-ordered plan (eri_plan_on_stream) whose device memory lives and
         dies on that stream; compute it on the same stream.  mol: a Mol whose
-        shells the quartets index (eri_plan_on_mol); basis is then ignored."""
+        shells the quartets index (eri_plan_on_mol); basis is then ignored.
+        ordered: the parts of a multi-part quartet add into its block in a
+        fixed order, one launch round each (bitwise reproducible); else they
+        run together and reduce atomically (fewer launches)."""
         lib = library()
         q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
         if mol is not None:
@@ -209,7 +213,7 @@ class Plan:
             self._keep = keep + [q]
         o = _Opts(AXIS_RULES[axis_rule], SCHEDULES[schedule], SPH_MODES[sph_mode], TIERS[tier],
                   ORIENTATIONS[orientation], int(streams), 1 if digest else 0, VOTES[votes],
-                  1 if persistent else 0)
+                  1 if persistent else 0, 1 if ordered else 0)
         h = ctypes.c_void_p()
         qb = None
         if qbound is not None:

@@ -22,7 +22,8 @@ def eri():
 def test_compute_host_matches_device(eri):
     import torch
     basis, q = synth.class_sweep((2, 1, 1, 0), 500, kset=(1, 3), seed=9, box_angstrom=3.0)
-    p = eri.Plan(basis, q)
+    # ordered: parts add in a fixed order, so two evaluations agree bit for bit
+    p = eri.Plan(basis, q, ordered=True)
     dev = torch.empty(p.output_count, dtype=torch.float64, device="cuda")
     p.compute(dev)
     host = torch.empty(p.output_count, dtype=torch.float64).pin_memory()
@@ -67,3 +68,27 @@ def test_unsupported_tier_is_an_error(eri):
     with pytest.raises(eri.EriError) as e:
         eri.Plan(basis, q, tier="reg")
     assert e.value.code == -2
+
+
+def test_ordered_parts_and_one_round_agree(eri):
+    """The default plan runs every part of a multi-part quartet in one launch
+    round, reducing into the zeroed block; an ordered plan adds the parts in
+    round order.  Same blocks up to the order of the additions, fewer launches
+    by default, and the ordered plan is bitwise reproducible."""
+    import torch
+    basis = synth.water_cluster(2, seed=8)
+    q = synth.all_unique_quartets(basis.nshell)
+    p1 = eri.Plan(basis, q)
+    p2 = eri.Plan(basis, q, ordered=True)
+    assert p1.stats()["launches"] < p2.stats()["launches"]
+    a = torch.empty(p1.output_count, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    c = torch.empty_like(a)
+    p1.compute(a)
+    p2.compute(b)
+    p2.compute(c)
+    torch.cuda.synchronize()
+    assert torch.equal(b, c)
+    assert torch.allclose(a, b, rtol=1e-13, atol=1e-16)
+    with pytest.raises(eri.EriError):
+        eri.Plan(basis, q, ordered=True, persistent=True)

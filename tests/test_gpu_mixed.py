@@ -84,8 +84,9 @@ def test_mixed_threshold_zero_is_fp64(eri):
     import torch
     basis, q = synth.class_sweep((2, 1, 1, 0), 300, kset=(1, 3), seed=2)
     qb = np.full(q.shape[0], 1e-3)
-    p64 = eri.Plan(basis, q)
-    pmx = eri.Plan(basis, q, qbound=qb, fp32_below=0.0)
+    # ordered: parts add in a fixed order, so the two agree bit for bit
+    p64 = eri.Plan(basis, q, ordered=True)
+    pmx = eri.Plan(basis, q, qbound=qb, fp32_below=0.0, ordered=True)
     assert pmx.stats()["fp32_parts"] == 0
     a = torch.empty(p64.output_count, dtype=torch.float64, device="cuda")
     b = torch.empty_like(a)
