@@ -1032,14 +1032,25 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
     FlatMap sig_id;
     std::vector<std::pair<int64_t, int32_t>> sigs;  // (K4, kb)
     std::vector<uint32_t> key(nparts);
+    // signatures of up to 64 x 64 primitive pairs (nearly all) by direct
+    // lookup, the rest through the hash map
+    constexpr int kSmallSig = 64;
+    std::vector<int32_t> sig_small(kSmallSig * kSmallSig, -1);
     for (int64_t q = 0; q < nparts; ++q) {
       const QInfo& x = qi[q];
       gdense[gid(x)] = 0;
-      const uint64_t sk = ((uint64_t)(uint32_t)x.kb << 32) | (uint32_t)x.kk;
-      key[q] = (uint32_t)sig_id.get_or_insert(sk, [&] {
+      auto make = [&] {
         sigs.push_back({(int64_t)x.kb * x.kk, x.kb});
         return (int32_t)sigs.size() - 1;
-      });
+      };
+      if (x.kb <= kSmallSig && x.kk <= kSmallSig) {
+        int32_t& id = sig_small[(x.kb - 1) * kSmallSig + x.kk - 1];
+        if (id < 0) id = make();
+        key[q] = (uint32_t)id;
+      } else {
+        const uint64_t sk = ((uint64_t)(uint32_t)x.kb << 32) | (uint32_t)x.kk;
+        key[q] = (uint32_t)sig_id.get_or_insert(sk, make);
+      }
     }
     int32_t ng = 0;
     for (int32_t& g : gdense)
