@@ -234,8 +234,12 @@ int eri_plan_launch_precision(const eri_plan_t* plan, int i);
  * bits depend on the order of the additions).  nbf must equal the number of
  * basis functions of the plan's shells (spherical, or Cartesian with
  * sph_mode 2), shells numbered consecutively.  The plan must have been built
- * with opts.digest = 1.  Asynchronous on stream.  Errors: ERI_EINVAL (NULL
- * blocks or density, wrong nbf), ERI_ESTATE (plan without digest data). */
+ * with opts.digest = 1.  Asynchronous on stream.  Each mirrored pair of J (or
+ * K) entries receives one reduction, into a plan-owned triangle (2 nbf^2
+ * doubles, allocated with the plan when at most 1 GiB) that is then added
+ * into J and K on the same stream; digestions of one plan must therefore not
+ * overlap on different streams.  Errors: ERI_EINVAL (NULL blocks or density,
+ * wrong nbf), ERI_ESTATE (plan without digest data). */
 int eri_digest_jk(eri_plan_t* plan, const double* blocks, const double* density, int32_t nbf, double* J,
                   double* K, void* stream);
 

@@ -21,7 +21,9 @@
 // Blocks of up to 128 elements are digested by one thread each (a warp
 // covers 32 quartets); larger blocks by one warp each, whose lanes own output
 // entries of one contraction at a time (no two lanes add to the same entry).
-// Blocks are read through L1; J and K receive FP64 reductions.
+// Blocks are read through L1; J and K receive FP64 reductions.  With
+// EriDigestArgs.tri the two mirrored entries of each contribution receive
+// one reduction, into a triangle that is folded into J and K afterwards.
 #include "eri_digest.cuh"
 
 __global__ void __launch_bounds__(128) eri_digest_small_kernel(const EriDigestArgs g) {
@@ -38,6 +40,23 @@ __global__ void __launch_bounds__(128) eri_digest_warp_kernel(const EriDigestArg
     const int64_t q = g.list[w];
     eri_digest_quartet(g, q, threadIdx.x & 31, 32, g.blocks + g.offsets[q], [](const double* p) { return *p; });
   }
+}
+
+// M[r][c] += T[min(r, c)][max(r, c)]: a triangle of mirrored-pair sums (see
+// eri_jk_add) added into the caller's full n x n matrix.
+__global__ void __launch_bounds__(256) eri_digest_fold_kernel(const double* __restrict__ T, double* __restrict__ M,
+                                                             int n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int64_t r = t / n, c = t - r * n;
+  M[t] += r <= c ? T[t] : T[c * n + r];
+}
+
+extern "C" cudaError_t eri_digest_fold_launch(const double* T, double* M, int n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nn = (int64_t)n * n;
+  eri_digest_fold_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(T, M, n);
+  return cudaGetLastError();
 }
 
 // small = 1: one thread per quartet of the list (32 per warp), else one warp

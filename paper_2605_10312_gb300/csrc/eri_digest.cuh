@@ -18,7 +18,26 @@ struct EriDigestArgs {
   double* K;                             // [nbf][nbf] or null
   int64_t nq;
   int32_t nbf;
+  int32_t tri;  // 1: J and K are triangle scratch (one reduction per mirrored pair, see eri_jk_add)
 };
+
+// Add s to M_rc and M_cr (every J and K contribution comes in such mirrored
+// pairs).  tri: only the entry with r <= c receives the pair (2 s on the
+// diagonal), halving the reductions; the triangle is folded into the
+// caller's full matrix afterwards.
+__device__ __forceinline__ void eri_jk_add(double* M, int64_t n, int64_t r, int64_t c, double s, bool tri) {
+  if (tri) {
+    if (r > c) {
+      const int64_t t = r;
+      r = c;
+      c = t;
+    }
+    atomicAdd(M + r * n + c, r == c ? 2.0 * s : s);
+  } else {
+    atomicAdd(M + r * n + c, s);
+    atomicAdd(M + c * n + r, s);
+  }
+}
 
 // number of the 8 index permutations that map (a b | c d) onto itself
 __device__ __forceinline__ int eri_stabilizer(int a, int b, int c, int d) {
@@ -45,6 +64,7 @@ __device__ __forceinline__ void eri_digest_quartet(const EriDigestArgs& g, int64
             nd = g.shell_bf[d + 1] - Dd;
   const double f = 1.0 / (double)eri_stabilizer(a, b, c, d);
   const double* __restrict__ Dm = g.D;
+  const bool tri = g.tri != 0;
   const int64_t n = g.nbf;
   const int sj = nc * nd, si = nb * sj;  // strides of i and j in the block; k stride nd
   if (g.J) {
@@ -56,8 +76,7 @@ __device__ __forceinline__ void eri_digest_quartet(const EriDigestArgs& g, int64
       for (int k = 0; k < nc; ++k)
         for (int l = 0; l < nd; ++l) s = fma(ld(r + k * nd + l), __ldg(Dm + (C + k) * n + Dd + l), s);
       s *= 2.0 * f;
-      atomicAdd(g.J + (A + i) * n + B + j, s);
-      atomicAdd(g.J + (B + j) * n + A + i, s);
+      eri_jk_add(g.J, n, A + i, B + j, s, tri);
     }
     // Jcd[k][l] = 2 f sum_ij v D_ij
     for (int o = lane; o < nc * nd; o += W) {
@@ -67,8 +86,7 @@ __device__ __forceinline__ void eri_digest_quartet(const EriDigestArgs& g, int64
         for (int j = 0; j < nb; ++j)
           s = fma(ld(v + (int64_t)i * si + (int64_t)j * sj + o), __ldg(Dm + (A + i) * n + B + j), s);
       s *= 2.0 * f;
-      atomicAdd(g.J + (C + k) * n + Dd + l, s);
-      atomicAdd(g.J + (Dd + l) * n + C + k, s);
+      eri_jk_add(g.J, n, C + k, Dd + l, s, tri);
     }
   }
   if (g.K) {
@@ -80,8 +98,7 @@ __device__ __forceinline__ void eri_digest_quartet(const EriDigestArgs& g, int64
         for (int l = 0; l < nd; ++l)
           s = fma(ld(v + (int64_t)i * si + (int64_t)j * sj + k * nd + l), __ldg(Dm + (B + j) * n + Dd + l), s);
       s *= f;
-      atomicAdd(g.K + (A + i) * n + C + k, s);
-      atomicAdd(g.K + (C + k) * n + A + i, s);
+      eri_jk_add(g.K, n, A + i, C + k, s, tri);
     }
     // Kad[i][l] = f sum_jk v D_jk
     for (int o = lane; o < na * nd; o += W) {
@@ -91,8 +108,7 @@ __device__ __forceinline__ void eri_digest_quartet(const EriDigestArgs& g, int64
         for (int k = 0; k < nc; ++k)
           s = fma(ld(v + (int64_t)i * si + (int64_t)j * sj + k * nd + l), __ldg(Dm + (B + j) * n + C + k), s);
       s *= f;
-      atomicAdd(g.K + (A + i) * n + Dd + l, s);
-      atomicAdd(g.K + (Dd + l) * n + A + i, s);
+      eri_jk_add(g.K, n, A + i, Dd + l, s, tri);
     }
     // Kbc[j][k] = f sum_il v D_il
     for (int o = lane; o < nb * nc; o += W) {
@@ -102,8 +118,7 @@ __device__ __forceinline__ void eri_digest_quartet(const EriDigestArgs& g, int64
         for (int l = 0; l < nd; ++l)
           s = fma(ld(v + (int64_t)i * si + (int64_t)j * sj + k * nd + l), __ldg(Dm + (A + i) * n + Dd + l), s);
       s *= f;
-      atomicAdd(g.K + (B + j) * n + C + k, s);
-      atomicAdd(g.K + (C + k) * n + B + j, s);
+      eri_jk_add(g.K, n, B + j, C + k, s, tri);
     }
     // Kbd[j][l] = f sum_ik v D_ik
     for (int o = lane; o < nb * nd; o += W) {
@@ -113,8 +128,7 @@ __device__ __forceinline__ void eri_digest_quartet(const EriDigestArgs& g, int64
         for (int k = 0; k < nc; ++k)
           s = fma(ld(v + (int64_t)i * si + (int64_t)j * sj + k * nd + l), __ldg(Dm + (A + i) * n + C + k), s);
       s *= f;
-      atomicAdd(g.K + (B + j) * n + Dd + l, s);
-      atomicAdd(g.K + (Dd + l) * n + B + j, s);
+      eri_jk_add(g.K, n, B + j, Dd + l, s, tri);
     }
   }
 }

@@ -39,6 +39,7 @@ extern "C" cudaError_t eri_coop_boys_launch(const double* T, int64_t n, int L, c
                                             cudaStream_t stream);
 
 extern "C" cudaError_t eri_digest_launch(const EriDigestArgs* g, int small, cudaStream_t stream);
+extern "C" cudaError_t eri_digest_fold_launch(const double* T, double* M, int n, cudaStream_t stream);
 // blocks of up to this many elements are digested by one thread each
 static const int64_t kSmallBlock = 128;
 
@@ -681,6 +682,7 @@ struct eri_plan_s {
   DevBuf<int64_t> d_rsmall, d_rlarge;  // fused digestion: the same lists for quartets with no persistent part
   int32_t nbf = 0;
   bool digest = false;
+  DevBuf<double> jk_tri;             // digest plans: J and K triangles of mirrored-pair sums (2 nbf^2)
   DevBuf<int32_t> d_nab;
   cudaGraphExec_t graph_exec = nullptr;
   bool stream_ordered = false;         // built by eri_plan_on_stream: memory is freed on alloc_stream
@@ -1523,6 +1525,11 @@ static int plan_impl(const eri_shell* shells, int32_t nshell, const eri_basis* b
       return rc;
     plan->nbf = bf[nshell];
     plan->digest = true;
+    // triangle scratch for the digestion (one reduction per mirrored pair of
+    // J and K entries instead of two), when it is at most 1 GiB
+    const size_t tri = 2 * (size_t)plan->nbf * (size_t)plan->nbf;
+    if (tri > 0 && tri * sizeof(double) <= ((size_t)1 << 30) && (rc = plan->jk_tri.alloc(tri, "J/K triangles")))
+      return rc;
   }
   plan->h2d_bytes = (double)(dsh.size() * sizeof(DevShell) + 2 * ex.size() * sizeof(double) +
                              (mol ? mol_alias.size() * sizeof(EriPairRec)
@@ -1857,6 +1864,17 @@ static int digest_lists(eri_plan_t* plan, const double* blocks, const double* de
   g.K = K;
   g.nq = plan->nq;
   g.nbf = nbf;
+  g.tri = 0;
+  // mirrored pairs of J and K entries reduce once into the plan's triangles,
+  // which are then added into J and K
+  const size_t nn = (size_t)nbf * (size_t)nbf;
+  const bool tri = plan->jk_tri.n >= 2 * nn && nn > 0;
+  if (tri) {
+    CUDA_OR(cudaMemsetAsync(plan->jk_tri.p, 0, 2 * nn * sizeof(double), (cudaStream_t)stream), "zero J/K triangles");
+    g.J = J ? plan->jk_tri.p : nullptr;
+    g.K = K ? plan->jk_tri.p + nn : nullptr;
+    g.tri = 1;
+  }
   const DevBuf<int64_t>& sm = rest ? plan->d_rsmall : plan->d_small;
   const DevBuf<int64_t>& lg = rest ? plan->d_rlarge : plan->d_large;
   if (sm.n > 0) {
@@ -1868,6 +1886,10 @@ static int digest_lists(eri_plan_t* plan, const double* blocks, const double* de
     g.list = lg.p;
     g.nlist = (int64_t)lg.n;
     CUDA_OR(eri_digest_launch(&g, 0, (cudaStream_t)stream), "digest launch");
+  }
+  if (tri) {
+    if (J) CUDA_OR(eri_digest_fold_launch(plan->jk_tri.p, J, nbf, (cudaStream_t)stream), "fold J");
+    if (K) CUDA_OR(eri_digest_fold_launch(plan->jk_tri.p + nn, K, nbf, (cudaStream_t)stream), "fold K");
   }
   return ERI_OK;
 }
