@@ -716,6 +716,36 @@ def fp64_issue(cp):
     return int(i1.sum()), int(i2.sum())
 
 
+def fp64_balance(cp):
+    """How evenly a team's Phase-1 FP64 work is spread over the SM's four
+    sub-partitions within each wave (warp w of a team runs on sub-partition
+    w mod 4; the waves end at a barrier, so a wave lasts as long as its
+    busiest sub-partition): sum over waves of the FP64 warp-instructions
+    divided by sum over waves of 4 x the busiest sub-partition's share.  1.0
+    is perfect balance; meaningful for teams of 128 lanes or more, which
+    hold warps on all four sub-partitions."""
+    W = cp.T * cp.ilp
+    warps = cp.T // 32
+    n = int(np.sum(cp.steps1))
+    d = cp.ph1[: n * W].astype(np.int64).reshape(n, warps, 32, cp.ilp, 4)
+    meta = d[..., 3] >> 16
+    term = (meta & 0xC000) == 0
+
+    def any_lane(m):
+        return m.any(axis=2).astype(np.int64)
+
+    per = (2 * any_lane(term) + 2 * any_lane(term & (((meta >> 4) & 31) > 0))
+           + any_lane(term & (((meta >> 9) & 15) > 0))).sum(axis=2)  # [step, warp]
+    bounds = np.concatenate([[0], np.cumsum(cp.steps1.astype(np.int64))])
+    total = busiest = 0
+    for w in range(len(cp.steps1)):
+        per_warp = per[bounds[w]:bounds[w + 1]].sum(axis=0)
+        sub = np.bincount(np.arange(warps) % 4, weights=per_warp, minlength=4)
+        total += sub.sum()
+        busiest += 4 * sub.max()
+    return float(total / busiest) if busiest else 1.0
+
+
 ROW_BYTES = 56 * 8           # one primitive quartet's coefficient row (executor constant)
 DEEP_ROWS = 32               # rows per team for deep contractions (one per lane of a warp)
 SHALLOW_ROWS = 12            # rows per team for contractions of at most 12 primitive quartets

@@ -334,6 +334,27 @@ def test_fp64_issue_count_bounds():
     assert c["vrr_flops"] / (64 * i1) < 1 and c["p2_flops"] / (64 * i2) < 1
 
 
+def test_fp64_balance_over_sub_partitions():
+    """The sub-partition balance of a wave lies in (0, 1]; a team whose
+    FP64 work sits on one warp of four scores 1/4; the shipped (ff|ff) program
+    (128-lane teams, one warp per sub-partition) balances its waves to better
+    than 0.8."""
+    import copy
+    prog = program.make(3, 3, 3, 3)
+    deep, _ = coop.choose_both(prog)
+    assert deep.T == 128
+    b = coop.fp64_balance(deep)
+    assert 0.8 < b <= 1.0
+    # every descriptor of warps 1-3 made a no-op: all work on sub-partition 0
+    one = copy.deepcopy(deep)
+    W = one.T * one.ilp
+    n = int(one.steps1.sum())
+    ph = one.ph1[: n * W].reshape(n, one.T, one.ilp, 4)
+    ph[:, 32:] = 0
+    ph[:, 32:, :, 3] = 0x8000 << 16
+    assert abs(coop.fp64_balance(one) - 0.25) < 1e-12
+
+
 def test_gggg_production_program_matches_oracle():
     """The (gg|gg) cooperative program the build ships (512-lane teams,
     waves of up to four steps), walked wave by wave on the CPU, reproduces the
