@@ -23,7 +23,7 @@ arrive:
     built in parallel on a second pool of host threads, then launched in
     order on the slot's stream into consecutive ranges of one output
     buffer.  Chunk plans add class launches of their own: measured on the
-    serving benchmark, chunking every large request cut the burst capacity
+    serving benchmark (with plans of ordered part rounds), chunking every large request cut the burst capacity
     from 194 to 154 requests/s (chunks of 250,000 quartets) and 88
     (100,000) and raised p50 at 50 requests/s from 18 to 22 ms while it cut
     p99 there from 213 to 150 ms; chunking only while fewer than half the
@@ -228,8 +228,6 @@ class Server:
                 # chunk plans only while the planner threads have room
                 light = len(planning) + len(running) < self.chunk_inflight
                 chunk = self.chunk_quartets if light else None
-                if len(self.chunks(req.quartets.shape[0], chunk)) > 1:
-                    self.chunked += 1
                 nbytes = self.footprint(self.molecules[req.mol], req.quartets, chunk)
                 if nbytes > self.budget:
                     queue.popleft()
@@ -242,6 +240,8 @@ class Server:
                 queue.popleft()
                 slot = free_slots.pop()
                 free_bytes -= nbytes
+                if len(self.chunks(req.quartets.shape[0], chunk)) > 1:
+                    self.chunked += 1
                 results[req.rid].admitted = now
                 fut = self.pool.submit(self._build_and_launch, req, self.streams[slot], chunk)
                 planning[fut] = (req, slot, nbytes)
