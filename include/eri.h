@@ -81,7 +81,8 @@ typedef struct {
                            (the caller's plus streams the plan owns, joined back before eri_compute returns):
                            0 auto (4 for plans holding several classes, else 1), 1 serial, at most 8 */
   int32_t digest;       /* 1: also keep on the device what eri_digest_jk / eri_compute_jk need (the quartet list,
-                           16 B per quartet); 0: no */
+                           16 B per quartet, digestion lists, and the J/K triangles, 2 nbf^2 doubles when at
+                           most 1 GiB); 0: no */
   int32_t votes;        /* team-cooperative tier: 0 auto (the class table of eri_set_class_votes, else on for
                            teams of 128 lanes or more), 1 each lane predicates its optional FP64 terms, 2 each
                            optional term sits behind a warp vote */
@@ -94,9 +95,9 @@ typedef struct {
                            chunks of a deep contraction): 0: every part runs in the same launch round and
                            reduces into the quartet's zeroed block with FP64 atomic additions, so the last bits
                            of such blocks depend on the order of the additions; 1: part k runs in launch round
-                           k and adds into the block in that order (bitwise reproducible; more launches, each
-                           round joined before the next).  Chunks of one part reduce atomically either way.
-                           A persistent plan takes 0 */
+                           k and adds into the block in that order (bitwise reproducible for quartets whose
+                           parts are not chunked; more launches, each round joined before the next).  Chunks
+                           of one part reduce atomically either way.  A persistent plan takes 0 */
 } eri_opts;
 
 typedef struct eri_plan_s eri_plan_t;
